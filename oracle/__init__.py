@@ -1,0 +1,256 @@
+"""Python binding of the FP64 CPU oracle (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its binding) never does.
+
+The C library ``sdf_oracle.c`` restates the paper plainly in double
+precision: Eq. 2 (network), Alg. 2 with Eqs. 3-4 (analytic normals), Alg. 1
+(multiscale sphere tracing), the neural normal mapping of Sec. 5 and the
+threshold recurrences of Props. 1-2 (Sec. 3.3).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import platform
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "sdf_oracle.c"
+_BUILD = _HERE / "_build"
+
+SDF_KIND_NET, SDF_KIND_SPHERE, SDF_KIND_TORUS = 0, 1, 2
+
+
+def lib_path() -> Path:
+    return _BUILD / f"liboracle_{platform.machine()}.so"
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle with gcc (IEEE double, no contraction into FMA)."""
+    out = lib_path()
+    if out.exists() and not force and out.stat().st_mtime >= _SRC.stat().st_mtime:
+        return out
+    _BUILD.mkdir(exist_ok=True)
+    tmp = out.with_suffix(f".tmp{os.getpid()}.so")
+    cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+           "-Wall", "-o", str(tmp), str(_SRC), "-lm", "-lpthread"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+class _SDF(C.Structure):
+    _fields_ = [("kind", C.c_int), ("net", C.c_void_p), ("c", C.c_double * 3), ("r", C.c_double),
+                ("R", C.c_double), ("time", C.c_double)]
+
+
+class _TraceParams(C.Structure):
+    _fields_ = [("n_levels", C.c_int), ("levels", C.POINTER(_SDF)), ("delta", C.POINTER(C.c_double)),
+                ("cap", C.POINTER(C.c_int)), ("scale", C.POINTER(C.c_double)), ("eps", C.c_double),
+                ("box_lo", C.c_double), ("box_hi", C.c_double), ("final_mode", C.c_int)]
+
+
+class _RayResult(C.Structure):
+    _fields_ = [("hit", C.c_int), ("iters", C.c_int), ("p", C.c_double * 3), ("tau", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(str(build()))
+        vp, dp, fp = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_float)
+        L.oracle_net_from_bytes.restype = vp
+        L.oracle_net_from_bytes.argtypes = [C.c_char_p, C.c_size_t]
+        L.oracle_net_free.argtypes = [vp]
+        L.oracle_net_shape.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.oracle_net_round_hidden_bf16.argtypes = [vp]
+        L.oracle_net_eval.restype = C.c_double
+        L.oracle_net_eval.argtypes = [vp, dp]
+        L.oracle_net_grad.argtypes = [vp, dp, dp]
+        L.oracle_lipschitz.restype = C.c_double
+        L.oracle_lipschitz.argtypes = [vp]
+        L.oracle_sdf_value.restype = C.c_double
+        L.oracle_sdf_value.argtypes = [C.POINTER(_SDF), dp]
+        L.oracle_trace_ray.argtypes = [C.POINTER(_TraceParams), dp, dp, C.POINTER(_RayResult), dp,
+                                       C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]
+        L.oracle_trace_batch.argtypes = [C.POINTER(_TraceParams), fp, fp, C.c_int64, C.POINTER(C.c_int64),
+                                         C.c_int64, fp, dp, fp, C.POINTER(C.c_uint8), C.POINTER(C.c_int32),
+                                         C.c_int]
+        L.oracle_first_root.restype = C.c_int
+        L.oracle_first_root.argtypes = [C.POINTER(_SDF), dp, dp, C.c_double, C.c_double, C.c_double,
+                                        C.c_double, dp]
+        L.oracle_grad_batch.argtypes = [vp, dp, C.c_int64, C.c_double, dp, dp, C.c_int]
+        L.oracle_normal_map.argtypes = [vp, dp, C.POINTER(C.c_uint8), C.c_int64, C.c_double, dp, C.c_int]
+        L.oracle_thresholds_prop1.argtypes = [dp, C.c_int, dp]
+        L.oracle_thresholds_prop2.argtypes = [dp, C.c_int, dp]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _fp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+class Net:
+    """An SDFN network loaded by the oracle (folded, float64)."""
+
+    def __init__(self, data: bytes, round_hidden_bf16: bool = False):
+        self._h = lib().oracle_net_from_bytes(data, len(data))
+        if not self._h:
+            raise ValueError("oracle could not parse the SDFN image")
+        if round_hidden_bf16:
+            lib().oracle_net_round_hidden_bf16(self._h)
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        lib().oracle_net_shape(self._h, C.byref(a), C.byref(b), C.byref(c))
+        self.in_dim, self.width, self.n_hidden = a.value, b.value, c.value
+
+    @classmethod
+    def from_file(cls, path, **kw):
+        return cls(Path(path).read_bytes(), **kw)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().oracle_net_free(self._h)
+            self._h = None
+
+    def eval(self, p) -> float:
+        q = np.zeros(4)
+        q[:len(p)] = p
+        return lib().oracle_net_eval(self._h, _dp(q))
+
+    def grad(self, p) -> np.ndarray:
+        q = np.zeros(4)
+        q[:len(p)] = p
+        g = np.zeros(4)
+        lib().oracle_net_grad(self._h, _dp(q), _dp(g))
+        return g[:self.in_dim].copy()
+
+    def lipschitz(self) -> float:
+        return lib().oracle_lipschitz(self._h)
+
+    def grad_batch(self, pts, time: float = 0.0, with_value: bool = False, threads: int | None = None):
+        """Alg. 2 at SoA points (3, n) -> gradients (3, n) float64 (and values)."""
+        pts = np.ascontiguousarray(pts, np.float64)
+        n = pts.shape[1]
+        g = np.zeros((3, n))
+        v = np.zeros(n) if with_value else None
+        lib().oracle_grad_batch(self._h, _dp(pts), n, time, _dp(g), _dp(v) if with_value else None,
+                                threads or default_threads())
+        return (g, v) if with_value else g
+
+    def normal_map(self, pts, mask=None, time: float = 0.0, threads: int | None = None) -> np.ndarray:
+        pts = np.ascontiguousarray(pts, np.float64)
+        n = pts.shape[1]
+        out = np.zeros((3, n))
+        m = None if mask is None else np.ascontiguousarray(mask, np.uint8)
+        lib().oracle_normal_map(self._h, _dp(pts), None if m is None else m.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                n, time, _dp(out), threads or default_threads())
+        return out
+
+
+class SDF:
+    """One level of a traced sequence: a network or an analytic shape."""
+
+    def __init__(self, kind, net: Net | None = None, centre=(0, 0, 0), r=0.0, R=0.0, time=0.0):
+        self.net = net  # keeps the network alive
+        self.s = _SDF(kind, net._h if net is not None else None, (C.c_double * 3)(*centre), r, R, time)
+
+    @classmethod
+    def of_net(cls, net: Net, time: float = 0.0):
+        return cls(SDF_KIND_NET, net=net, time=time)
+
+    @classmethod
+    def sphere(cls, centre, r):
+        return cls(SDF_KIND_SPHERE, centre=centre, r=r)
+
+    @classmethod
+    def torus(cls, centre, R, r):
+        return cls(SDF_KIND_TORUS, centre=centre, R=R, r=r)
+
+    def value(self, p) -> float:
+        q = np.ascontiguousarray(p, np.float64)
+        return lib().oracle_sdf_value(C.byref(self.s), _dp(q))
+
+
+class TraceParams:
+    """Alg. 1 parameters for a nested sequence f_1 |> ... |> f_m."""
+
+    def __init__(self, levels, delta, caps, scales, eps, box=(-1.0, 1.0), final_mode=0):
+        m = len(levels)
+        self.levels = list(levels)
+        self._lv = (_SDF * m)(*[lv.s for lv in levels])
+        self._delta = np.ascontiguousarray(np.broadcast_to(np.asarray(delta, np.float64), (m,)))
+        self._cap = (C.c_int * m)(*[int(c) for c in caps])
+        self._scale = np.ascontiguousarray(np.broadcast_to(np.asarray(scales, np.float64), (m,)))
+        self.p = _TraceParams(m, self._lv, _dp(self._delta), self._cap, _dp(self._scale), float(eps),
+                              float(box[0]), float(box[1]), int(final_mode))
+
+    def trace_ray(self, o, v, traj_cap: int = 0):
+        o = np.ascontiguousarray(o, np.float64)
+        v = np.ascontiguousarray(v, np.float64)
+        r = _RayResult()
+        if traj_cap:
+            traj = np.zeros((traj_cap, 3))
+            lvl = (C.c_int * traj_cap)()
+            tl = C.c_int()
+            lib().oracle_trace_ray(C.byref(self.p), _dp(o), _dp(v), C.byref(r), _dp(traj), lvl, traj_cap,
+                                   C.byref(tl))
+            return r, traj[:tl.value].copy(), np.array(lvl[:tl.value])
+        lib().oracle_trace_ray(C.byref(self.p), _dp(o), _dp(v), C.byref(r), None, None, 0, None)
+        return r
+
+    def trace_batch(self, orig, dirs, idx=None, threads: int | None = None):
+        """Trace SoA float32 rays (3, N); `idx` selects a subset.  Returns a dict."""
+        orig = np.ascontiguousarray(orig, np.float32)
+        dirs = np.ascontiguousarray(dirs, np.float32)
+        N = orig.shape[1]
+        ii = None if idx is None else np.ascontiguousarray(idx, np.int64)
+        n = N if ii is None else ii.size
+        pos = np.zeros((3, n), np.float32)
+        pos64 = np.zeros((3, n))
+        tau = np.zeros(n, np.float32)
+        hit = np.zeros(n, np.uint8)
+        iters = np.zeros(n, np.int32)
+        lib().oracle_trace_batch(C.byref(self.p), _fp(orig), _fp(dirs), N,
+                                 None if ii is None else ii.ctypes.data_as(C.POINTER(C.c_int64)), n,
+                                 _fp(pos), _dp(pos64), _fp(tau), hit.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                 iters.ctypes.data_as(C.POINTER(C.c_int32)), threads or default_threads())
+        return {"pos": pos64, "tau": tau, "hit": hit, "iters": iters}
+
+
+def first_root(sdf: SDF, o, v, t0, t1, h=1e-4, tol=1e-13):
+    o = np.ascontiguousarray(o, np.float64)
+    v = np.ascontiguousarray(v, np.float64)
+    t = C.c_double()
+    ok = lib().oracle_first_root(C.byref(sdf.s), _dp(o), _dp(v), t0, t1, h, tol, C.byref(t))
+    return t.value if ok else None
+
+
+def thresholds_prop1(eps):
+    e = np.ascontiguousarray(eps, np.float64)
+    d = np.zeros_like(e)
+    lib().oracle_thresholds_prop1(_dp(e), e.size, _dp(d))
+    return d
+
+
+def thresholds_prop2(eps):
+    e = np.ascontiguousarray(eps, np.float64)
+    d = np.zeros_like(e)
+    lib().oracle_thresholds_prop2(_dp(e), e.size, _dp(d))
+    return d

@@ -1,0 +1,405 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Nothing here compares the oracle with itself: each check uses a closed form,
+an independent library routine (LAPACK SVD, torch autograd, numpy roots),
+brute force, or a property the paper states (Props. 1-2, the Lipschitz step).
+"""
+import json
+import math
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2201_09147_gb300 import inputs
+
+GOLDEN = Path(__file__).resolve().parent / "golden"
+
+
+def folded_arrays(net: inputs.SineNet):
+    Ws, bs = [], []
+    for i, (w, b) in enumerate(zip(net.weights[:-1], net.biases[:-1])):
+        s = 1.0 if net.folded else (net.omega0 if i == 0 else net.omega)
+        Ws.append(s * w.astype(np.float64))
+        bs.append(s * b.astype(np.float64))
+    return Ws, bs, net.weights[-1][0].astype(np.float64), float(net.biases[-1][0])
+
+
+# ---------------------------------------------------------------------------
+# P1: the (w, k) reading reproduces the paper's memory column
+# ---------------------------------------------------------------------------
+
+def test_param_counts_match_paper_memory_column():
+    rows = json.loads((GOLDEN / "mem_column.json").read_text())["rows"]
+    for row in rows:
+        kib = sum(inputs.param_count(3, w, k) for w, k in row["nets"]) * 4 / 1024
+        assert abs(kib - row["mem_kb"]) <= row["tol_kb"], (row, kib)
+
+
+def test_netfile_roundtrip_and_size():
+    net = inputs.siren_init(0, 64, 1)
+    b = inputs.net_to_bytes(net)
+    assert len(b) == 32 + 4 * 4481
+    back = inputs.net_from_bytes(b)
+    for w0, w1 in zip(net.weights, back.weights):
+        assert np.array_equal(w0.astype(np.float32), w1)
+
+
+# ---------------------------------------------------------------------------
+# P2: network value and gradient in closed form
+# ---------------------------------------------------------------------------
+
+def single_sine_layer_net(seed, width):
+    """f(p) = sum_k c_k sin(w_k . p + b_k) + b: a (width, 0) network, omega = 1."""
+    return inputs.random_plain_net(seed, width, 0, scale=1.5)
+
+
+def test_single_layer_value_and_gradient_closed_form():
+    net = single_sine_layer_net(21, 16)
+    on = oracle.Net(inputs.net_to_bytes(net))
+    W = net.weights[0].astype(np.float64)
+    b = net.biases[0].astype(np.float64)
+    c = net.weights[1][0].astype(np.float64)
+    b_out = float(net.biases[1][0])
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        p = rng.uniform(-1, 1, 3)
+        a = W @ p + b
+        assert abs(on.eval(p) - (c @ np.sin(a) + b_out)) <= 1e-13
+        g_ref = (c * np.cos(a)) @ W
+        assert np.max(np.abs(on.grad(p) - g_ref)) <= 1e-13
+
+
+def test_zero_hidden_weights_reduce_to_bias_chain():
+    net = inputs.random_plain_net(22, 8, 2, scale=0.9)
+    for i in (1, 2):
+        net.weights[i][:] = 0.0
+    on = oracle.Net(inputs.net_to_bytes(net))
+    b2, b1 = net.biases[2].astype(np.float64), net.biases[1].astype(np.float64)
+    expect = net.weights[3][0].astype(np.float64) @ np.sin(b2) + float(net.biases[3][0])
+    for p in ([0.1, -0.2, 0.3], [0.9, 0.9, -0.9]):
+        assert abs(on.eval(np.array(p)) - expect) <= 1e-14
+        assert np.all(on.grad(np.array(p)) == 0.0)
+    del b1
+
+
+def test_frequency_folding_matches_unfolded_definition():
+    """Layer 0 scaled by omega0, hidden layers by omega, output linear (SIREN, Sec. 2)."""
+    net = inputs.siren_init(4, 64, 2, omega0=30.0, omega=20.0)
+    on = oracle.Net(inputs.net_to_bytes(net))
+    W = [w.astype(np.float64) for w in net.weights]
+    b = [x.astype(np.float64) for x in net.biases]
+    p = np.array([0.2, -0.4, 0.1])
+    x = np.sin(30.0 * (W[0] @ p + b[0]))
+    x = np.sin(20.0 * (W[1] @ x + b[1]))
+    x = np.sin(20.0 * (W[2] @ x + b[2]))
+    f = W[3][0] @ x + b[3][0]
+    assert abs(on.eval(p) - f) <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# P3: the analytic gradient (Alg. 2) against independent differentiation
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(64, 1), (64, 3), (128, 2)])
+def test_gradient_matches_torch_autograd(shape):
+    torch = pytest.importorskip("torch")
+    net = inputs.siren_init(8, *shape)
+    on = oracle.Net(inputs.net_to_bytes(net))
+    Ws, bs, wo, bo = folded_arrays(net)
+    Wt = [torch.tensor(w) for w in Ws]
+    bt = [torch.tensor(x) for x in bs]
+    rng = np.random.default_rng(1)
+    for _ in range(10):
+        p = rng.uniform(-1, 1, 3)
+        x = torch.tensor(p, requires_grad=True)
+        h = x
+        for w, b in zip(Wt, bt):
+            h = torch.sin(w @ h + b)
+        f = torch.tensor(wo) @ h + bo
+        (g,) = torch.autograd.grad(f, x)
+        ref = g.numpy()
+        assert abs(on.eval(p) - f.item()) <= 1e-12 * max(1.0, abs(f.item()))
+        assert np.max(np.abs(on.grad(p) - ref)) <= 1e-10 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("shape", [(64, 1), (256, 3)])
+def test_gradient_matches_central_differences(shape):
+    net = inputs.siren_init(9, *shape)
+    on = oracle.Net(inputs.net_to_bytes(net))
+    h = 1e-6
+    rng = np.random.default_rng(2)
+    for _ in range(4):
+        p = rng.uniform(-1, 1, 3)
+        g = on.grad(p)
+        fd = np.array([(on.eval(p + h * e) - on.eval(p - h * e)) / (2 * h) for e in np.eye(3)])
+        assert np.linalg.norm(g - fd) <= 1e-5 * np.linalg.norm(g)
+
+
+def test_gradient_batch_equals_single_point():
+    net = inputs.siren_init(10, 64, 2)
+    on = oracle.Net(inputs.net_to_bytes(net))
+    pts = inputs.random_points(3, 37)
+    g, v = on.grad_batch(pts, with_value=True, threads=3)
+    for i in (0, 17, 36):
+        assert np.array_equal(g[:, i], on.grad(pts[:, i].astype(np.float64)))
+        assert v[i] == on.eval(pts[:, i].astype(np.float64))
+
+
+def test_hadamard_identity_of_sec_5_1():
+    """(W (.) cos[a|...|a]) G = (W G) (.) cos(a), the identity behind Alg. 2."""
+    rng = np.random.default_rng(3)
+    W = rng.normal(size=(7, 5))
+    a = rng.normal(size=7)
+    G = rng.normal(size=(5, 3))
+    lhs = (W * np.cos(a)[:, None]) @ G
+    rhs = (W @ G) * np.cos(a)[:, None]
+    assert np.allclose(lhs, rhs, atol=1e-14)
+
+
+def test_4d_network_time_input():
+    net = inputs.siren_init(12, 64, 1, in_dim=4)
+    on = oracle.Net(inputs.net_to_bytes(net))
+    sdf = oracle.SDF.of_net(on, time=0.25)
+    p = np.array([0.1, 0.2, -0.3])
+    assert sdf.value(p) == on.eval(np.array([0.1, 0.2, -0.3, 0.25]))
+    g = on.grad_batch(p[:, None], time=0.25)[:, 0]
+    assert np.allclose(g, on.grad(np.array([0.1, 0.2, -0.3, 0.25]))[:3], rtol=0, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# P4: Alg. 1 on exact SDFs
+# ---------------------------------------------------------------------------
+
+def ray_sphere(o, v, c, r):
+    oc = o - c
+    b = oc @ v
+    disc = b * b - (oc @ oc - r * r)
+    if disc < 0:
+        return None
+    t = -b - math.sqrt(disc)
+    return t if t >= 0 else None
+
+
+def test_sphere_hit_matches_quadratic_root():
+    c, r = np.array([0.1, -0.05, 0.0]), 0.5
+    tp = oracle.TraceParams([oracle.SDF.sphere(c, r)], [0.0], [200], [1.0], 1e-6)
+    o_all, v_all = inputs.random_rays(5, 400)
+    n_hit = 0
+    for i in range(o_all.shape[1]):
+        o = o_all[:, i].astype(np.float64)
+        v = v_all[:, i].astype(np.float64)
+        v /= np.linalg.norm(v)
+        t_ref = ray_sphere(o, v, c, r)
+        res = tp.trace_ray(o, v)
+        if t_ref is None:
+            assert res.hit == 0
+            continue
+        cosang = abs((o + t_ref * v - c) @ v) / r
+        if cosang < 0.2:
+            continue  # grazing: convergence along the ray is slow
+        n_hit += 1
+        assert res.hit == 1
+        assert abs(res.tau - t_ref) <= 1e-6 / cosang + 1e-12
+        assert np.allclose(res.p, o + res.tau * v, atol=1e-12)
+    assert n_hit > 100
+
+
+def ray_torus_roots(o, v, R, r):
+    """Real roots t of |(o + t v) - torus| = 0 (torus about z), via the quartic."""
+    ox, oy, oz = o
+    vx, vy, vz = v
+    # (|p|^2 + R^2 - r^2)^2 = 4 R^2 (x^2 + y^2)
+    a2 = vx * vx + vy * vy + vz * vz
+    a1 = 2 * (ox * vx + oy * vy + oz * vz)
+    a0 = ox * ox + oy * oy + oz * oz + R * R - r * r
+    q = np.polymul([a2, a1, a0], [a2, a1, a0])
+    q = np.polysub(q, 4 * R * R * np.array([vx * vx + vy * vy, 2 * (ox * vx + oy * vy), ox * ox + oy * oy]))
+    roots = np.roots(q)
+    return sorted(x.real for x in roots if abs(x.imag) < 1e-9 and x.real >= 0)
+
+
+def test_torus_hit_matches_quartic_and_dense_march():
+    R, r = 0.5, 0.2
+    tor = oracle.SDF.torus((0, 0, 0), R, r)
+    tp = oracle.TraceParams([tor], [0.0], [400], [1.0], 1e-7)
+    o_all, v_all = inputs.random_rays(6, 300)
+    checked = 0
+    for i in range(o_all.shape[1]):
+        o = o_all[:, i].astype(np.float64)
+        v = v_all[:, i].astype(np.float64)
+        v /= np.linalg.norm(v)
+        roots = ray_torus_roots(o, v, R, r)
+        res = tp.trace_ray(o, v)
+        if not roots:
+            assert res.hit == 0
+            continue
+        t_ref = roots[0]
+        t_dm = oracle.first_root(tor, o, v, 0.0, 6.0, h=1e-4, tol=1e-13)
+        p = o + t_ref * v
+        q = np.array([p[0], p[1]]) * (1 - R / math.hypot(p[0], p[1]))
+        nrm = np.array([q[0], q[1], p[2]]) / r
+        cosang = abs(nrm @ v)
+        if cosang < 0.3:
+            continue
+        checked += 1
+        assert t_dm is not None and abs(t_dm - t_ref) <= 1e-9
+        assert res.hit == 1
+        assert abs(res.tau - t_ref) <= 1e-7 / cosang + 1e-10
+    assert checked > 50
+
+
+def test_nested_sphere_shells_equal_single_level():
+    """f_1 = sphere of radius r + delta_1 nests the sphere f_2 of radius r (Eq. 1)."""
+    c, r, d1 = np.zeros(3), 0.45, 0.03
+    f1 = oracle.SDF.sphere(c, r + d1)
+    f2 = oracle.SDF.sphere(c, r)
+    two = oracle.TraceParams([f1, f2], [d1, 0.0], [100, 100], [1.0, 1.0], 1e-8)
+    one = oracle.TraceParams([f2], [0.0], [200], [1.0], 1e-8)
+    o_all, v_all = inputs.random_rays(7, 300)
+    for i in range(o_all.shape[1]):
+        o = o_all[:, i].astype(np.float64)
+        v = v_all[:, i].astype(np.float64)
+        v /= np.linalg.norm(v)
+        a, b = two.trace_ray(o, v), one.trace_ray(o, v)
+        t_ref = ray_sphere(o, v, c, r)
+        if t_ref is None:
+            # the coarse shell may be hit while the fine sphere is missed
+            assert b.hit == 0
+            continue
+        cosang = abs((o + t_ref * v - c) @ v) / r
+        if cosang < 0.2:
+            continue
+        assert a.hit == 1 and b.hit == 1
+        assert abs(a.tau - t_ref) <= 1e-8 / cosang + 1e-12
+        assert abs(a.tau - b.tau) <= 2e-8 / cosang + 1e-12
+
+
+def test_alg1_steps_before_testing():
+    """Alg. 1 applies p = p + t v before re-testing t: one step lands exactly on a plane SDF."""
+    # a sphere of huge radius is a plane to within 1e-12 near the ray
+    c = np.array([0.0, 0.0, -1e6])
+    f = oracle.SDF.sphere(c, 1e6 + 0.2)  # surface near z = 0.2
+    tp = oracle.TraceParams([f], [0.0], [10], [1.0], 1e-9, box=(-1, 1))
+    res, traj, _ = tp.trace_ray(np.array([0.0, 0.0, 2.0]), np.array([0.0, 0.0, -1.0]), traj_cap=10)
+    assert res.hit == 1
+    assert len(traj) == 2  # one step to the surface, one more to measure t <= eps
+    assert abs(res.p[2] - 0.2) <= 1e-9
+
+
+# ---------------------------------------------------------------------------
+# P5/P6: the Lipschitz step never crosses the surface; brute force first hit
+# ---------------------------------------------------------------------------
+
+def test_lipschitz_bound_matches_lapack():
+    from paper_2201_09147_gb300 import workloads
+    net = workloads.random_siren_64x1()
+    on = oracle.Net(inputs.net_to_bytes(net))
+    Ws, _, wo, _ = folded_arrays(net)
+    ref = np.prod([np.linalg.norm(w, 2) for w in Ws]) * np.linalg.norm(wo)
+    assert abs(on.lipschitz() - ref) <= 1e-10 * ref
+
+
+def slab_entry(o, v, lo=-1.0, hi=1.0):
+    with np.errstate(divide="ignore"):
+        t1, t2 = (lo - o) / v, (hi - o) / v
+    return max(0.0, float(np.max(np.minimum(t1, t2))))
+
+
+def test_lipschitz_steps_never_cross_and_find_first_root():
+    """With s = 1/L no step crosses the zero set (|f(p + t v / L) - f(p)| <= |t|)."""
+    from paper_2201_09147_gb300 import workloads
+    wl = workloads.get("random_siren_64x1", 20, 20)
+    on = oracle.Net(inputs.net_to_bytes(wl.levels[0]))
+    L = on.lipschitz()
+    sdf = oracle.SDF.of_net(on)
+    tp = oracle.TraceParams([sdf], [0.0], [600], [1.0 / L], 1e-3)
+    orig, dirs = wl.rays()
+    n_hits = 0
+    for i in range(orig.shape[1]):
+        o = orig[:, i].astype(np.float64)
+        v = dirs[:, i].astype(np.float64)
+        res, traj, _ = tp.trace_ray(o, v, traj_cap=600)
+        if len(traj) < 2:
+            continue
+        vals = np.array([on.eval(q) for q in traj])
+        # every iterate stays on the side of the zero set where the ray started
+        assert np.all(vals * vals[0] >= 0.0), i
+        if res.hit and vals[0] > 0:
+            n_hits += 1
+            assert abs(on.eval(res.p)) <= 1e-3 + 1e-9
+            # the first root along the ray lies at or beyond the end point
+            t_end = float((res.p - o) @ v)
+            t_in = slab_entry(o, v)
+            t_root = oracle.first_root(sdf, o, v, t_in, t_end + 1e-3, h=1e-4, tol=1e-12)
+            assert t_root is None or t_root >= t_end - 1e-9
+    assert n_hits > 3
+
+
+def test_box_exit_means_no_root_on_the_path():
+    """A Lipschitz-stepped ray that leaves the box passed no root (dense march over the path)."""
+    from paper_2201_09147_gb300 import workloads
+    wl = workloads.get("random_siren_64x1", 16, 16)
+    on = oracle.Net(inputs.net_to_bytes(wl.levels[0]))
+    sdf = oracle.SDF.of_net(on)
+    L = on.lipschitz()
+    tp = oracle.TraceParams([sdf], [0.0], [400], [1.0 / L], 1e-3)
+    orig, dirs = wl.rays()
+    exits = 0
+    for i in range(orig.shape[1]):
+        o = orig[:, i].astype(np.float64)
+        v = dirs[:, i].astype(np.float64)
+        res = tp.trace_ray(o, v)
+        if res.hit or res.iters == 0:
+            continue
+        t_in = slab_entry(o, v)
+        if on.eval(o + t_in * v) <= 0:
+            continue
+        exits += 1
+        t_root = oracle.first_root(sdf, o, v, t_in, res.tau - 2e-3, h=2e-4, tol=1e-9)
+        assert t_root is None
+    assert exits > 20
+
+
+# ---------------------------------------------------------------------------
+# P7: threshold recurrences of Props. 1 and 2 imply the nesting of Eq. 1
+# ---------------------------------------------------------------------------
+
+def _nested(f_coarse, d_coarse, f_fine, d_fine):
+    inner = np.abs(f_fine) <= d_fine
+    return np.all(np.abs(f_coarse[inner]) <= d_coarse)
+
+
+def test_prop2_thresholds_nest_approximations_of_one_surface():
+    rng = np.random.default_rng(4)
+    P = rng.uniform(-1, 1, (200000, 3))
+    f = np.linalg.norm(P, axis=1) - 0.5
+    eps = np.array([0.05, 0.02, 0.008])
+    fs = [f + e * np.sin(7 * k + 11 * P[:, 0]) * np.cos(5 * P[:, 1] - k) * 0.999 for k, e in enumerate(eps)]
+    delta = oracle.thresholds_prop2(eps)
+    assert np.all(np.diff(delta) < 0)
+    for j in range(len(eps) - 1):
+        assert _nested(fs[j], delta[j], fs[j + 1], delta[j + 1])
+    # shrinking a threshold below the recurrence breaks the nesting for adversarial errors
+    adv = [f + eps[0] * 0.999, f - eps[1] * 0.999]
+    d2 = oracle.thresholds_prop2(eps[:2])
+    assert _nested(adv[0], d2[0], adv[1], d2[1])
+    assert not _nested(adv[0], d2[0] * 0.98, adv[1], d2[1])
+
+
+def test_prop1_thresholds_nest_successive_differences():
+    rng = np.random.default_rng(5)
+    P = rng.uniform(-1, 1, (200000, 3))
+    base = np.linalg.norm(P - 0.1, axis=1) - 0.4
+    eps = np.array([0.0, 0.03, 0.01, 0.004])  # eps[0] unused by Prop. 1
+    fs = [base]
+    for k in range(1, len(eps)):
+        fs.append(fs[-1] + eps[k] * 0.999 * np.sin(3 * k + 9 * P[:, 2]))
+    delta = oracle.thresholds_prop1(eps)
+    for j in range(len(eps) - 1):
+        assert _nested(fs[j], delta[j], fs[j + 1], delta[j + 1])
+    adv = [base, base + eps[1] * 0.999]
+    d2 = oracle.thresholds_prop1(eps[:2])
+    assert _nested(adv[0], d2[0], adv[1], d2[1])
+    assert not _nested(adv[0], d2[0] * 0.97, adv[1], d2[1])
