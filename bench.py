@@ -1,0 +1,424 @@
+"""Benchmark: Mrays/s to hit + normal at 1920 x 1080.
+
+One step renders one frame of the ``normal_map_1080p`` workload through the
+C ABI: multiscale sphere tracing of the coarse (64,1) network until its
+delta-shell (Alg. 1, BF16 tensor-core hidden layer) followed by neural normal
+mapping of the fine (256,3) network at every hit (Sec. 5, Alg. 2 on the
+tensor cores).  Inputs are resident in HBM; the L2 is flushed between timed
+steps.  Also reported: the same frame end to end from host buffers
+(sdf_render_host), the plain FP32 (256,3) single-network tracer, the error
+against the FP64 oracle on a sample of rays, and the oracle's own speed on the
+host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "Mrays/s to hit+normal at 1080p (multiscale BF16 vs plain FP32, same GPU, stated error)"
+UNIT = "Mrays/s"
+WORKLOAD = "normal_map_1080p"
+ORACLE_ROW_STRIDE = 32  # the CPU-baseline sample: every 32nd image row
+
+
+def peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(wl, rows):
+    """Runs the FP64 oracle on the given image rows: trace + normal map at its hits."""
+    import oracle
+    orig, dirs = wl.rays(rows=rows)
+    t0 = time.perf_counter()
+    onets = [oracle.Net(b) for b in wl.level_bytes()]
+    tp = oracle.TraceParams([oracle.SDF.of_net(n) for n in onets], wl.delta, wl.caps, wl.step_scale, wl.eps,
+                            final_mode=wl.final_mode)
+    res = tp.trace_batch(orig, dirs)
+    fine = oracle.Net(wl.fine_bytes())
+    nrm = fine.normal_map(res["pos"], res["hit"])
+    dt = time.perf_counter() - t0
+    return res, nrm, dt, orig.shape[1]
+
+
+def reference_arm(args):
+    """The FP64 oracle as the reference implementation, timed on the host cores."""
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2201_09147_gb300 import workloads
+    oracle.build()
+    wl = workloads.get(WORKLOAD)
+    rows = np.arange(0, wl.height, ORACLE_ROW_STRIDE * 2)
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_sample(wl, rows[:2])
+    times, n = [], 0
+    for _ in range(args.steps):
+        _, _, dt, n = oracle_sample(wl, rows)
+        times.append(dt)
+    value = n * len(times) / sum(times) / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rays_per_frame": wl.n_rays, "sample_rows_stride": ORACLE_ROW_STRIDE * 2},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
+                             "sample": f"{n} rays per step (every {ORACLE_ROW_STRIDE * 2}th row of the 1080p frame)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def source_sha(path: Path) -> str:
+    return hashlib.sha256(path.read_bytes()).hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="lean run for ncu: the timed steps only (no L2 flush buffer, no comparison legs)")
+    args = ap.parse_args()
+    if args.profile:
+        args.no_cpu_baseline = args.no_plain = True
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2201_09147_gb300 import build, sdfnn, workloads
+    build.build()
+    pk = peaks()
+
+    wl = workloads.get(WORKLOAD)
+    n = wl.n_rays
+    orig_h, dirs_h = wl.rays()
+    orig = torch.from_numpy(orig_h).cuda()
+    dirs = torch.from_numpy(dirs_h).cuda()
+    coarse = [sdfnn.Net(b, sdfnn.SDF_BF16, local) for b in wl.level_bytes()]
+    fine = sdfnn.Net(wl.fine_bytes(), sdfnn.SDF_BF16, local)
+    pos = torch.empty((3, n), device="cuda")
+    tt = torch.empty(n, device="cuda")
+    hit = torch.empty(n, dtype=torch.uint8, device="cuda")
+    nrm = torch.empty((3, n), device="cuda")
+    # writing 512 MB between timed steps evicts the 129 MB L2
+    flush = torch.empty((1 if args.profile else 512 * 1024 * 1024 // 4), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        sdfnn.trace_multiscale(coarse, wl.delta, wl.caps, wl.eps, orig, dirs, step_scale=wl.step_scale,
+                               final_mode=wl.final_mode, out_pos=pos, out_t=tt, out_hit=hit, want_iters=False)
+        ev_mid = torch.cuda.Event(enable_timing=True)
+        ev_mid.record(stream)
+        sdfnn.normal_map(fine, pos, hit, out=nrm)
+        return ev_mid
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    sdfnn.sync_status()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    evs = []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        em = step()
+        e1.record(stream)
+        evs.append((e0, em, e1))
+        flush.zero_()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    sdfnn.sync_status()
+    step_ms = [a.elapsed_time(c) for a, _, c in evs]
+    trace_ms = [a.elapsed_time(b) for a, b, _ in evs]
+    nmap_ms = [b.elapsed_time(c) for _, b, c in evs]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * n * args.steps / (total_ms / 1e3) / 1e6
+    n_hit = int(hit.sum().item())
+
+    # roofline of the dominant kernel (algorithmic work / event-timed duration)
+    W, KH = fine.width, fine.n_hidden
+    normal_flops_per_point = 4 * KH * 2 * W * W          # forward + 3 tangents through the hidden layers
+    nm_ms = statistics.mean(nmap_ms)
+    tr_ms = statistics.mean(trace_ms)
+    # iteration histogram for the trace's algorithmic work (one extra untimed run)
+    _, _, _, iters = sdfnn.trace_multiscale(coarse, wl.delta, wl.caps, wl.eps, orig, dirs,
+                                            step_scale=wl.step_scale, final_mode=wl.final_mode)
+    torch.cuda.synchronize()
+    total_evals = int(iters.to(torch.int64).sum().item())
+    cw, ck = coarse[0].width, coarse[0].n_hidden
+    sines_per_eval = (ck + 1) * cw
+    traffic_path = ROOT / "profiles" / "traffic.json"
+    traffic = None
+    if traffic_path.exists():
+        tj = json.loads(traffic_path.read_text())
+        if tj.get("source_sha") == source_sha(ROOT / "paper_2201_09147_gb300" / "csrc" / "tc.cu"):
+            traffic = tj.get("bytes_per_launch")
+    if nm_ms >= tr_ms:
+        achieved = n_hit * normal_flops_per_point / (nm_ms / 1e3) / 1e12
+        peak = pk["bf16_tflops_sustained"]
+        roofline = {"kernel": "grad_tc_kernel<256> (neural normal mapping, (256,3))", "bound": "tensor",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": traffic, "peak_source": f"{pk['source']} bf16 sustained",
+                    "work": f"{n_hit} points x {normal_flops_per_point} hidden-layer MMA flops"}
+    else:
+        # sine-bound: one MUFU sine per hidden unit per evaluation
+        sm_mhz = clk.get("sm_mhz") or 1900.0
+        peak_gsin = 152 * 16 * sm_mhz * 1e6 / 1e9
+        achieved = total_evals * sines_per_eval / (tr_ms / 1e3) / 1e9
+        roofline = {"kernel": "trace_level_tc_kernel<64> (coarse (64,1) trace)", "bound": "alu", "achieved": achieved,
+                    "peak": peak_gsin, "unit": "Gsin/s", "frac": achieved / peak_gsin, "traffic": traffic,
+                    "peak_source": "152 SMs x 16 MUFU/clk x median SM clock",
+                    "work": f"{total_evals} evaluations x {sines_per_eval} sines"}
+
+    # end to end from pinned host buffers through sdf_render_host
+    e2e_value = None
+    if not args.profile:
+        ho = torch.from_numpy(orig_h).pin_memory()
+        hd = torch.from_numpy(dirs_h).pin_memory()
+        hp = torch.empty((3, n)).pin_memory()
+        hh = torch.empty(n, dtype=torch.uint8).pin_memory()
+        hn = torch.empty((3, n)).pin_memory()
+
+        def e2e_step():
+            sdfnn.render_host(coarse, wl.delta, wl.caps, wl.eps, fine, ho, hd, hp, hh, hn,
+                              step_scale=wl.step_scale, final_mode=wl.final_mode)
+
+        e2e_step()
+        e2e_times = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step()
+            e2e_times.append(time.perf_counter() - t0)
+        e2e_value = ws * n / statistics.mean(e2e_times) / 1e6
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+              "config": {"workload": WORKLOAD, "rays_per_frame": n, "resolution": [wl.width, wl.height],
+                         "coarse": "(64,1) BF16, final_mode 1, delta_0 0.04, cap 40",
+                         "fine": "(256,3) BF16 normal mapping", "l2": "flushed between steps (512 MB write)",
+                         "parallelism": f"replicas x{ws}"},
+              "clocks": clk, "gpu_launches": 3 * args.steps,
+              "e2e": ({"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 3 * 4 * n,
+                       "d2h_bytes_per_step": (3 + 3) * 4 * n + n} if e2e_value is not None else None),
+              "roofline": roofline,
+              "breakdown_ms": {"trace_coarse": tr_ms, "normal_map_fine": nm_ms, "hits": n_hit,
+                               "mean_coarse_iters": total_evals / n},
+              "wall_s_timed_region": t_wall}
+
+    if not args.no_plain:
+        # plain FP32 single-network (256,3) tracer with its own normals: the comparison path
+        plain = workloads.get("plain_256x3_1080p")
+        pn = [sdfnn.Net(b, sdfnn.SDF_FP32, local) for b in plain.level_bytes()]
+        pf = sdfnn.Net(plain.fine_bytes(), sdfnn.SDF_FP32, local)
+
+        def plain_step():
+            sdfnn.trace_multiscale(pn, plain.delta, plain.caps, plain.eps, orig, dirs, step_scale=plain.step_scale,
+                                   final_mode=plain.final_mode, out_pos=pos, out_t=tt, out_hit=hit, want_iters=False)
+            sdfnn.normal_map(pf, pos, hit, out=nrm)
+
+        plain_step()
+        torch.cuda.synchronize()
+        pt = []
+        for _ in range(2):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plain_step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            pt.append(a.elapsed_time(b))
+        plain_value = n / (statistics.mean(pt) / 1e3) / 1e6
+        # multiscale with FP32 hidden layers: isolates the algorithm from the precision
+        c32 = [sdfnn.Net(b, sdfnn.SDF_FP32, local) for b in wl.level_bytes()]
+        f32 = sdfnn.Net(wl.fine_bytes(), sdfnn.SDF_FP32, local)
+        ft = []
+        for _ in range(3):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sdfnn.trace_multiscale(c32, wl.delta, wl.caps, wl.eps, orig, dirs, step_scale=wl.step_scale,
+                                   final_mode=wl.final_mode, out_pos=pos, out_t=tt, out_hit=hit, want_iters=False)
+            sdfnn.normal_map(f32, pos, hit, out=nrm)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ft.append(a.elapsed_time(b))
+        ms_fp32_value = n / (statistics.mean(ft[1:]) / 1e3) / 1e6
+        # the same frame with FP16 tensor-core operands
+        c16 = [sdfnn.Net(b, sdfnn.SDF_FP16, local) for b in wl.level_bytes()]
+        f16 = sdfnn.Net(wl.fine_bytes(), sdfnn.SDF_FP16, local)
+        ht = []
+        for _ in range(args.warmup + args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sdfnn.trace_multiscale(c16, wl.delta, wl.caps, wl.eps, orig, dirs, step_scale=wl.step_scale,
+                                   final_mode=wl.final_mode, out_pos=pos, out_t=tt, out_hit=hit, want_iters=False)
+            sdfnn.normal_map(f16, pos, hit, out=nrm)
+            b.record(stream)
+            ht.append((a, b))
+        torch.cuda.synchronize()
+        fp16_value = n / (statistics.mean([a.elapsed_time(b) for a, b in ht[args.warmup:]]) / 1e3) / 1e6
+        result["comparisons"] = {"fp16_Mrays_s": fp16_value,
+                                 "plain_fp32_256x3_Mrays_s": plain_value,
+                                 "speedup_vs_plain_fp32": value / ws / plain_value,
+                                 "multiscale_fp32_Mrays_s": ms_fp32_value,
+                                 "speedup_algorithm_only": ms_fp32_value / plain_value,
+                                 "speedup_precision_only_multiscale": value / ws / ms_fp32_value}
+        sdfnn.sync_status()
+
+    if rank == 0 and not args.no_cpu_baseline:
+        # FP64 oracle on a bounded sample of the same frame: speed, and the error of this run
+        rows = np.arange(0, wl.height, ORACLE_ROW_STRIDE)
+        res, onrm, dt, ns = oracle_sample(wl, rows)
+        import oracle
+        result["cpu_baseline"] = {"value": ns / dt / 1e6, "unit": UNIT, "cores": oracle.default_threads(),
+                                  "kind": "oracle",
+                                  "sample": f"{ns} rays: every {ORACLE_ROW_STRIDE}th row of the 1080p frame, "
+                                            f"trace + normal map in FP64"}
+        idx = (rows[:, None] * wl.width + np.arange(wl.width)[None, :]).ravel()
+        fine_oracle = oracle.Net(wl.fine_bytes())
+
+        def error_of(cnets, fnet):
+            sdfnn.trace_multiscale(cnets, wl.delta, wl.caps, wl.eps, orig, dirs, step_scale=wl.step_scale,
+                                   final_mode=wl.final_mode, out_pos=pos, out_t=tt, out_hit=hit, want_iters=False)
+            sdfnn.normal_map(fnet, pos, hit, out=nrm)
+            sdfnn.sync_status()
+            gp = pos.cpu().numpy()[:, idx]
+            gh = hit.cpu().numpy()[idx].astype(bool)
+            gn = nrm.cpu().numpy()[:, idx]
+            oh = res["hit"].astype(bool)
+            both = gh & oh
+            dp = np.linalg.norm(gp[:, both] - res["pos"][:, both], axis=0)
+            ref = fine_oracle.normal_map(gp.astype(np.float64), gh.astype(np.uint8))
+            c = np.clip(np.sum(gn[:, gh] * ref[:, gh], axis=0), -1, 1)
+            ang = np.degrees(np.arccos(c))
+            return {"rays": int(idx.size), "hits": int(gh.sum()), "hit_agreement": float(np.mean(gh == oh)),
+                    "hit_point_p999": float(np.quantile(dp, 0.999)) if dp.size else None,
+                    "hit_point_max": float(dp.max()) if dp.size else None,
+                    "normal_deg_p999": float(np.quantile(ang, 0.999)) if ang.size else None,
+                    "normal_deg_max": float(ang.max()) if ang.size else None}
+
+        result["error_vs_oracle"] = error_of(coarse, fine)
+        if not args.no_plain:
+            result["error_vs_oracle_fp16"] = error_of(c16, f16)
+    if rank == 0:
+        print(json.dumps(result))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,165 @@
+/*
+ * sdfnn.h - C ABI of the GB300 (sm_103a) renderer for nested neural SDFs.
+ *
+ * Implements the rendering hot path of da Silva et al., "Neural Implicit
+ * Mapping via Nested Neighborhoods" (CVPR 2023):
+ *   - multiscale sphere tracing of a nested sequence f_1 |> ... |> f_m (Sec. 4, Alg. 1),
+ *   - analytic gradients of sine MLPs (Sec. 5.1, Eqs. 3-4, Alg. 2),
+ *   - neural normal mapping N(p) = grad f(p) on a coarse surface (Sec. 5).
+ *
+ * Conventions shared by every call:
+ *   - Point and ray arrays are structure-of-arrays float32: element c of item
+ *     i lives at ptr[c * n + i] (c = 0, 1, 2 for x, y, z).
+ *   - Buffers passed to sdf_trace_multiscale, sdf_normals and sdf_normal_map
+ *     are caller-owned DEVICE memory (cudaMalloc / torch CUDA tensors) on the
+ *     device the networks were loaded on.  Host pointers are rejected with
+ *     SDF_ERR_ARG before any kernel runs.  sdf_render_host is the one call
+ *     that takes host memory.
+ *   - Calls are asynchronous on `cuda_stream` (a cudaStream_t; NULL means the
+ *     legacy default stream).  Argument errors are returned immediately.
+ *     Errors a kernel detects on the device (a bounded wait that expired:
+ *     SDF_ERR_TIMEOUT) are latched in a per-device status word and returned
+ *     by sdf_sync_status.
+ *   - n == 0 is valid and launches nothing.
+ *   - Every non-OK return sets a thread-local message (sdf_last_error).
+ *
+ * Network files ("SDFN", little-endian):
+ *   offset 0  char[4] "SDFN"       offset 16 u32 n_hidden k
+ *   offset 4  u32 version = 1      offset 20 f32 omega0 (layer-0 sine frequency)
+ *   offset 8  u32 in_dim (3 or 4)  offset 24 f32 omega  (hidden sine frequency)
+ *   offset 12 u32 width w          offset 28 u32 flags  (bit 0: weights already folded)
+ *   offset 32 f32 W_0[w][in_dim], b_0[w], then k times (W_i[w][w], b_i[w]),
+ *             then W_out[w], b_out: the MLP of Eq. 2 with k + 1 sine layers
+ *             of width w, written (w, k) in Sec. 6.
+ */
+#ifndef SDFNN_H
+#define SDFNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sdf_net *sdf_net_t; /* opaque, owned by the library until sdf_net_free */
+
+enum {
+    SDF_OK = 0,
+    SDF_ERR_ARG = -1,         /* NULL / host pointer, bad size, inconsistent parameters */
+    SDF_ERR_FILE = -2,        /* file cannot be read */
+    SDF_ERR_FORMAT = -3,      /* not a valid SDFN image */
+    SDF_ERR_CUDA = -4,        /* a CUDA runtime call failed */
+    SDF_ERR_NONFINITE = -5,   /* NaN or Inf in the network parameters */
+    SDF_ERR_TIMEOUT = -6,     /* a kernel's bounded wait expired (device status word) */
+    SDF_ERR_UNSUPPORTED = -7  /* shape / precision combination this build does not run */
+};
+
+/* Arithmetic of the hidden w x w layers.  Layer 0, the output layer, the
+ * sine/cosine epilogues, the ray state and the step update are FP32 in all
+ * modes. */
+enum {
+    SDF_FP32 = 0, /* SIMT FP32 contractions (the plain comparison path) */
+    SDF_BF16 = 1, /* tcgen05 tensor-core contractions, bfloat16 operands, FP32 accumulation */
+    SDF_FP8 = 2,  /* reserved: FP8 E4M3 with per-layer scales (returns SDF_ERR_UNSUPPORTED) */
+    SDF_FP16 = 3  /* tcgen05 tensor-core contractions, IEEE half operands, FP32 accumulation:
+                     same tensor rate as SDF_BF16 with 3 more mantissa bits; the sine
+                     activations lie in [-1, 1] and need no wider exponent range */
+};
+
+/* Load a network and prepare it on `device`: fold the sine frequencies into
+ * the weights (layer 0 by omega0, hidden layers by omega), compute the
+ * Lipschitz bound L = prod_i ||W_i||_2 * ||W_out||_2 in FP64 (sin is
+ * 1-Lipschitz, so 1/L is a step that never crosses the zero set), and upload
+ * FP32 parameters plus, for SDF_BF16 / SDF_FP16, the hidden matrices rounded
+ * to bfloat16 / half (nearest even) in the tensor-core operand layout.
+ * Supported shapes: in_dim 3 or 4, width 64, 128 or 256, 1 <= n_hidden <= 4.
+ * Errors: SDF_ERR_ARG (NULL out / bad precision / bad device), SDF_ERR_FILE,
+ * SDF_ERR_FORMAT, SDF_ERR_NONFINITE, SDF_ERR_UNSUPPORTED, SDF_ERR_CUDA.
+ * On error *out is set to NULL and nothing is leaked. */
+int sdf_net_load(const char *path, int precision, int device, sdf_net_t *out);
+int sdf_net_load_mem(const void *bytes, size_t n_bytes, int precision, int device, sdf_net_t *out);
+
+/* Shape and Lipschitz bound of a loaded network (any out pointer may be NULL). */
+int sdf_net_info(sdf_net_t net, int *in_dim, int *width, int *n_hidden, double *lipschitz);
+
+/* Time coordinate fed as the 4th input of 4-D networks by sdf_normals and
+ * sdf_normal_map (Sec. 3.2 families of neural SDFs).  Ignored for 3-D nets. */
+int sdf_net_set_time(sdf_net_t net, float time);
+
+/* Frees the network and its device memory.  NULL is a no-op.  The caller
+ * must not free a network while work that uses it is still in flight. */
+void sdf_net_free(sdf_net_t net);
+
+/* Parameters of Alg. 1 for a nested sequence f_1 |> ... |> f_m. */
+typedef struct {
+    int n_levels;              /* m >= 1 (at most 8) */
+    const sdf_net_t *nets;     /* m networks, same device, same in_dim */
+    const float *delta;        /* m thresholds delta_j (Eq. 1); delta_m is used only when final_mode == 1 */
+    const int *max_iters;      /* m iteration caps (>= 0); the paper fixes iteration counts (Sec. 6) */
+    float eps;                 /* epsilon of Alg. 1 (> 0) */
+    const float *step_scale;   /* m step scales s_j, or NULL for s_j = 1/L_j */
+    float box_min, box_max;    /* rays are clipped to the cube [box_min, box_max]^3 */
+    int final_mode;            /* 0: trace S_m (Alg. 1); 1: stop on the delta_m shell of f_m */
+    float time;                /* 4th input of 4-D networks */
+} sdf_trace_params;
+
+/* Multiscale sphere tracing (Sec. 4, Alg. 1) of n rays.
+ *   orig, dir : device, SoA (3, n) float32; dir must be unit length.
+ *   out_pos   : device, SoA (3, n) float32, end point of each ray.
+ *   out_t     : device, (n) float32, distance travelled from orig to out_pos.
+ *   out_hit   : device, (n) uint8, 1 = hit, 0 = miss.
+ *   out_iters : device, (n) uint16 total steps over all levels, or NULL.
+ * Per ray: start where the ray enters the cube (or at orig if inside; a ray
+ * that misses the cube is a miss with no evaluation); for each level j run
+ *     t = f_j(p) - d_j ;  p += s_j * t * dir
+ * (d_j = delta_j, or 0 on the last level with final_mode 0) while t > eps
+ * and fewer than max_iters[j] steps were taken, the step taken before the
+ * test as in Alg. 1.  A point outside the cube widened by 1e-3 ends the ray
+ * as a miss.  Hit iff the last level ended with t <= eps.
+ * Errors: SDF_ERR_ARG (NULL or host pointers, n < 0, m out of range, eps <= 0,
+ * negative caps, delta_j <= 0 for a level that uses it, mixed devices or
+ * in_dim), SDF_ERR_UNSUPPORTED, SDF_ERR_CUDA. */
+int sdf_trace_multiscale(const sdf_trace_params *params, const float *orig, const float *dir, int64_t n,
+                         float *out_pos, float *out_t, uint8_t *out_hit, uint16_t *out_iters,
+                         void *cuda_stream);
+
+/* Analytic gradient grad f(p) (Sec. 5.1, Eqs. 3-4, Alg. 2) at n points.
+ *   pts      : device, SoA (3, n) float32.
+ *   out_grad : device, SoA (3, n) float32, unnormalised gradient (x, y, z).
+ * Errors: SDF_ERR_ARG, SDF_ERR_CUDA. */
+int sdf_normals(sdf_net_t net, const float *pts, int64_t n, float *out_grad, void *cuda_stream);
+
+/* Neural normal mapping (Sec. 5): N(p) = grad f(p) / |grad f(p)| of the fine
+ * network at points of a coarser surface (end points of a coarse trace, or
+ * mesh vertices).
+ *   pts        : device, SoA (3, n) float32.
+ *   mask       : device, (n) uint8 (0 = skip) or NULL for all points.
+ *   out_normal : device, SoA (3, n) float32; (0, 0, 0) where the mask is 0
+ *                or |grad f| < 1e-12.
+ * Errors: SDF_ERR_ARG, SDF_ERR_CUDA. */
+int sdf_normal_map(sdf_net_t fine, const float *pts, const uint8_t *mask, int64_t n, float *out_normal,
+                   void *cuda_stream);
+
+/* One frame end to end from HOST memory: copies orig/dir to the device,
+ * runs sdf_trace_multiscale and then sdf_normal_map(fine) on the hits, and
+ * copies hit, end point and normal back.  Device buffers are taken from the
+ * stream-ordered allocator.  orig, dir: host (3, n); out_pos, out_normal:
+ * host (3, n); out_hit: host (n).  Returns after the results are in host
+ * memory (the stream is synchronised).
+ * Errors: as sdf_trace_multiscale and sdf_normal_map. */
+int sdf_render_host(const sdf_trace_params *params, sdf_net_t fine, const float *orig, const float *dir,
+                    int64_t n, float *out_pos, uint8_t *out_hit, float *out_normal, void *cuda_stream);
+
+/* Synchronises the stream, then returns and clears the status word of the
+ * current device (SDF_OK, or the first device-side error since the last call). */
+int sdf_sync_status(void *cuda_stream);
+
+/* Thread-local message describing the last non-OK return of this thread. */
+const char *sdf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDFNN_H */

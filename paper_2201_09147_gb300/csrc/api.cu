@@ -1,0 +1,582 @@
+// C-ABI layer of libsdfnn: network loading and preparation, argument
+// validation, and orchestration of the kernels on the caller's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_fp16.h>
+
+#include "../../include/sdfnn.h"
+#include "common.cuh"
+#include "internal.h"
+
+using namespace sdfnn;
+
+struct sdf_net {
+    int device = 0;
+    int precision = SDF_FP32;
+    int in_dim = 3, width = 0, n_hidden = 0;
+    double lipschitz = 0.0;
+    float time = 0.0f;
+    float bout = 0.0f;
+    float* d_f32 = nullptr;       // folded FP32 parameters
+    uint8_t* d_bf16 = nullptr;    // swizzled 16-bit hidden weights (SDF_BF16 / SDF_FP16)
+    size_t off_w0 = 0, off_b0 = 0, off_wt[kMaxHidden] = {}, off_bh[kMaxHidden] = {}, off_wout = 0;
+    uint32_t bf16_layer_bytes = 0;
+    int rows_pad = 0;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(SDF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+struct DeviceInfo {
+    int num_sms = 0;
+    int* d_status = nullptr;
+};
+
+std::mutex g_dev_mutex;
+std::vector<DeviceInfo> g_devices;
+
+// Per-device SM count and status word (allocated once, kept until exit).
+// The caller has already made `dev` current.
+int device_info(int dev, DeviceInfo* out) {
+    std::lock_guard<std::mutex> lock(g_dev_mutex);
+    if (static_cast<int>(g_devices.size()) <= dev) g_devices.resize(dev + 1);
+    DeviceInfo& d = g_devices[dev];
+    if (d.num_sms == 0) {
+        cudaError_t e = cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+        e = cudaMalloc(&d.d_status, sizeof(int));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(status)");
+        e = cudaMemset(d.d_status, 0, sizeof(int));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(status)");
+    }
+    *out = d;
+    return SDF_OK;
+}
+
+// Device memory of `dev` (device or managed allocation) or fails with SDF_ERR_ARG.
+int check_device_ptr(const void* p, int dev, const char* name) {
+    if (p == nullptr) return fail(SDF_ERR_ARG, "%s is NULL", name);
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SDF_ERR_ARG, "%s: not a CUDA pointer (%s)", name, cudaGetErrorString(e));
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(SDF_ERR_ARG, "%s must be device memory", name);
+    if (at.type == cudaMemoryTypeDevice && at.device != dev)
+        return fail(SDF_ERR_ARG, "%s lives on device %d, the network on device %d", name, at.device, dev);
+    return SDF_OK;
+}
+
+uint32_t rd_u32(const uint8_t* p) {
+    return static_cast<uint32_t>(p[0]) | (static_cast<uint32_t>(p[1]) << 8) | (static_cast<uint32_t>(p[2]) << 16) |
+           (static_cast<uint32_t>(p[3]) << 24);
+}
+float rd_f32(const uint8_t* p) {
+    const uint32_t u = rd_u32(p);
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// Largest singular value by power iteration on M^T M in double precision.
+double top_singular_value(const std::vector<double>& M, int rows, int cols) {
+    std::vector<double> x(cols, 1.0), y(rows);
+    double prev = 0.0;
+    for (int it = 0; it < 200000; ++it) {
+        double nx = 0.0;
+        for (double v : x) nx += v * v;
+        nx = std::sqrt(nx);
+        if (nx == 0.0) return 0.0;
+        for (double& v : x) v /= nx;
+        for (int r = 0; r < rows; ++r) {
+            double s = 0.0;
+            const double* row = &M[static_cast<size_t>(r) * cols];
+            for (int c = 0; c < cols; ++c) s += row[c] * x[c];
+            y[r] = s;
+        }
+        double ny = 0.0;
+        for (double v : y) ny += v * v;
+        const double sigma = std::sqrt(ny);
+        std::fill(x.begin(), x.end(), 0.0);
+        for (int r = 0; r < rows; ++r) {
+            const double* row = &M[static_cast<size_t>(r) * cols];
+            for (int c = 0; c < cols; ++c) x[c] += row[c] * y[r];
+        }
+        if (it > 16 && std::fabs(sigma - prev) <= 1e-15 * sigma) return sigma;
+        prev = sigma;
+    }
+    return prev;
+}
+
+uint16_t to_bf16_rne(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return static_cast<uint16_t>(u >> 16);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return static_cast<uint16_t>(u >> 16);
+}
+
+NetView view_of(const sdf_net* n) {
+    NetView v{};
+    v.in_dim = n->in_dim;
+    v.width = n->width;
+    v.n_hidden = n->n_hidden;
+    v.w0 = n->d_f32 + n->off_w0;
+    v.b0 = n->d_f32 + n->off_b0;
+    for (int l = 0; l < n->n_hidden; ++l) {
+        v.wt[l] = n->d_f32 + n->off_wt[l];
+        v.bh[l] = n->d_f32 + n->off_bh[l];
+    }
+    v.wout = n->d_f32 + n->off_wout;
+    v.bout = n->bout;
+    v.wbf = n->d_bf16;
+    v.wbf_lo = n->d_bf16 ? n->d_bf16 + static_cast<size_t>(n->n_hidden) * n->bf16_layer_bytes : nullptr;
+    v.wbf_layer_bytes = n->bf16_layer_bytes;
+    v.rows_pad = n->rows_pad;
+    v.op_f16 = n->precision == SDF_FP16 ? 1 : 0;
+    return v;
+}
+
+void free_net(sdf_net* n) {
+    if (!n) return;
+    DeviceGuard g(n->device);
+    if (n->d_f32) cudaFree(n->d_f32);
+    if (n->d_bf16) cudaFree(n->d_bf16);
+    delete n;
+}
+
+int load_from_memory(const uint8_t* buf, size_t len, int precision, int device, sdf_net_t* out) {
+    if (!out) return fail(SDF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!buf) return fail(SDF_ERR_ARG, "bytes is NULL");
+    if (precision == SDF_FP8) return fail(SDF_ERR_UNSUPPORTED, "FP8 hidden layers are not built in this version");
+    if (precision != SDF_FP32 && precision != SDF_BF16 && precision != SDF_FP16)
+        return fail(SDF_ERR_ARG, "unknown precision %d", precision);
+    if (len < 32 || std::memcmp(buf, "SDFN", 4) != 0) return fail(SDF_ERR_FORMAT, "not an SDFN image");
+    const uint32_t version = rd_u32(buf + 4), in_dim = rd_u32(buf + 8), width = rd_u32(buf + 12);
+    const uint32_t n_hidden = rd_u32(buf + 16), flags = rd_u32(buf + 28);
+    const float omega0 = rd_f32(buf + 20), omega = rd_f32(buf + 24);
+    if (version != 1) return fail(SDF_ERR_FORMAT, "unsupported SDFN version %u", version);
+    if (in_dim < 1 || in_dim > 4096 || width < 1 || width > 4096 || n_hidden > 64)
+        return fail(SDF_ERR_FORMAT, "implausible shape in=%u width=%u hidden=%u", in_dim, width, n_hidden);
+    const size_t count = static_cast<size_t>(width) * in_dim + width +
+                         static_cast<size_t>(n_hidden) * (static_cast<size_t>(width) * width + width) + width + 1;
+    if (len != 32 + 4 * count) return fail(SDF_ERR_FORMAT, "SDFN size %zu, expected %zu", len, 32 + 4 * count);
+    if ((in_dim != 3 && in_dim != 4) || (width != 64 && width != 128 && width != 256) || n_hidden < 1 ||
+        n_hidden > static_cast<uint32_t>(kMaxHidden))
+        return fail(SDF_ERR_UNSUPPORTED, "shape in=%u (w=%u, k=%u) not supported (in 3|4, w 64|128|256, 1<=k<=%d)",
+                    in_dim, width, n_hidden, kMaxHidden);
+    if (!std::isfinite(omega0) || !std::isfinite(omega)) return fail(SDF_ERR_NONFINITE, "non-finite omega");
+    const uint8_t* q = buf + 32;
+    for (size_t i = 0; i < count; ++i)
+        if (!std::isfinite(rd_f32(q + 4 * i))) return fail(SDF_ERR_NONFINITE, "non-finite parameter %zu", i);
+
+    const int W = static_cast<int>(width), IN = static_cast<int>(in_dim), KH = static_cast<int>(n_hidden);
+    const bool folded = (flags & 1u) != 0;
+    // folded FP64 copies: layer 0 by omega0, hidden layers by omega, output unchanged
+    std::vector<std::vector<double>> Wl(KH + 1), bl(KH + 1);
+    size_t o = 0;
+    for (int l = 0; l <= KH; ++l) {
+        const int fan_in = l == 0 ? IN : W;
+        const double s = folded ? 1.0 : (l == 0 ? omega0 : omega);
+        Wl[l].resize(static_cast<size_t>(W) * fan_in);
+        bl[l].resize(W);
+        for (auto& v : Wl[l]) v = s * rd_f32(q + 4 * o++);
+        for (auto& v : bl[l]) v = s * rd_f32(q + 4 * o++);
+    }
+    std::vector<double> wout(W);
+    for (auto& v : wout) v = rd_f32(q + 4 * o++);
+    const float bout = rd_f32(q + 4 * o++);
+
+    // Lipschitz bound of Eq. 2 (sin is 1-Lipschitz)
+    double L = top_singular_value(Wl[0], W, IN);
+    for (int l = 1; l <= KH; ++l) L *= top_singular_value(Wl[l], W, W);
+    double nw = 0.0;
+    for (double v : wout) nw += v * v;
+    L *= std::sqrt(nw);
+
+    sdf_net* n = new sdf_net;
+    n->device = device;
+    n->precision = precision;
+    n->in_dim = IN;
+    n->width = W;
+    n->n_hidden = KH;
+    n->lipschitz = L;
+    n->bout = bout;
+
+    // FP32 layout: w0 [W][IN], b0, then per hidden layer W^T [k][n] and b, then w_out
+    std::vector<float> f32;
+    n->off_w0 = f32.size();
+    for (double v : Wl[0]) f32.push_back(static_cast<float>(v));
+    n->off_b0 = f32.size();
+    for (double v : bl[0]) f32.push_back(static_cast<float>(v));
+    for (int l = 1; l <= KH; ++l) {
+        while (f32.size() % 4) f32.push_back(0.0f);
+        n->off_wt[l - 1] = f32.size();
+        for (int k = 0; k < W; ++k)
+            for (int r = 0; r < W; ++r) f32.push_back(static_cast<float>(Wl[l][static_cast<size_t>(r) * W + k]));
+        n->off_bh[l - 1] = f32.size();
+        for (double v : bl[l]) f32.push_back(static_cast<float>(v));
+    }
+    n->off_wout = f32.size();
+    for (double v : wout) f32.push_back(static_cast<float>(v));
+
+    // 16-bit hidden weights (bfloat16 or half, round to nearest even), K-major
+    // with the 128-byte swizzle, rows padded to >= 128
+    std::vector<uint8_t> bf;
+    if (precision == SDF_BF16 || precision == SDF_FP16) {
+        // heads for all layers, then the remainders (weight - head) rounded again
+        n->rows_pad = W < 128 ? 128 : W;
+        n->bf16_layer_bytes = static_cast<uint32_t>(n->rows_pad) * W * 2u;
+        const size_t half_bytes = static_cast<size_t>(KH) * n->bf16_layer_bytes;
+        bf.assign(2 * half_bytes, 0);
+        auto to16 = [&](float x) -> uint16_t {
+            return precision == SDF_FP16 ? __half_as_ushort(__float2half_rn(x)) : to_bf16_rne(x);
+        };
+        auto from16 = [&](uint16_t h) -> float {
+            if (precision == SDF_FP16) return __half2float(__ushort_as_half(h));
+            const uint32_t u = static_cast<uint32_t>(h) << 16;
+            float f;
+            std::memcpy(&f, &u, 4);
+            return f;
+        };
+        for (int l = 1; l <= KH; ++l) {
+            uint8_t* dst = bf.data() + static_cast<size_t>(l - 1) * n->bf16_layer_bytes;
+            for (int r = 0; r < W; ++r)
+                for (int k = 0; k < W; ++k) {
+                    const float x = static_cast<float>(Wl[l][static_cast<size_t>(r) * W + k]);
+                    const uint16_t h = to16(x);
+                    const uint16_t lo = to16(x - from16(h));
+                    std::memcpy(dst + sw128_offset(r, k, n->rows_pad), &h, 2);
+                    std::memcpy(dst + half_bytes + sw128_offset(r, k, n->rows_pad), &lo, 2);
+                }
+        }
+    }
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        delete n;
+        return fail(SDF_ERR_ARG, "device %d not available", device);
+    }
+    DeviceGuard g(device);
+    if (!g.ok) {
+        delete n;
+        return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", device);
+    }
+    cudaError_t e = cudaMalloc(&n->d_f32, f32.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(n->d_f32, f32.data(), f32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !bf.empty()) {
+        e = cudaMalloc(&n->d_bf16, bf.size());
+        if (e == cudaSuccess) e = cudaMemcpy(n->d_bf16, bf.data(), bf.size(), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        free_net(n);
+        return cuda_fail(e, "uploading network");
+    }
+    *out = n;
+    g_last_error.clear();
+    return SDF_OK;
+}
+
+bool finite_pos(float x) { return std::isfinite(x) && x > 0.0f; }
+
+struct Scratch {
+    void* ptr = nullptr;
+    cudaStream_t s = nullptr;
+    ~Scratch() {
+        if (ptr) cudaFreeAsync(ptr, s);
+    }
+};
+
+int trace_impl(const sdf_trace_params* P, const float* orig, const float* dir, int64_t n, float* out_pos,
+               float* out_t, uint8_t* out_hit, uint16_t* out_iters, cudaStream_t s) {
+    if (!P) return fail(SDF_ERR_ARG, "params is NULL");
+    if (n < 0 || n > 0x7fffffffLL) return fail(SDF_ERR_ARG, "n = %lld out of range", static_cast<long long>(n));
+    const int m = P->n_levels;
+    if (m < 1 || m > kMaxLevels) return fail(SDF_ERR_ARG, "n_levels = %d out of range 1..%d", m, kMaxLevels);
+    if (!P->nets || !P->delta || !P->max_iters) return fail(SDF_ERR_ARG, "nets, delta and max_iters are required");
+    if (!finite_pos(P->eps)) return fail(SDF_ERR_ARG, "eps must be finite and > 0");
+    if (!std::isfinite(P->box_min) || !std::isfinite(P->box_max) || !(P->box_min < P->box_max))
+        return fail(SDF_ERR_ARG, "box_min < box_max required");
+    if (P->final_mode != 0 && P->final_mode != 1) return fail(SDF_ERR_ARG, "final_mode must be 0 or 1");
+    if (!std::isfinite(P->time)) return fail(SDF_ERR_ARG, "time must be finite");
+    const int dev = P->nets[0] ? P->nets[0]->device : -1;
+    for (int j = 0; j < m; ++j) {
+        const sdf_net* net = P->nets[j];
+        if (!net) return fail(SDF_ERR_ARG, "nets[%d] is NULL", j);
+        if (net->device != dev) return fail(SDF_ERR_ARG, "networks live on different devices");
+        if (net->in_dim != P->nets[0]->in_dim) return fail(SDF_ERR_ARG, "networks differ in input dimension");
+        if (P->max_iters[j] < 0) return fail(SDF_ERR_ARG, "max_iters[%d] < 0", j);
+        const bool uses_delta = (j < m - 1) || P->final_mode == 1;
+        if (uses_delta && !finite_pos(P->delta[j])) return fail(SDF_ERR_ARG, "delta[%d] must be finite and > 0", j);
+        if (P->step_scale && !finite_pos(P->step_scale[j]))
+            return fail(SDF_ERR_ARG, "step_scale[%d] must be finite and > 0", j);
+        if (!P->step_scale && !(net->lipschitz > 0.0))
+            return fail(SDF_ERR_ARG, "nets[%d] has a zero Lipschitz bound; pass step_scale", j);
+        if (net->precision != SDF_FP32 && !tc_trace_supported(net->width, net->n_hidden))
+            return fail(SDF_ERR_UNSUPPORTED, "tensor-core tracing of a (%d,%d) network is not built", net->width,
+                        net->n_hidden);
+    }
+    DeviceGuard g(dev);
+    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", dev);
+    if (n == 0) return SDF_OK;
+    int rc;
+    if ((rc = check_device_ptr(orig, dev, "orig")) || (rc = check_device_ptr(dir, dev, "dir")) ||
+        (rc = check_device_ptr(out_pos, dev, "out_pos")) || (rc = check_device_ptr(out_t, dev, "out_t")) ||
+        (rc = check_device_ptr(out_hit, dev, "out_hit")))
+        return rc;
+    if (out_iters && (rc = check_device_ptr(out_iters, dev, "out_iters"))) return rc;
+    DeviceInfo di;
+    if ((rc = device_info(dev, &di))) return rc;
+
+    // scratch: counters (grab_j, count_j) then two ray-index lists
+    const size_t counter_bytes = 2 * kMaxLevels * sizeof(unsigned long long);
+    const size_t list_bytes = (m > 1) ? static_cast<size_t>(n) * sizeof(int32_t) : 0;
+    Scratch sc;
+    sc.s = s;
+    cudaError_t e = cudaMallocAsync(&sc.ptr, counter_bytes + 2 * list_bytes + 256, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch)");
+    e = cudaMemsetAsync(sc.ptr, 0, counter_bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    auto* counters = static_cast<unsigned long long*>(sc.ptr);
+    int32_t* lists[2] = {reinterpret_cast<int32_t*>(static_cast<uint8_t*>(sc.ptr) + counter_bytes),
+                         reinterpret_cast<int32_t*>(static_cast<uint8_t*>(sc.ptr) + counter_bytes + list_bytes)};
+
+    for (int j = 0; j < m; ++j) {
+        const sdf_net* net = P->nets[j];
+        const bool last = (j == m - 1);
+        LevelArgs la{};
+        la.net = view_of(net);
+        la.d = (last && P->final_mode == 0) ? 0.0f : P->delta[j];
+        la.scale = P->step_scale ? P->step_scale[j] : static_cast<float>(1.0 / net->lipschitz);
+        la.cap = P->max_iters[j];
+        la.is_last = last ? 1 : 0;
+        la.time = P->time;
+        la.eps = P->eps;
+        la.box_lo = P->box_min;
+        la.box_hi = P->box_max;
+        la.orig = orig;
+        la.dir = dir;
+        la.n = n;
+        la.out_pos = out_pos;
+        la.out_t = out_t;
+        la.out_hit = out_hit;
+        la.out_iters = out_iters;
+        la.in_list = j == 0 ? nullptr : lists[(j - 1) & 1];
+        la.in_count = j == 0 ? nullptr : &counters[kMaxLevels + j - 1];
+        la.out_list = last ? nullptr : lists[j & 1];
+        la.out_count = last ? nullptr : &counters[kMaxLevels + j];
+        la.grab = &counters[j];
+        la.status = di.d_status;
+        e = (net->precision != SDF_FP32) ? launch_trace_level_tc(la, di.num_sms, s)
+                                         : launch_trace_level_simt(la, di.num_sms, s);
+        if (e != cudaSuccess) return cuda_fail(e, "launching trace level");
+    }
+    return SDF_OK;
+}
+
+int grad_impl(sdf_net_t net, const float* pts, const uint8_t* mask, int64_t n, float* out, int normalize,
+              cudaStream_t s) {
+    if (!net) return fail(SDF_ERR_ARG, "net is NULL");
+    if (n < 0 || n > 0x7fffffffLL) return fail(SDF_ERR_ARG, "n = %lld out of range", static_cast<long long>(n));
+    DeviceGuard g(net->device);
+    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", net->device);
+    if (n == 0) return SDF_OK;
+    int rc;
+    if ((rc = check_device_ptr(pts, net->device, "pts")) || (rc = check_device_ptr(out, net->device, "out")))
+        return rc;
+    if (mask && (rc = check_device_ptr(mask, net->device, "mask"))) return rc;
+    if (net->precision != SDF_FP32 && !tc_grad_supported(net->width, net->n_hidden))
+        return fail(SDF_ERR_UNSUPPORTED, "tensor-core gradients of a (%d,%d) network are not built", net->width,
+                    net->n_hidden);
+    DeviceInfo di;
+    if ((rc = device_info(net->device, &di))) return rc;
+    const size_t counter_bytes = 4 * sizeof(unsigned long long);
+    const size_t list_bytes = mask ? static_cast<size_t>(n) * sizeof(int32_t) : 0;
+    Scratch sc;
+    sc.s = s;
+    cudaError_t e = cudaMallocAsync(&sc.ptr, counter_bytes + list_bytes + 256, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch)");
+    e = cudaMemsetAsync(sc.ptr, 0, counter_bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    auto* counters = static_cast<unsigned long long*>(sc.ptr);
+    int32_t* list = mask ? reinterpret_cast<int32_t*>(static_cast<uint8_t*>(sc.ptr) + counter_bytes) : nullptr;
+    if (mask) {
+        e = launch_mask_compact(mask, n, list, &counters[1], out, di.num_sms, s);
+        if (e != cudaSuccess) return cuda_fail(e, "launching mask compaction");
+    }
+    GradArgs ga{};
+    ga.net = view_of(net);
+    ga.time = net->time;
+    ga.pts = pts;
+    ga.n = n;
+    ga.list = list;
+    ga.count = mask ? &counters[1] : nullptr;
+    ga.out = out;
+    ga.normalize = normalize;
+    ga.grab = &counters[0];
+    ga.status = di.d_status;
+    e = (net->precision != SDF_FP32) ? launch_grad_tc(ga, di.num_sms, s) : launch_grad_simt(ga, di.num_sms, s);
+    if (e != cudaSuccess) return cuda_fail(e, "launching gradient kernel");
+    return SDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sdf_net_load_mem(const void* bytes, size_t n_bytes, int precision, int device, sdf_net_t* out) {
+    return load_from_memory(static_cast<const uint8_t*>(bytes), n_bytes, precision, device, out);
+}
+
+int sdf_net_load(const char* path, int precision, int device, sdf_net_t* out) {
+    if (!out) return fail(SDF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!path) return fail(SDF_ERR_ARG, "path is NULL");
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(SDF_ERR_FILE, "cannot open %s", path);
+    std::vector<uint8_t> buf;
+    uint8_t tmp[1 << 16];
+    size_t got;
+    while ((got = std::fread(tmp, 1, sizeof(tmp), fp)) > 0) buf.insert(buf.end(), tmp, tmp + got);
+    const bool err = std::ferror(fp) != 0;
+    std::fclose(fp);
+    if (err) return fail(SDF_ERR_FILE, "error reading %s", path);
+    return load_from_memory(buf.data(), buf.size(), precision, device, out);
+}
+
+int sdf_net_info(sdf_net_t net, int* in_dim, int* width, int* n_hidden, double* lipschitz) {
+    if (!net) return fail(SDF_ERR_ARG, "net is NULL");
+    if (in_dim) *in_dim = net->in_dim;
+    if (width) *width = net->width;
+    if (n_hidden) *n_hidden = net->n_hidden;
+    if (lipschitz) *lipschitz = net->lipschitz;
+    return SDF_OK;
+}
+
+int sdf_net_set_time(sdf_net_t net, float time) {
+    if (!net) return fail(SDF_ERR_ARG, "net is NULL");
+    if (!std::isfinite(time)) return fail(SDF_ERR_ARG, "time must be finite");
+    net->time = time;
+    return SDF_OK;
+}
+
+void sdf_net_free(sdf_net_t net) { free_net(net); }
+
+int sdf_trace_multiscale(const sdf_trace_params* params, const float* orig, const float* dir, int64_t n,
+                         float* out_pos, float* out_t, uint8_t* out_hit, uint16_t* out_iters, void* cuda_stream) {
+    return trace_impl(params, orig, dir, n, out_pos, out_t, out_hit, out_iters,
+                      static_cast<cudaStream_t>(cuda_stream));
+}
+
+int sdf_normals(sdf_net_t net, const float* pts, int64_t n, float* out_grad, void* cuda_stream) {
+    return grad_impl(net, pts, nullptr, n, out_grad, 0, static_cast<cudaStream_t>(cuda_stream));
+}
+
+int sdf_normal_map(sdf_net_t fine, const float* pts, const uint8_t* mask, int64_t n, float* out_normal,
+                   void* cuda_stream) {
+    return grad_impl(fine, pts, mask, n, out_normal, 1, static_cast<cudaStream_t>(cuda_stream));
+}
+
+int sdf_render_host(const sdf_trace_params* params, sdf_net_t fine, const float* orig, const float* dir, int64_t n,
+                    float* out_pos, uint8_t* out_hit, float* out_normal, void* cuda_stream) {
+    if (!params || !params->nets || params->n_levels < 1 || !params->nets[0])
+        return fail(SDF_ERR_ARG, "params / nets missing");
+    if (!fine) return fail(SDF_ERR_ARG, "fine is NULL");
+    if (!orig || !dir || !out_pos || !out_hit || !out_normal) return fail(SDF_ERR_ARG, "NULL host buffer");
+    if (n < 0 || n > 0x7fffffffLL) return fail(SDF_ERR_ARG, "n out of range");
+    if (n == 0) return SDF_OK;
+    const int dev = params->nets[0]->device;
+    if (fine->device != dev) return fail(SDF_ERR_ARG, "fine network on another device");
+    DeviceGuard g(dev);
+    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", dev);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const size_t v3 = 3 * static_cast<size_t>(n) * sizeof(float), v1 = static_cast<size_t>(n) * sizeof(float);
+    // device buffers: orig, dir, pos, normal (3n floats each), t (n floats), hit (n bytes)
+    const size_t bytes = 4 * v3 + v1 + static_cast<size_t>(n) + 1024;
+    Scratch sc;
+    sc.s = s;
+    cudaError_t e = cudaMallocAsync(&sc.ptr, bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(frame)");
+    uint8_t* b = static_cast<uint8_t*>(sc.ptr);
+    float* d_orig = reinterpret_cast<float*>(b);
+    float* d_dir = reinterpret_cast<float*>(b + v3);
+    float* d_pos = reinterpret_cast<float*>(b + 2 * v3);
+    float* d_nrm = reinterpret_cast<float*>(b + 3 * v3);
+    float* d_t = reinterpret_cast<float*>(b + 4 * v3);
+    uint8_t* d_hit = b + 4 * v3 + v1;
+    if ((e = cudaMemcpyAsync(d_orig, orig, v3, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_dir, dir, v3, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "copying rays to the device");
+    int rc = trace_impl(params, d_orig, d_dir, n, d_pos, d_t, d_hit, nullptr, s);
+    if (rc) return rc;
+    rc = grad_impl(fine, d_pos, d_hit, n, d_nrm, 1, s);
+    if (rc) return rc;
+    if ((e = cudaMemcpyAsync(out_pos, d_pos, v3, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(out_normal, d_nrm, v3, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(out_hit, d_hit, static_cast<size_t>(n), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(e, "copying results to the host");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return SDF_OK;
+}
+
+int sdf_sync_status(void* cuda_stream) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    DeviceInfo di;
+    int rc = device_info(dev, &di);
+    if (rc) return rc;
+    int status = 0;
+    e = cudaMemcpy(&status, di.d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the status word");
+    if (status != 0) {
+        const int zero = 0;
+        cudaMemcpy(di.d_status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        return fail(status, "device reported status %d (a bounded wait expired)", status);
+    }
+    return SDF_OK;
+}
+
+const char* sdf_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// Internal interface between the C-ABI layer (api.cu) and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sdfnn {
+
+constexpr int kMaxHidden = 4;
+constexpr int kMaxLevels = 8;
+
+// Device view of one prepared network (all pointers are device memory).
+struct NetView {
+    int in_dim, width, n_hidden;
+    const float* w0;               // [width][in_dim], folded by omega0
+    const float* b0;               // [width], folded
+    const float* wt[kMaxHidden];   // FP32 hidden weights, transposed: wt[i][k * width + n] = W_i[n][k], folded
+    const float* bh[kMaxHidden];   // [width], folded
+    const float* wout;             // [width]
+    float bout;
+    const uint8_t* wbf;            // 16-bit hidden weights in the 128-byte-swizzled K-major layout
+    const uint8_t* wbf_lo;         // 16-bit rounding of (weight - head), same layout, or NULL
+    uint32_t wbf_layer_bytes;      // bytes per hidden layer in wbf
+    int rows_pad;                  // rows per 64-wide K block in wbf (max(width, 128), zero padded)
+    int op_f16;                    // tensor-core operand type of wbf: 1 = IEEE half, 0 = bfloat16
+};
+
+// One level of Alg. 1 as launched.
+struct LevelArgs {
+    NetView net;
+    float d;          // t = f(p) - d
+    float scale;      // step = scale * t
+    int cap;          // iteration cap of this level
+    int is_last;      // last level: the hit decision is taken here
+    float time;       // 4th network input
+    float eps, box_lo, box_hi;
+    // rays and outputs (SoA, n items)
+    const float* orig;
+    const float* dir;
+    int64_t n;
+    float* out_pos;
+    float* out_t;
+    uint8_t* out_hit;
+    uint16_t* out_iters;
+    // work lists: level 0 reads rays 0..n-1 directly; later levels read in_list[0..*in_count)
+    const int32_t* in_list;
+    const unsigned long long* in_count;
+    int32_t* out_list;              // NULL on the last level
+    unsigned long long* out_count;
+    unsigned long long* grab;       // work counter, zero at launch
+    int* status;
+};
+
+// Gradient / normal-mapping launch.
+struct GradArgs {
+    NetView net;
+    float time;
+    const float* pts;               // SoA (3, n)
+    int64_t n;
+    const int32_t* list;            // NULL: points 0..n-1; else list[0..*count)
+    const unsigned long long* count;
+    float* out;                     // SoA (3, n)
+    int normalize;                  // 1: unit normal (0 where |g| < 1e-12)
+    unsigned long long* grab;       // tile counter, zero at launch
+    int* status;
+};
+
+// Kernel launchers (return cudaError_t of the launch).
+cudaError_t launch_trace_level_simt(const LevelArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_grad_simt(const GradArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_trace_level_tc(const LevelArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_grad_tc(const GradArgs& a, int num_sms, cudaStream_t s);
+bool tc_trace_supported(int width, int n_hidden);
+bool tc_trace_split(int width, int n_hidden);  // head+remainder operands in the trace kernel
+bool tc_grad_supported(int width, int n_hidden);
+
+// Builds list[] of the indices with mask[i] != 0 (order unspecified), zeroes
+// out[.][i] where mask[i] == 0, and counts into *count (zero at launch).
+cudaError_t launch_mask_compact(const uint8_t* mask, int64_t n, int32_t* list, unsigned long long* count,
+                                float* out, int num_sms, cudaStream_t s);
+
+}  // namespace sdfnn

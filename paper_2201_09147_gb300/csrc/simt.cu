@@ -1,0 +1,374 @@
+// FP32 SIMT kernels: the plain FP32 path (SDF_FP32) and its building blocks.
+//
+// Both kernels evaluate the sine MLP of Eq. 2 on tiles of 128 rows held in
+// shared memory, one layer at a time, as a register-tiled FP32 GEMM
+// (256 threads; each thread owns 8 rows x width/16 output features), with the
+// sine (or sine/cosine) epilogue fused after each layer.
+//
+//   trace_level_simt : one level of multiscale sphere tracing (Alg. 1).  The
+//                      128 rows are persistent ray slots; a slot whose ray
+//                      finishes is refilled from the level's work list with a
+//                      warp-aggregated atomic (ballot + popc), so tiles stay
+//                      dense until the work runs out.
+//   grad_simt        : analytic gradients (Alg. 2, Eqs. 3-4).  The 128 rows
+//                      are 32 points x 4 streams: the forward activations and
+//                      the three forward tangents G^x, G^y, G^z, which share
+//                      every weight load.
+#include <cstdint>
+
+#include "common.cuh"
+#include "internal.h"
+#include "rays.cuh"
+
+namespace sdfnn {
+namespace {
+
+constexpr int kSimtThreads = 256;
+constexpr int kChunkK = 16;  // rows of W^T staged per step
+
+// Activation tile X^T[k][r] (k = feature, r = row) with 4-float groups of r
+// permuted by (k / 4) % 8 to keep the epilogue's column stores conflict free.
+__device__ __forceinline__ int xt_index(int k, int r) { return k * 128 + ((((r >> 2) ^ ((k >> 2) & 7))) << 2) + (r & 3); }
+
+template <int W>
+struct SimtSmem {
+    float xt[W * 128];
+    float ws[2 * kChunkK * W];
+    float f[128];
+    float px[128], py[128], pz[128];  // ray positions (trace) / points (grad)
+    int idx[128];
+    long long tile;
+};
+
+// acc[i][j] = sum_k X[r0 + i][k] * W[n_j][k] for the thread's 8 rows and its
+// features n_j = (j / 4) * 64 + fg * 4 + j % 4.  W^T is streamed from global
+// memory (L2 resident) through a double-buffered shared-memory stage.
+// Starts and ends with the block synchronised.
+template <int W>
+__device__ __forceinline__ void simt_gemm(const float* __restrict__ xt, const float* __restrict__ wt_g,
+                                          float* __restrict__ ws, float (&acc)[8][W / 16], int r0, int fg) {
+    constexpr int G = W / 64;
+    constexpr int NCH = W / kChunkK;
+    constexpr int F4_PER_CHUNK = kChunkK * W / 4;
+    constexpr int PER_T = F4_PER_CHUNK / kSimtThreads;
+    static_assert(PER_T >= 1, "chunk too small");
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < W / 16; ++j) acc[i][j] = 0.0f;
+
+    const float4* src = reinterpret_cast<const float4*>(wt_g);
+    float4 pre[PER_T];
+#pragma unroll
+    for (int u = 0; u < PER_T; ++u) pre[u] = __ldg(src + tid + u * kSimtThreads);
+#pragma unroll
+    for (int u = 0; u < PER_T; ++u) reinterpret_cast<float4*>(ws)[tid + u * kSimtThreads] = pre[u];
+    __syncthreads();
+
+    for (int c = 0; c < NCH; ++c) {
+        const float* wsc = ws + (c & 1) * kChunkK * W;
+        if (c + 1 < NCH) {
+#pragma unroll
+            for (int u = 0; u < PER_T; ++u) pre[u] = __ldg(src + (c + 1) * F4_PER_CHUNK + tid + u * kSimtThreads);
+        }
+#pragma unroll 4
+        for (int kk = 0; kk < kChunkK; ++kk) {
+            const int k = c * kChunkK + kk;
+            const int sw = (k >> 2) & 7;
+            const float4 xa = *reinterpret_cast<const float4*>(xt + k * 128 + ((((r0 >> 2)) ^ sw) << 2));
+            const float4 xb = *reinterpret_cast<const float4*>(xt + k * 128 + ((((r0 >> 2) + 1) ^ sw) << 2));
+            const float x[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const float4 wv = *reinterpret_cast<const float4*>(wsc + kk * W + g * 64 + fg * 4);
+                const float w4[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[i][g * 4 + e] = fmaf(x[i], w4[e], acc[i][g * 4 + e]);
+            }
+        }
+        if (c + 1 < NCH) {
+            float4* dst = reinterpret_cast<float4*>(ws + ((c + 1) & 1) * kChunkK * W);
+#pragma unroll
+            for (int u = 0; u < PER_T; ++u) dst[tid + u * kSimtThreads] = pre[u];
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ int feat_of(int j, int fg) { return (j >> 2) * 64 + fg * 4 + (j & 3); }
+
+// Sum over the 16 lanes that share a row group (lanes l and l ^ 1, 2, 4, 8).
+__device__ __forceinline__ float reduce16(float v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// trace kernel
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void __launch_bounds__(kSimtThreads) trace_level_simt_kernel(const LevelArgs a) {
+    extern __shared__ float4 smem_f4[];
+    SimtSmem<W>& S = *reinterpret_cast<SimtSmem<W>*>(smem_f4);
+    constexpr int FPT = W / 16;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rg = warp * 2 + (lane >> 4), fg = lane & 15, r0 = rg * 8;
+    const NetView& net = a.net;
+    const long long n_work = a.in_list ? static_cast<long long>(*a.in_count) : a.n;
+    Ray ray;  // threads 0..127 own ray slot tid
+
+    while (true) {
+        if (tid < 128) {
+            refill_ray(a, ray, n_work);
+            S.px[tid] = ray.px;
+            S.py[tid] = ray.py;
+            S.pz[tid] = ray.pz;
+        }
+        if (!__syncthreads_or(tid < 128 && ray.state == kSlotActive)) break;
+        if (a.cap <= 0) {
+            if (tid < 128) pass_ray(a, ray);
+            continue;
+        }
+
+        // layer 0 (FP32): X[r][n] = sin(W_0[n] . (p_r, time) + b_0[n])
+#pragma unroll
+        for (int j = 0; j < FPT; ++j) {
+            const int n = feat_of(j, fg);
+            const float wx = __ldg(net.w0 + n * net.in_dim + 0), wy = __ldg(net.w0 + n * net.in_dim + 1),
+                        wz = __ldg(net.w0 + n * net.in_dim + 2);
+            float bb = __ldg(net.b0 + n);
+            if (net.in_dim == 4) bb = fmaf(__ldg(net.w0 + n * 4 + 3), a.time, bb);
+            float o[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int r = r0 + i;
+                const float z = fmaf(wx, S.px[r], fmaf(wy, S.py[r], fmaf(wz, S.pz[r], bb)));
+                o[i] = sin_r(z);
+            }
+            *reinterpret_cast<float4*>(S.xt + xt_index(n, r0)) = make_float4(o[0], o[1], o[2], o[3]);
+            *reinterpret_cast<float4*>(S.xt + xt_index(n, r0 + 4)) = make_float4(o[4], o[5], o[6], o[7]);
+        }
+        __syncthreads();
+
+        float acc[8][FPT];
+        for (int l = 0; l < net.n_hidden; ++l) {
+            simt_gemm<W>(S.xt, net.wt[l], S.ws, acc, r0, fg);
+            if (l + 1 < net.n_hidden) {
+#pragma unroll
+                for (int j = 0; j < FPT; ++j) {
+                    const int n = feat_of(j, fg);
+                    const float bb = __ldg(net.bh[l] + n);
+                    float o[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) o[i] = sin_r(acc[i][j] + bb);
+                    *reinterpret_cast<float4*>(S.xt + xt_index(n, r0)) = make_float4(o[0], o[1], o[2], o[3]);
+                    *reinterpret_cast<float4*>(S.xt + xt_index(n, r0 + 4)) = make_float4(o[4], o[5], o[6], o[7]);
+                }
+                __syncthreads();
+            } else {
+                // output layer: f = W_n P_{n-1} + b_n
+                float dot[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) dot[i] = 0.0f;
+#pragma unroll
+                for (int j = 0; j < FPT; ++j) {
+                    const int n = feat_of(j, fg);
+                    const float bb = __ldg(net.bh[l] + n), wo = __ldg(net.wout + n);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) dot[i] = fmaf(wo, sin_r(acc[i][j] + bb), dot[i]);
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float s = reduce16(dot[i]);
+                    if (fg == 0) S.f[r0 + i] = s + net.bout;
+                }
+            }
+        }
+        __syncthreads();
+        if (tid < 128) step_ray(a, ray, S.f[tid]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// gradient kernel (Alg. 2 with the three tangents sharing the forward pass)
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void __launch_bounds__(kSimtThreads) grad_simt_kernel(const GradArgs a) {
+    extern __shared__ float4 smem_f4[];
+    SimtSmem<W>& S = *reinterpret_cast<SimtSmem<W>*>(smem_f4);
+    constexpr int FPT = W / 16;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rg = warp * 2 + (lane >> 4), fg = lane & 15, r0 = rg * 8;
+    const int p0 = r0 >> 2;  // this thread's rows are points p0, p0 + 1, four streams each
+    const NetView& net = a.net;
+    const long long n_work = a.list ? static_cast<long long>(*a.count) : a.n;
+
+    while (true) {
+        if (tid == 0) S.tile = static_cast<long long>(atomicAdd(a.grab, 1ull));
+        __syncthreads();
+        const long long base = S.tile * 32;
+        if (base >= n_work) break;
+        if (tid < 32) {
+            const long long k = base + tid;
+            int i = -1;
+            if (k < n_work) i = a.list ? a.list[k] : static_cast<int>(k);
+            S.idx[tid] = i;
+            S.px[tid] = i >= 0 ? a.pts[i] : 0.0f;
+            S.py[tid] = i >= 0 ? a.pts[a.n + i] : 0.0f;
+            S.pz[tid] = i >= 0 ? a.pts[2 * a.n + i] : 0.0f;
+        }
+        __syncthreads();
+
+        // input layer: A_0 = W_0 p + b_0;  P_0 = sin(A_0);  G_0^c = W_0[:, c] (.) cos(A_0)
+#pragma unroll
+        for (int j = 0; j < FPT; ++j) {
+            const int n = feat_of(j, fg);
+            const float wx = __ldg(net.w0 + n * net.in_dim + 0), wy = __ldg(net.w0 + n * net.in_dim + 1),
+                        wz = __ldg(net.w0 + n * net.in_dim + 2);
+            float bb = __ldg(net.b0 + n);
+            if (net.in_dim == 4) bb = fmaf(__ldg(net.w0 + n * 4 + 3), a.time, bb);
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) {
+                const int p = p0 + pp;
+                const float z = fmaf(wx, S.px[p], fmaf(wy, S.py[p], fmaf(wz, S.pz[p], bb)));
+                float s, c;
+                sincos_r(z, &s, &c);
+                *reinterpret_cast<float4*>(S.xt + xt_index(n, r0 + pp * 4)) = make_float4(s, wx * c, wy * c, wz * c);
+            }
+        }
+        __syncthreads();
+
+        float acc[8][FPT];
+        for (int l = 0; l < net.n_hidden; ++l) {
+            simt_gemm<W>(S.xt, net.wt[l], S.ws, acc, r0, fg);
+            const bool last = (l + 1 == net.n_hidden);
+            float dot[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) dot[i] = 0.0f;
+#pragma unroll
+            for (int j = 0; j < FPT; ++j) {
+                const int n = feat_of(j, fg);
+                const float bb = __ldg(net.bh[l] + n);
+                const float wo = last ? __ldg(net.wout + n) : 0.0f;
+#pragma unroll
+                for (int pp = 0; pp < 2; ++pp) {
+                    // hidden layer: P_i = sin(A_i);  G_i = (W_i G_{i-1}) (.) cos(A_i)
+                    float s, c;
+                    sincos_r(acc[pp * 4][j] + bb, &s, &c);
+                    const float g0 = c * acc[pp * 4 + 1][j], g1 = c * acc[pp * 4 + 2][j], g2 = c * acc[pp * 4 + 3][j];
+                    if (!last) {
+                        *reinterpret_cast<float4*>(S.xt + xt_index(n, r0 + pp * 4)) = make_float4(s, g0, g1, g2);
+                    } else {
+                        dot[pp * 4 + 0] = fmaf(wo, s, dot[pp * 4 + 0]);
+                        dot[pp * 4 + 1] = fmaf(wo, g0, dot[pp * 4 + 1]);
+                        dot[pp * 4 + 2] = fmaf(wo, g1, dot[pp * 4 + 2]);
+                        dot[pp * 4 + 3] = fmaf(wo, g2, dot[pp * 4 + 3]);
+                    }
+                }
+            }
+            if (!last) {
+                __syncthreads();
+            } else {
+                // output layer: grad_c = W_n G^c_{n-1}
+#pragma unroll
+                for (int i = 0; i < 8; ++i) dot[i] = reduce16(dot[i]);
+                if (fg == 0) {
+#pragma unroll
+                    for (int pp = 0; pp < 2; ++pp) {
+                        const int i = S.idx[p0 + pp];
+                        if (i >= 0) {
+                            float gx = dot[pp * 4 + 1], gy = dot[pp * 4 + 2], gz = dot[pp * 4 + 3];
+                            if (a.normalize) {
+                                const float len = sqrtf(gx * gx + gy * gy + gz * gz);
+                                const float inv = len >= 1e-12f ? 1.0f / len : 0.0f;
+                                gx *= inv;
+                                gy *= inv;
+                                gz *= inv;
+                            }
+                            a.out[i] = gx;
+                            a.out[a.n + i] = gy;
+                            a.out[2 * a.n + i] = gz;
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void mask_compact_kernel(const uint8_t* __restrict__ mask, int64_t n, int32_t* __restrict__ list,
+                                    unsigned long long* count, float* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride) {
+        const int64_t i = base + lane;
+        const bool in = i < n;
+        const bool m = in && mask[i] != 0;
+        const long long k = warp_grab(count, m);
+        if (m) {
+            list[k] = static_cast<int32_t>(i);
+        } else if (in && out) {
+            out[i] = 0.0f;
+            out[n + i] = 0.0f;
+            out[2 * n + i] = 0.0f;
+        }
+    }
+}
+
+template <class Kernel>
+cudaError_t launch_persistent(Kernel k, size_t smem, int num_sms, cudaStream_t s, const void* arg) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kSimtThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    void* args[] = {const_cast<void*>(arg)};
+    return cudaLaunchKernel(reinterpret_cast<const void*>(k), dim3(num_sms * per_sm), dim3(kSimtThreads), args, smem,
+                            s);
+}
+
+}  // namespace
+
+cudaError_t launch_trace_level_simt(const LevelArgs& a, int num_sms, cudaStream_t s) {
+    switch (a.net.width) {
+    case 64:
+        return launch_persistent(trace_level_simt_kernel<64>, sizeof(SimtSmem<64>), num_sms, s, &a);
+    case 128:
+        return launch_persistent(trace_level_simt_kernel<128>, sizeof(SimtSmem<128>), num_sms, s, &a);
+    case 256:
+        return launch_persistent(trace_level_simt_kernel<256>, sizeof(SimtSmem<256>), num_sms, s, &a);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_grad_simt(const GradArgs& a, int num_sms, cudaStream_t s) {
+    switch (a.net.width) {
+    case 64:
+        return launch_persistent(grad_simt_kernel<64>, sizeof(SimtSmem<64>), num_sms, s, &a);
+    case 128:
+        return launch_persistent(grad_simt_kernel<128>, sizeof(SimtSmem<128>), num_sms, s, &a);
+    case 256:
+        return launch_persistent(grad_simt_kernel<256>, sizeof(SimtSmem<256>), num_sms, s, &a);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_mask_compact(const uint8_t* mask, int64_t n, int32_t* list, unsigned long long* count, float* out,
+                                int num_sms, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int blocks = static_cast<int>((n + 255) / 256);
+    if (blocks > num_sms * 8) blocks = num_sms * 8;
+    mask_compact_kernel<<<blocks, 256, 0, s>>>(mask, n, list, count, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sdfnn

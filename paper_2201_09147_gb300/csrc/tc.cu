@@ -1,0 +1,883 @@
+// Tensor-core (tcgen05) kernels of the 16-bit paths (SDF_BF16, SDF_FP16).
+// Both run tcgen05.mma.kind::f16 with FP32 accumulation in TMEM; the operand
+// type (bfloat16 or IEEE half) is a template parameter.
+//
+// trace_level_tc : one level of multiscale sphere tracing (Alg. 1).  A CTA
+//   holds 128 persistent ray slots, one per thread and per TMEM lane.  Each
+//   evaluation of f (Eq. 2) runs layer 0 in FP32 on the CUDA cores, writes
+//   sin(A_0) in 16 bits into the A operand (128 rays x width, K-major,
+//   128-byte swizzle), then for every hidden layer one thread issues
+//   tcgen05.mma (M = 128 rays, N = width, K = width) against the resident
+//   16-bit weights; each thread reads its own row back with tcgen05.ld, adds
+//   the bias and applies the sine in registers.  The output layer is an FP32
+//   dot product of the last sine layer straight from TMEM, so the step
+//   t = f - d is never rounded to 16 bits.
+//
+// grad_tc : analytic gradients (Alg. 2).  Tiles of 64 points; the MMA runs
+//   with the features as rows (M = 128 per TMEM tile, width/128 tiles) and
+//   N = 256 columns = 64 points x {forward, G^x, G^y, G^z}, so one weight
+//   tile feeds the forward pass and the three tangents at once and the
+//   thread that owns feature m finds A_i[m] and the three G_i[m] of a point
+//   in its own TMEM lane: the epilogue P_i = sin(A_i), G_i = cos(A_i) (.)
+//   (W_i G_{i-1}) needs no data exchange.  Hidden weights stream from L2
+//   through a ring of shared-memory stages filled by bulk copies (TMA); the
+//   output layer W_n G_{n-1} is one more small MMA (rows = the 256
+//   point-streams, N = 16, w_out as a head row plus a remainder row).
+#include <cstdint>
+
+#include "common.cuh"
+#include "internal.h"
+#include "rays.cuh"
+
+namespace sdfnn {
+namespace {
+
+// ---------------------------------------------------------------------------
+// trace kernel
+// ---------------------------------------------------------------------------
+constexpr int kTraceThreads = 128;
+
+struct TraceLayout {
+    uint32_t x, xlo, w, wlo, w0, b0, bh, wout, bars, misc, total;
+};
+
+// Shared-memory layout of the resident-weight trace kernel.  With `split`
+// the activations and weights are each held as a 16-bit head plus the
+// 16-bit rounding of the remainder (two operand copies).
+__host__ __device__ inline TraceLayout trace_layout(int W, int KH, bool split = false) {
+    TraceLayout L;
+    uint32_t o = 0;
+    const uint32_t xbytes = 128u * W * 2u, wbytes = static_cast<uint32_t>(KH) * W * W * 2u;
+    L.x = o;
+    o += xbytes;
+    L.xlo = o;
+    o += split ? xbytes : 0u;
+    L.w = o;
+    o += wbytes;
+    L.wlo = o;
+    o += split ? wbytes : 0u;
+    L.w0 = o;
+    o += W * 4u * 4u;
+    L.b0 = o;
+    o += W * 4u;
+    L.bh = o;
+    o += static_cast<uint32_t>(KH) * W * 4u;
+    L.wout = o;
+    o += W * 4u;
+    L.bars = o;
+    o += 64u;
+    L.misc = o;
+    o += 64u;
+    L.total = o;
+    return L;
+}
+
+constexpr uint32_t kSplitSmemLimit = 200u * 1024u;
+
+// The trace kernel's tensor pipe is mostly idle (its time goes to the sines),
+// so whenever the doubled operands fit it computes each hidden layer as
+// hi(W) hi(X) + lo(W) hi(X) + hi(W) lo(X) with hi/lo the 16-bit head and
+// remainder: the contraction then carries ~16 (BF16) or ~22 (FP16)
+// significant bits instead of 8 or 11.
+inline bool trace_split(int W, int KH) { return trace_layout(W, KH, true).total + 1024 <= kSplitSmemLimit; }
+
+// 16-bit head and remainder of two floats, packed as pairs.
+template <bool F16>
+__device__ __forceinline__ void pack_split(float a, float b, uint32_t& hi, uint32_t& lo) {
+    hi = pack16x2<F16>(a, b);
+    const float ah = from16<F16>(static_cast<uint16_t>(hi & 0xFFFFu));
+    const float bh = from16<F16>(static_cast<uint16_t>(hi >> 16));
+    lo = pack16x2<F16>(a - ah, b - bh);
+}
+
+template <int W, bool F16, bool SPLIT>
+__global__ void __launch_bounds__(kTraceThreads) trace_level_tc_kernel(const LevelArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const uint32_t raw_s = smem_u32(smem_raw);
+    const uint32_t base_s = (raw_s + 1023u) & ~1023u;
+    uint8_t* base = smem_raw + (base_s - raw_s);
+    const NetView& net = a.net;
+    const int KH = net.n_hidden;
+    const TraceLayout L = trace_layout(W, KH, SPLIT);
+    float* w0s = reinterpret_cast<float*>(base + L.w0);
+    float* b0s = reinterpret_cast<float*>(base + L.b0);
+    float* bhs = reinterpret_cast<float*>(base + L.bh);
+    float* wos = reinterpret_cast<float*>(base + L.wout);
+    const uint32_t bar_w = base_s + L.bars, bar_mma = base_s + L.bars + 8;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.misc);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(base + L.misc + 8);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t x_s = base_s + L.x, w_s = base_s + L.w, xlo_s = base_s + L.xlo, wlo_s = base_s + L.wlo;
+
+    if (tid == 0) {
+        mbar_init(bar_w, 1);
+        mbar_init(bar_mma, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(smem_u32(tmem_slot), W);
+        tmem_relinquish();
+    }
+    for (int i = tid; i < W; i += kTraceThreads) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) w0s[i * 4 + c] = net.w0[i * net.in_dim + c];
+        w0s[i * 4 + 3] = 0.0f;
+        float bb = net.b0[i];
+        if (net.in_dim == 4) bb = fmaf(net.w0[i * 4 + 3], a.time, bb);
+        b0s[i] = bb;
+        wos[i] = net.wout[i];
+        for (int l = 0; l < KH; ++l) bhs[l * W + i] = net.bh[l][i];
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (tid == 0) {
+        mbar_arrive_expect_tx(bar_w, static_cast<uint32_t>(KH) * W * W * 2u * (SPLIT ? 2u : 1u));
+        for (int l = 0; l < KH; ++l)
+            for (int kb = 0; kb < W / 64; ++kb) {
+                const size_t src = static_cast<size_t>(l) * net.wbf_layer_bytes + static_cast<size_t>(kb) * net.rows_pad * 128u;
+                bulk_g2s(w_s + l * W * W * 2u + kb * W * 128u, net.wbf + src, W * 128u, bar_w);
+                if (SPLIT) bulk_g2s(wlo_s + l * W * W * 2u + kb * W * 128u, net.wbf_lo + src, W * 128u, bar_w);
+            }
+    }
+    bool ok = mbar_wait_bounded(bar_w, 0, a.status, abort_flag);
+
+    const long long n_work = a.in_list ? static_cast<long long>(*a.in_count) : a.n;
+    const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+    constexpr uint32_t idesc = idesc_f32acc(128, W, F16);
+    uint32_t mma_phase = 0;
+    Ray ray;
+
+    while (ok) {
+        refill_ray(a, ray, n_work);
+        if (!__syncthreads_or(ray.state == kSlotActive)) break;
+        if (a.cap <= 0) {
+            pass_ray(a, ray);
+            continue;
+        }
+        // layer 0 (FP32): row tid of X = 16-bit sin(W_0 p + b_0)
+        for (int k8 = 0; k8 < W / 8; ++k8) {
+            uint32_t pk[4], pl[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e0 = k8 * 8 + 2 * q, e1 = e0 + 1;
+                const float z0 = fmaf(w0s[e0 * 4 + 0], ray.px,
+                                      fmaf(w0s[e0 * 4 + 1], ray.py, fmaf(w0s[e0 * 4 + 2], ray.pz, b0s[e0])));
+                const float z1 = fmaf(w0s[e1 * 4 + 0], ray.px,
+                                      fmaf(w0s[e1 * 4 + 1], ray.py, fmaf(w0s[e1 * 4 + 2], ray.pz, b0s[e1])));
+                if (SPLIT)
+                    pack_split<F16>(sin_r(z0), sin_r(z1), pk[q], pl[q]);
+                else
+                    pk[q] = pack16x2<F16>(sin_r(z0), sin_r(z1));
+            }
+            const uint32_t off = sw128_chunk_offset(tid, k8, 128);
+            st_shared_v4(x_s + off, pk[0], pk[1], pk[2], pk[3]);
+            if (SPLIT) st_shared_v4(xlo_s + off, pl[0], pl[1], pl[2], pl[3]);
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+
+        float f = 0.0f;
+        for (int l = 0; l < KH; ++l) {
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t wl = w_s + l * W * W * 2u, wll = wlo_s + l * W * W * 2u;
+#pragma unroll
+                for (int kb = 0; kb < W / 64; ++kb)
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint32_t xo = kb * 128u * 128u + kk * 32u, wo = kb * W * 128u + kk * 32u;
+                        mma_f16kind(tmem, desc_kmajor_sw128(x_s + xo), desc_kmajor_sw128(wl + wo), idesc,
+                                    (kb | kk) != 0);
+                        if (SPLIT) {
+                            mma_f16kind(tmem, desc_kmajor_sw128(x_s + xo), desc_kmajor_sw128(wll + wo), idesc, 1u);
+                            mma_f16kind(tmem, desc_kmajor_sw128(xlo_s + xo), desc_kmajor_sw128(wl + wo), idesc, 1u);
+                        }
+                    }
+                mma_commit(bar_mma);
+            }
+            ok = mbar_wait_bounded(bar_mma, mma_phase, a.status, abort_flag);
+            mma_phase ^= 1u;
+            if (!ok) break;
+            tc_fence_after();
+            const float* bl = bhs + l * W;
+            if (l + 1 < KH) {
+                // hidden epilogue: X row = 16-bit sin(D + b)
+                for (int c0 = 0; c0 < W; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(tmem + lane_base + c0, v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        uint32_t pk[4], pl[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int j = q * 8 + 2 * e;
+                            const float s0 = sin_r(v[j] + bl[c0 + j]), s1 = sin_r(v[j + 1] + bl[c0 + j + 1]);
+                            if (SPLIT)
+                                pack_split<F16>(s0, s1, pk[e], pl[e]);
+                            else
+                                pk[e] = pack16x2<F16>(s0, s1);
+                        }
+                        const uint32_t off = sw128_chunk_offset(tid, (c0 >> 3) + q, 128);
+                        st_shared_v4(x_s + off, pk[0], pk[1], pk[2], pk[3]);
+                        if (SPLIT) st_shared_v4(xlo_s + off, pl[0], pl[1], pl[2], pl[3]);
+                    }
+                }
+                fence_proxy_async_smem();
+                tc_fence_before();
+                __syncthreads();
+            } else {
+                // output layer in FP32: f = w_out . sin(D + b) + b_out
+                float dot = 0.0f;
+                for (int c0 = 0; c0 < W; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(tmem + lane_base + c0, v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) dot = fmaf(wos[c0 + j], sin_r(v[j] + bl[c0 + j]), dot);
+                }
+                f = dot + net.bout;
+            }
+        }
+        if (!ok) break;
+        tc_fence_before();
+        step_ray(a, ray, f);
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, W);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// trace kernel, width 256 with streamed weights
+// ---------------------------------------------------------------------------
+// Same per-ray structure as trace_level_tc_kernel, for networks whose hidden
+// weights do not fit in shared memory next to the activations ((256, k >= 2)
+// is 128 KB per layer).  A producer warp streams the 64-wide K blocks of every
+// hidden layer (256 rows x 128 bytes = 32 KB) from L2 through a 3-stage ring
+// in the order the MMAs consume them, cycling over the layers for as long as
+// rays remain; thread 0 issues the MMAs as stages arrive.
+constexpr int kStreamW = 256;
+constexpr int kStreamStages = 3;
+constexpr uint32_t kStreamStageBytes = kStreamW * 128u;
+constexpr int kStreamThreads = 160;  // 128 ray threads + 1 producer warp
+
+struct StreamLayout {
+    uint32_t x, ring, w0, b0, bh, wout, bars, misc, total;
+};
+
+__host__ __device__ inline StreamLayout stream_layout(int KH) {
+    StreamLayout L;
+    uint32_t o = 0;
+    L.x = o;
+    o += 128u * kStreamW * 2u;
+    L.ring = o;
+    o += kStreamStages * kStreamStageBytes;
+    L.w0 = o;
+    o += kStreamW * 4u * 4u;
+    L.b0 = o;
+    o += kStreamW * 4u;
+    L.bh = o;
+    o += static_cast<uint32_t>(KH) * kStreamW * 4u;
+    L.wout = o;
+    o += kStreamW * 4u;
+    L.bars = o;
+    o += (2 * kStreamStages + 1) * 8u;
+    o = (o + 15u) & ~15u;
+    L.misc = o;
+    o += 32u;
+    L.total = o;
+    return L;
+}
+
+// OR-reduction barrier over the first `nthreads` threads (named barrier `id`).
+__device__ __forceinline__ bool bar_or(int id, int nthreads, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(static_cast<uint32_t>(pred)), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void bar_named(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+template <bool F16>
+__global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(const LevelArgs a) {
+    constexpr int W = kStreamW, KB = W / 64, NS = kStreamStages;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const uint32_t raw_s = smem_u32(smem_raw);
+    const uint32_t base_s = (raw_s + 1023u) & ~1023u;
+    uint8_t* base = smem_raw + (base_s - raw_s);
+    const NetView& net = a.net;
+    const int KH = net.n_hidden;
+    const StreamLayout L = stream_layout(KH);
+    float* w0s = reinterpret_cast<float*>(base + L.w0);
+    float* b0s = reinterpret_cast<float*>(base + L.b0);
+    float* bhs = reinterpret_cast<float*>(base + L.bh);
+    float* wos = reinterpret_cast<float*>(base + L.wout);
+    const uint32_t bar_full = base_s + L.bars, bar_empty = bar_full + 8u * NS, bar_mma = bar_empty + 8u * NS;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.misc);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(base + L.misc + 4);
+    volatile int* done_flag = reinterpret_cast<volatile int*>(base + L.misc + 8);
+    volatile uint32_t* consumed = reinterpret_cast<volatile uint32_t*>(base + L.misc + 12);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t x_s = base_s + L.x, ring_s = base_s + L.ring;
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(bar_full + 8u * s, 1);
+            mbar_init(bar_empty + 8u * s, 1);
+        }
+        mbar_init(bar_mma, 1);
+        *abort_flag = 0;
+        *done_flag = 0;
+        *consumed = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(smem_u32(tmem_slot), W);
+        tmem_relinquish();
+    }
+    for (int i = tid; i < W; i += kStreamThreads) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) w0s[i * 4 + c] = net.w0[i * net.in_dim + c];
+        w0s[i * 4 + 3] = 0.0f;
+        float bb = net.b0[i];
+        if (net.in_dim == 4) bb = fmaf(net.w0[i * 4 + 3], a.time, bb);
+        b0s[i] = bb;
+        wos[i] = net.wout[i];
+        for (int l = 0; l < KH; ++l) bhs[l * W + i] = net.bh[l][i];
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 4) {
+        // producer: K blocks of layer 0..KH-1 in consumption order, cyclically
+        if (lane == 0) {
+            uint32_t g = 0;
+            bool ok = true;
+            while (ok) {
+                const uint32_t stage = g % NS, use = g / NS;
+                if (use > 0) {
+                    const uint32_t bar = bar_empty + 8u * stage, par = (use - 1) & 1u;
+                    const uint64_t t0 = globaltimer_ns();
+                    bool got = false;
+                    while (!(got = mbar_try_wait(bar, par))) {
+                        if (*done_flag || *abort_flag) break;
+                        if (globaltimer_ns() - t0 > kWaitBudgetNs) {
+                            raise_status(a.status, kStatusTimeout);
+                            *abort_flag = 1;
+                            break;
+                        }
+                    }
+                    if (!got) break;
+                }
+                const uint32_t l = (g / KB) % KH, kb = g % KB;
+                mbar_arrive_expect_tx(bar_full + 8u * stage, kStreamStageBytes);
+                bulk_g2s(ring_s + stage * kStreamStageBytes,
+                         net.wbf + static_cast<size_t>(l) * net.wbf_layer_bytes +
+                             static_cast<size_t>(kb) * net.rows_pad * 128u,
+                         kStreamStageBytes, bar_full + 8u * stage);
+                ++g;
+            }
+            // every copy issued must land before the block exits
+            for (uint32_t gg = *consumed; gg < g; ++gg)
+                mbar_wait_bounded(bar_full + 8u * (gg % NS), (gg / NS) & 1u, a.status, abort_flag);
+        }
+    } else {
+        const long long n_work = a.in_list ? static_cast<long long>(*a.in_count) : a.n;
+        const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+        constexpr uint32_t idesc = idesc_f32acc(128, W, F16);
+        uint32_t mma_phase = 0, g = 0;
+        bool ok = true;
+        Ray ray;
+        while (ok) {
+            refill_ray(a, ray, n_work);
+            if (!bar_or(1, 128, ray.state == kSlotActive)) break;
+            if (a.cap <= 0) {
+                pass_ray(a, ray);
+                continue;
+            }
+            for (int k8 = 0; k8 < W / 8; ++k8) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int e0 = k8 * 8 + 2 * q, e1 = e0 + 1;
+                    const float z0 = fmaf(w0s[e0 * 4 + 0], ray.px,
+                                          fmaf(w0s[e0 * 4 + 1], ray.py, fmaf(w0s[e0 * 4 + 2], ray.pz, b0s[e0])));
+                    const float z1 = fmaf(w0s[e1 * 4 + 0], ray.px,
+                                          fmaf(w0s[e1 * 4 + 1], ray.py, fmaf(w0s[e1 * 4 + 2], ray.pz, b0s[e1])));
+                    pk[q] = pack16x2<F16>(sin_r(z0), sin_r(z1));
+                }
+                st_shared_v4(x_s + sw128_chunk_offset(tid, k8, 128), pk[0], pk[1], pk[2], pk[3]);
+            }
+            fence_proxy_async_smem();
+            tc_fence_before();
+            bar_named(1, 128);
+
+            float f = 0.0f;
+            for (int l = 0; l < KH; ++l) {
+                if (tid == 0) {
+                    tc_fence_after();
+                    for (int kb = 0; kb < KB && ok; ++kb, ++g) {
+                        const uint32_t stage = g % NS;
+                        ok = mbar_wait_bounded(bar_full + 8u * stage, (g / NS) & 1u, a.status, abort_flag);
+                        if (!ok) break;
+                        tc_fence_after();
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma_f16kind(tmem, desc_kmajor_sw128(x_s + kb * 128u * 128u + kk * 32u),
+                                        desc_kmajor_sw128(ring_s + stage * kStreamStageBytes + kk * 32u), idesc,
+                                        (kb | kk) != 0);
+                        mma_commit(bar_empty + 8u * stage);
+                    }
+                    if (ok) mma_commit(bar_mma);
+                }
+                ok = mbar_wait_bounded(bar_mma, mma_phase, a.status, abort_flag);
+                mma_phase ^= 1u;
+                if (!ok) break;
+                tc_fence_after();
+                const float* bl = bhs + l * W;
+                if (l + 1 < KH) {
+                    for (int c0 = 0; c0 < W; c0 += 32) {
+                        float v[32];
+                        tmem_ld32(tmem + lane_base + c0, v);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            uint32_t pk[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int j = q * 8 + 2 * e;
+                                pk[e] = pack16x2<F16>(sin_r(v[j] + bl[c0 + j]), sin_r(v[j + 1] + bl[c0 + j + 1]));
+                            }
+                            st_shared_v4(x_s + sw128_chunk_offset(tid, (c0 >> 3) + q, 128), pk[0], pk[1], pk[2],
+                                         pk[3]);
+                        }
+                    }
+                    fence_proxy_async_smem();
+                    tc_fence_before();
+                    bar_named(1, 128);
+                } else {
+                    float dot = 0.0f;
+                    for (int c0 = 0; c0 < W; c0 += 32) {
+                        float v[32];
+                        tmem_ld32(tmem + lane_base + c0, v);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) dot = fmaf(wos[c0 + j], sin_r(v[j] + bl[c0 + j]), dot);
+                    }
+                    f = dot + net.bout;
+                }
+            }
+            if (!ok) break;
+            tc_fence_before();
+            step_ray(a, ray, f);
+        }
+        if (tid == 0) *consumed = g;
+        bar_named(1, 128);
+        if (tid == 0) {
+            __threadfence_block();
+            *done_flag = 1;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, W);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// gradient kernel
+// ---------------------------------------------------------------------------
+template <int W>
+struct GradCfg {
+    static constexpr int MT = (W + 127) / 128;      // TMEM tiles of 128 feature rows
+    static constexpr int ROWS = MT * 128;           // feature rows incl. zero padding
+    static constexpr int KB = W / 64;               // 64-wide K blocks
+    static constexpr int NPTS = 64;                 // points per tile
+    static constexpr int NROWS = 4 * NPTS;          // point-streams = MMA N = rows of X
+    static constexpr int NS = (W == 256) ? 2 : 3;   // weight ring stages
+    static constexpr int EPI_WARPS = 4 * MT;
+    static constexpr int EPI_THREADS = EPI_WARPS * 32;
+    static constexpr int PRODUCER_WARP = EPI_WARPS;
+    static constexpr int MMA_WARP = EPI_WARPS + 1;
+    static constexpr int THREADS = (EPI_WARPS + 2) * 32;
+    static constexpr uint32_t STAGE_BYTES = ROWS * 128u;
+    static constexpr int TMEM_COLS = MT * 256;
+};
+
+struct GradLayout {
+    uint32_t x, ring, woutb, w0, b0, bh, pts, idx, bars, misc, total;
+};
+
+template <int W>
+__host__ __device__ inline GradLayout grad_layout(int KH) {
+    using C = GradCfg<W>;
+    GradLayout L;
+    uint32_t o = 0;
+    L.x = o;
+    o += C::NROWS * 128u * C::KB;
+    L.ring = o;
+    o += C::NS * C::STAGE_BYTES;
+    L.woutb = o;
+    o += C::KB * 16u * 128u;
+    L.w0 = o;
+    o += W * 4u * 4u;
+    L.b0 = o;
+    o += W * 4u;
+    L.bh = o;
+    o += static_cast<uint32_t>(KH) * W * 4u;
+    L.pts = o;
+    o += C::NPTS * 3u * 4u;
+    L.idx = o;
+    o += C::NPTS * 4u;
+    L.bars = o;
+    o += (2 * C::NS + 2) * 8u;
+    o = (o + 15u) & ~15u;
+    L.misc = o;
+    o += 32u;
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ void epi_barrier(int nthreads) {
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+template <int W, bool F16>
+__global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const GradArgs a) {
+    using C = GradCfg<W>;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const uint32_t raw_s = smem_u32(smem_raw);
+    const uint32_t base_s = (raw_s + 1023u) & ~1023u;
+    uint8_t* base = smem_raw + (base_s - raw_s);
+    const NetView& net = a.net;
+    const int KH = net.n_hidden;
+    const GradLayout L = grad_layout<W>(KH);
+    float* w0s = reinterpret_cast<float*>(base + L.w0);
+    float* b0s = reinterpret_cast<float*>(base + L.b0);
+    float* bhs = reinterpret_cast<float*>(base + L.bh);
+    float* pts = reinterpret_cast<float*>(base + L.pts);
+    int* idxs = reinterpret_cast<int*>(base + L.idx);
+    const uint32_t bar_full = base_s + L.bars;            // NS barriers
+    const uint32_t bar_empty = bar_full + 8u * C::NS;     // NS barriers
+    const uint32_t bar_xready = bar_empty + 8u * C::NS;
+    const uint32_t bar_dfull = bar_xready + 8u;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.misc);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(base + L.misc + 4);
+    long long* tile_slot = reinterpret_cast<long long*>(base + L.misc + 8);
+    const uint32_t x_s = base_s + L.x, ring_s = base_s + L.ring, wo_s = base_s + L.woutb;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        for (int s = 0; s < C::NS; ++s) {
+            mbar_init(bar_full + 8u * s, 1);
+            mbar_init(bar_empty + 8u * s, 1);
+        }
+        mbar_init(bar_xready, C::EPI_THREADS);
+        mbar_init(bar_dfull, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
+        tmem_relinquish();
+    }
+    for (int i = tid; i < W; i += C::THREADS) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) w0s[i * 4 + c] = net.w0[i * net.in_dim + c];
+        w0s[i * 4 + 3] = 0.0f;
+        float bb = net.b0[i];
+        if (net.in_dim == 4) bb = fmaf(net.w0[i * 4 + 3], a.time, bb);
+        b0s[i] = bb;
+        for (int l = 0; l < KH; ++l) bhs[l * W + i] = net.bh[l][i];
+    }
+    // w_out split into a 16-bit head (row 0) and the 16-bit rounding of its
+    // remainder (row 1) of a 16-row K-major operand (rows 2..15 zero): the
+    // output MMA then carries w_out to about 16 significant bits.
+    for (int i = tid; i < C::KB * 16 * 128 / 4; i += C::THREADS) reinterpret_cast<uint32_t*>(base + L.woutb)[i] = 0u;
+    __syncthreads();
+    for (int k = tid; k < W; k += C::THREADS) {
+        const float w = net.wout[k];
+        const uint16_t hi = bits16<F16>(w);
+        *reinterpret_cast<uint16_t*>(base + L.woutb + sw128_offset(0, k, 16)) = hi;
+        *reinterpret_cast<uint16_t*>(base + L.woutb + sw128_offset(1, k, 16)) = bits16<F16>(w - from16<F16>(hi));
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const long long n_work = a.list ? static_cast<long long>(*a.count) : a.n;
+    uint32_t g_prod = 0, g_mma = 0, xr_phase = 0, df_phase = 0;
+    bool ok = true;
+
+    while (true) {
+        if (tid == 0) *tile_slot = static_cast<long long>(atomicAdd(a.grab, 1ull));
+        const int stop = __syncthreads_or(*abort_flag != 0);
+        const long long base_pt = *tile_slot * C::NPTS;
+        if (stop || base_pt >= n_work) break;
+
+        if (warp == C::PRODUCER_WARP) {
+            if (lane == 0) {
+                for (int st = 0; st < KH * C::KB && ok; ++st, ++g_prod) {
+                    const uint32_t stage = g_prod % C::NS, use = g_prod / C::NS;
+                    if (use > 0) ok = mbar_wait_bounded(bar_empty + 8u * stage, (use - 1) & 1u, a.status, abort_flag);
+                    if (!ok) break;
+                    const int l = st / C::KB, kb = st % C::KB;
+                    mbar_arrive_expect_tx(bar_full + 8u * stage, C::STAGE_BYTES);
+                    bulk_g2s(ring_s + stage * C::STAGE_BYTES,
+                             net.wbf + static_cast<size_t>(l) * net.wbf_layer_bytes +
+                                 static_cast<size_t>(kb) * net.rows_pad * 128u,
+                             C::STAGE_BYTES, bar_full + 8u * stage);
+                }
+            }
+        } else if (warp == C::MMA_WARP) {
+            if (lane == 0) {
+                constexpr uint32_t idesc_h = idesc_f32acc(128, 256, F16);
+                constexpr uint32_t idesc_o = idesc_f32acc(128, 16, F16);
+                for (int l = 0; l <= KH && ok; ++l) {
+                    ok = mbar_wait_bounded(bar_xready, xr_phase, a.status, abort_flag);
+                    xr_phase ^= 1u;
+                    if (!ok) break;
+                    tc_fence_after();
+                    if (l < KH) {
+                        // D[mt] = W_l[mt rows] . X^T over all K blocks
+                        for (int kb = 0; kb < C::KB && ok; ++kb, ++g_mma) {
+                            const uint32_t stage = g_mma % C::NS, use = g_mma / C::NS;
+                            ok = mbar_wait_bounded(bar_full + 8u * stage, use & 1u, a.status, abort_flag);
+                            if (!ok) break;
+                            tc_fence_after();
+#pragma unroll
+                            for (int mt = 0; mt < C::MT; ++mt)
+#pragma unroll
+                                for (int kk = 0; kk < 4; ++kk)
+                                    mma_f16kind(tmem + mt * 256u,
+                                             desc_kmajor_sw128(ring_s + stage * C::STAGE_BYTES + mt * 128u * 128u + kk * 32u),
+                                             desc_kmajor_sw128(x_s + kb * C::NROWS * 128u + kk * 32u), idesc_h,
+                                             (kb | kk) != 0);
+                            mma_commit(bar_empty + 8u * stage);
+                        }
+                        if (ok) mma_commit(bar_dfull);
+                    } else {
+                        // output layer: D_out[h] (columns 16h) = X[128h .. 128h+127] . w_out^T
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+                            for (int kb = 0; kb < C::KB; ++kb)
+#pragma unroll
+                                for (int kk = 0; kk < 4; ++kk)
+                                    mma_f16kind(tmem + 16u * h,
+                                             desc_kmajor_sw128(x_s + kb * C::NROWS * 128u + h * 128u * 128u + kk * 32u),
+                                             desc_kmajor_sw128(wo_s + kb * 16u * 128u + kk * 32u), idesc_o,
+                                             (kb | kk) != 0);
+                        mma_commit(bar_dfull);
+                    }
+                }
+            }
+        } else {
+            // epilogue warps: thread <-> feature row m of TMEM tile mt
+            const int mt = warp >> 2, quad = warp & 3;
+            const int m = mt * 128 + quad * 32 + lane;
+            const uint32_t lane_addr = tmem + (static_cast<uint32_t>(quad * 32) << 16) + mt * 256u;
+            if (tid < C::NPTS) {
+                const long long k = base_pt + tid;
+                int i = -1;
+                if (k < n_work) i = a.list ? a.list[k] : static_cast<int>(k);
+                idxs[tid] = i;
+                pts[tid * 3 + 0] = i >= 0 ? a.pts[i] : 0.0f;
+                pts[tid * 3 + 1] = i >= 0 ? a.pts[a.n + i] : 0.0f;
+                pts[tid * 3 + 2] = i >= 0 ? a.pts[2 * a.n + i] : 0.0f;
+            }
+            epi_barrier(C::EPI_THREADS);
+            // input layer: P_0 = sin(A_0), G_0^c = W_0[:, c] (.) cos(A_0)
+            if (m < W) {
+                const float wx = w0s[m * 4 + 0], wy = w0s[m * 4 + 1], wz = w0s[m * 4 + 2], bb = b0s[m];
+                for (int p = 0; p < C::NPTS; ++p) {
+                    const float z = fmaf(wx, pts[p * 3 + 0], fmaf(wy, pts[p * 3 + 1], fmaf(wz, pts[p * 3 + 2], bb)));
+                    float s, c;
+                    sincos_r(z, &s, &c);
+                    st_shared_u16(x_s + sw128_offset(p * 4 + 0, m, C::NROWS), bits16<F16>(s));
+                    st_shared_u16(x_s + sw128_offset(p * 4 + 1, m, C::NROWS), bits16<F16>(wx * c));
+                    st_shared_u16(x_s + sw128_offset(p * 4 + 2, m, C::NROWS), bits16<F16>(wy * c));
+                    st_shared_u16(x_s + sw128_offset(p * 4 + 3, m, C::NROWS), bits16<F16>(wz * c));
+                }
+            }
+            fence_proxy_async_smem();
+            tc_fence_before();
+            mbar_arrive(bar_xready);
+
+            for (int l = 0; l < KH && ok; ++l) {
+                ok = mbar_wait_bounded(bar_dfull, df_phase, a.status, abort_flag);
+                df_phase ^= 1u;
+                if (!ok) break;
+                tc_fence_after();
+                const float bb = m < W ? bhs[l * W + m] : 0.0f;
+                for (int q = 0; q < C::NROWS / 32; ++q) {
+                    float v[32];
+                    tmem_ld32(lane_addr + q * 32u, v);
+                    tmem_wait_ld();
+                    if (m < W) {
+#pragma unroll
+                        for (int pp = 0; pp < 8; ++pp) {
+                            // P_i = sin(A_i);  G_i = (W_i G_{i-1}) (.) cos(A_i)
+                            const int p = q * 8 + pp;
+                            float s, c;
+                            sincos_r(v[pp * 4] + bb, &s, &c);
+                            st_shared_u16(x_s + sw128_offset(p * 4 + 0, m, C::NROWS), bits16<F16>(s));
+                            st_shared_u16(x_s + sw128_offset(p * 4 + 1, m, C::NROWS), bits16<F16>(c * v[pp * 4 + 1]));
+                            st_shared_u16(x_s + sw128_offset(p * 4 + 2, m, C::NROWS), bits16<F16>(c * v[pp * 4 + 2]));
+                            st_shared_u16(x_s + sw128_offset(p * 4 + 3, m, C::NROWS), bits16<F16>(c * v[pp * 4 + 3]));
+                        }
+                    }
+                }
+                fence_proxy_async_smem();
+                tc_fence_before();
+                mbar_arrive(bar_xready);
+            }
+            if (ok) ok = mbar_wait_bounded(bar_dfull, df_phase, a.status, abort_flag);
+            df_phase ^= 1u;
+            if (ok && mt == 0) {
+                tc_fence_after();
+                float v[32];
+                tmem_ld32(tmem + (static_cast<uint32_t>(quad * 32) << 16), v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    // row n = 128h + 32quad + lane = 4 * point + stream; head + remainder of w_out
+                    const float val = v[16 * h] + v[16 * h + 1];
+                    const int g = lane & ~3;
+                    const float gx = __shfl_sync(0xffffffffu, val, g + 1);
+                    const float gy = __shfl_sync(0xffffffffu, val, g + 2);
+                    const float gz = __shfl_sync(0xffffffffu, val, g + 3);
+                    const int p = (128 * h + 32 * quad + lane) >> 2;
+                    if ((lane & 3) == 0) {
+                        const int i = idxs[p];
+                        if (i >= 0) {
+                            float ox = gx, oy = gy, oz = gz;
+                            if (a.normalize) {
+                                const float len = sqrtf(gx * gx + gy * gy + gz * gz);
+                                const float inv = len >= 1e-12f ? 1.0f / len : 0.0f;
+                                ox *= inv;
+                                oy *= inv;
+                                oz *= inv;
+                            }
+                            a.out[i] = ox;
+                            a.out[a.n + i] = oy;
+                            a.out[2 * a.n + i] = oz;
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+        }
+        __syncthreads();
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, C::TMEM_COLS);
+    }
+}
+
+template <class Kernel>
+cudaError_t launch_tc(Kernel k, int threads, size_t smem, int tmem_cols, int num_sms, cudaStream_t s,
+                      const void* arg) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int tmem_cap = 512 / tmem_cols;
+    if (per_sm > tmem_cap) per_sm = tmem_cap;
+    void* args[] = {const_cast<void*>(arg)};
+    return cudaLaunchKernel(reinterpret_cast<const void*>(k), dim3(num_sms * per_sm), dim3(threads), args, smem, s);
+}
+
+}  // namespace
+
+bool tc_trace_supported(int width, int n_hidden) {
+    return n_hidden >= 1 && n_hidden <= kMaxHidden && (width == 64 || width == 128 || width == 256);
+}
+
+bool tc_grad_supported(int width, int n_hidden) {
+    return n_hidden >= 1 && n_hidden <= kMaxHidden && (width == 64 || width == 128 || width == 256);
+}
+
+template <int W, bool F16>
+static cudaError_t launch_trace_resident(const LevelArgs& a, int num_sms, cudaStream_t s) {
+    const int KH = a.net.n_hidden;
+    const bool split = a.net.wbf_lo != nullptr && trace_split(W, KH);
+    const size_t smem = trace_layout(W, KH, split).total + 1024;
+    if (split) return launch_tc(trace_level_tc_kernel<W, F16, true>, kTraceThreads, smem, W, num_sms, s, &a);
+    return launch_tc(trace_level_tc_kernel<W, F16, false>, kTraceThreads, smem, W, num_sms, s, &a);
+}
+
+cudaError_t launch_trace_level_tc(const LevelArgs& a, int num_sms, cudaStream_t s) {
+    const bool f16 = a.net.op_f16 != 0;
+    switch (a.net.width) {
+    case 64:
+        return f16 ? launch_trace_resident<64, true>(a, num_sms, s) : launch_trace_resident<64, false>(a, num_sms, s);
+    case 128:
+        return f16 ? launch_trace_resident<128, true>(a, num_sms, s) : launch_trace_resident<128, false>(a, num_sms, s);
+    case 256:
+        if (a.net.n_hidden == 1)
+            return f16 ? launch_trace_resident<256, true>(a, num_sms, s)
+                       : launch_trace_resident<256, false>(a, num_sms, s);
+        {
+            const size_t ssm = stream_layout(a.net.n_hidden).total + 1024;
+            return f16 ? launch_tc(trace_level_tc_stream_kernel<true>, kStreamThreads, ssm, 256, num_sms, s, &a)
+                       : launch_tc(trace_level_tc_stream_kernel<false>, kStreamThreads, ssm, 256, num_sms, s, &a);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+bool tc_trace_split(int width, int n_hidden) { return width <= 128 && trace_split(width, n_hidden); }
+
+template <int W>
+static cudaError_t launch_grad_w(const GradArgs& a, int num_sms, cudaStream_t s) {
+    const size_t smem = grad_layout<W>(a.net.n_hidden).total + 1024;
+    if (a.net.op_f16)
+        return launch_tc(grad_tc_kernel<W, true>, GradCfg<W>::THREADS, smem, GradCfg<W>::TMEM_COLS, num_sms, s, &a);
+    return launch_tc(grad_tc_kernel<W, false>, GradCfg<W>::THREADS, smem, GradCfg<W>::TMEM_COLS, num_sms, s, &a);
+}
+
+cudaError_t launch_grad_tc(const GradArgs& a, int num_sms, cudaStream_t s) {
+    switch (a.net.width) {
+    case 64:
+        return launch_grad_w<64>(a, num_sms, s);
+    case 128:
+        return launch_grad_w<128>(a, num_sms, s);
+    case 256:
+        return launch_grad_w<256>(a, num_sms, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace sdfnn

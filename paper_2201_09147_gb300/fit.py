@@ -1,0 +1,162 @@
+"""Offline bootstrap fitter for the nested SIREN sequences (input generator).
+
+Produces the trained sine MLPs that the multiscale tracer consumes.  The
+paper trains its networks with an external framework it only cites (Sec. 2,
+Sec. 3.3); this stand-in fits each network of a sequence independently to the
+seeded analytic scene of ``inputs.sphere_scene`` with plain PyTorch autograd:
+
+    loss = mean |f(x) - g(x)|                         (SDF values)
+         + lam_n * mean (1 - cos(grad f(x), grad g(x)))  (normals, near surface)
+         + lam_e * mean | |grad f(x)| - 1 |              (Eikonal)
+
+on a batch that is half near-surface (sphere-surface points plus N(0, 0.02)
+jitter) and half uniform in [-1, 1]^3.  Networks are stored unfolded (SIREN
+parametrisation, omega0 = omega = 30) in SDFN files.
+
+The thresholds of the sequence then follow Prop. 2 (Sec. 3.3) with the
+infinity norm estimated as the maximum over sampled points, as the paper
+prescribes; that estimate lives in the tests (it needs the oracle).
+
+This module is not on the rendering path: nothing in the CUDA library or its
+binding imports it.  Usage:
+
+    python -m paper_2201_09147_gb300.fit --out paper_2201_09147_gb300/scenes
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+from pathlib import Path
+
+import numpy as np
+import torch
+
+from . import inputs
+
+SCENES_DIR = Path(__file__).resolve().parent / "scenes"
+
+# name -> (width, n_hidden, steps)
+SEQUENCE_NETS = {
+    "s8_64x1": (64, 1, 3000),
+    "s8_64x2": (64, 2, 3000),
+    "s8_128x2": (128, 2, 3000),
+    "s8_256x2": (256, 2, 3000),
+    "s8_256x3": (256, 3, 3000),
+}
+
+
+class Siren(torch.nn.Module):
+    def __init__(self, net: inputs.SineNet):
+        super().__init__()
+        self.omega0, self.omega = net.omega0, net.omega
+        self.layers = torch.nn.ModuleList()
+        for w, b in zip(net.weights, net.biases):
+            lin = torch.nn.Linear(w.shape[1], w.shape[0])
+            with torch.no_grad():
+                lin.weight.copy_(torch.from_numpy(np.asarray(w, np.float32)))
+                lin.bias.copy_(torch.from_numpy(np.asarray(b, np.float32)))
+            self.layers.append(lin)
+
+    def forward(self, x):
+        n = len(self.layers)
+        for i, lin in enumerate(self.layers):
+            x = lin(x)
+            if i < n - 1:
+                x = torch.sin((self.omega0 if i == 0 else self.omega) * x)
+        return x[..., 0]
+
+    def to_sinenet(self, template: inputs.SineNet) -> inputs.SineNet:
+        ws = [lin.weight.detach().cpu().numpy().astype(np.float32) for lin in self.layers]
+        bs = [lin.bias.detach().cpu().numpy().astype(np.float32) for lin in self.layers]
+        return inputs.SineNet(template.in_dim, template.width, template.n_hidden, template.omega0,
+                              template.omega, ws, bs, folded=False)
+
+
+def scene_torch(scene: inputs.SphereScene, p: torch.Tensor):
+    """Analytic scene value and gradient (torch, float32)."""
+    c = torch.as_tensor(scene.centres, dtype=p.dtype, device=p.device)
+    r = torch.as_tensor(scene.radii, dtype=p.dtype, device=p.device)
+    diff = p[:, None, :] - c[None]
+    dist = diff.norm(dim=-1)
+    d = dist - r[None]
+    dmin, arg = d.min(dim=1)
+    nrm = diff[torch.arange(p.shape[0]), arg] / dist[torch.arange(p.shape[0]), arg, None].clamp_min(1e-12)
+    a, fr = scene.amp, scene.freq
+    sx, sy, sz = torch.sin(fr * p[:, 0]), torch.sin(fr * p[:, 1]), torch.sin(fr * p[:, 2])
+    cx, cy, cz = torch.cos(fr * p[:, 0]), torch.cos(fr * p[:, 1]), torch.cos(fr * p[:, 2])
+    val = dmin + a * sx * sy * sz
+    grad = nrm + a * fr * torch.stack([cx * sy * sz, sx * cy * sz, sx * sy * cz], dim=1)
+    return val, grad
+
+
+def sample_batch(scene: inputs.SphereScene, gen: torch.Generator, n: int):
+    half = n // 2
+    k = torch.randint(0, len(scene.radii), (half,), generator=gen)
+    u = torch.randn(half, 3, generator=gen)
+    u = u / u.norm(dim=1, keepdim=True)
+    c = torch.as_tensor(scene.centres, dtype=torch.float32)[k]
+    r = torch.as_tensor(scene.radii, dtype=torch.float32)[k]
+    near = c + r[:, None] * u + 0.02 * torch.randn(half, 3, generator=gen)
+    near = near.clamp(-1.0, 1.0)
+    unif = torch.rand(n - half, 3, generator=gen) * 2.0 - 1.0
+    return torch.cat([near, unif], dim=0), half
+
+
+def fit_net(scene, width, n_hidden, steps, seed=0, batch=1 << 14, lr=1e-4, lam_n=0.1, lam_e=0.05,
+            device="cpu", log_every=500):
+    torch.manual_seed(seed)
+    gen = torch.Generator().manual_seed(seed)
+    template = inputs.siren_init(seed, width, n_hidden)
+    model = Siren(template).to(device)
+    opt = torch.optim.Adam(model.parameters(), lr=lr)
+    sched = torch.optim.lr_scheduler.CosineAnnealingLR(opt, T_max=steps, eta_min=lr * 0.05)
+    t0 = time.time()
+    for it in range(steps):
+        x, half = sample_batch(scene, gen, batch)
+        x = x.to(device).requires_grad_(True)
+        gv, gg = scene_torch(scene, x.detach())
+        f = model(x)
+        (df,) = torch.autograd.grad(f.sum(), x, create_graph=True)
+        l_val = (f - gv).abs().mean()
+        cos = torch.nn.functional.cosine_similarity(df[:half], gg[:half], dim=1)
+        l_n = (1.0 - cos).mean()
+        l_e = (df.norm(dim=1) - 1.0).abs().mean()
+        loss = l_val + lam_n * l_n + lam_e * l_e
+        opt.zero_grad(set_to_none=True)
+        loss.backward()
+        opt.step()
+        sched.step()
+        if log_every and (it % log_every == 0 or it == steps - 1):
+            print(f"  ({width},{n_hidden}) it {it:5d} loss {loss.item():.5f} val {l_val.item():.5f} "
+                  f"n {l_n.item():.4f} eik {l_e.item():.4f}  {time.time() - t0:.0f}s", flush=True)
+    return model.cpu().to_sinenet(template)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=str(SCENES_DIR))
+    ap.add_argument("--nets", default=",".join(SEQUENCE_NETS))
+    ap.add_argument("--steps", type=int, default=0, help="override the step count")
+    ap.add_argument("--device", default="cpu")
+    ap.add_argument("--threads", type=int, default=0)
+    args = ap.parse_args()
+    if args.threads:
+        torch.set_num_threads(args.threads)
+    out = Path(args.out)
+    out.mkdir(parents=True, exist_ok=True)
+    scene = inputs.sphere_scene(seed=1)
+    meta = {}
+    for name in args.nets.split(","):
+        w, k, steps = SEQUENCE_NETS[name]
+        steps = args.steps or steps
+        print(f"fitting {name}: ({w},{k}) {steps} steps", flush=True)
+        net = fit_net(scene, w, k, steps, device=args.device)
+        inputs.write_net(out / f"{name}.sdfn", net)
+        meta[name] = {"width": w, "n_hidden": k, "steps": steps, "seed": 0, "scene_seed": 1}
+    (out / "fit_meta.json").write_text(json.dumps(meta, indent=1) + "\n")
+
+
+if __name__ == "__main__":
+    main()

@@ -293,32 +293,33 @@ def sphere_scene(seed: int = 1, m: int = 8, time: float | None = None) -> Sphere
 # --------------------------------------------------------------------------
 
 def icosphere(subdivisions: int) -> np.ndarray:
-    """Unit icosphere vertices (float64, (V, 3)), V = 10 * 4^s + 2."""
+    """Unit icosphere vertices (float64, (V, 3)), V = 10 * 4^s + 2.
+
+    Each subdivision splits every triangle into four through its edge
+    midpoints (shared between neighbours) projected onto the unit sphere.
+    """
     t = (1.0 + math.sqrt(5.0)) / 2.0
-    verts = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
-             (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
-    faces = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2),
-             (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5), (2, 4, 11),
-             (6, 2, 10), (8, 6, 7), (9, 8, 1)]
-    v = [np.array(p, np.float64) / np.linalg.norm(p) for p in verts]
-    f = np.array(faces, np.int64)
+    verts = np.array([(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t),
+                      (0, 1, -t), (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)], np.float64)
+    faces = np.array([(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4),
+                      (11, 10, 2), (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9),
+                      (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)], np.int64)
+    verts /= np.linalg.norm(verts, axis=1, keepdims=True)
     for _ in range(subdivisions):
-        cache = {}
-        new_faces = []
-
-        def mid(a, b):
-            key = (a, b) if a < b else (b, a)
-            if key not in cache:
-                m = v[a] + v[b]
-                v.append(m / np.linalg.norm(m))
-                cache[key] = len(v) - 1
-            return cache[key]
-
-        for a, b, c in f:
-            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
-            new_faces += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
-        f = np.array(new_faces, np.int64)
-    return np.array(v)
+        nv = verts.shape[0]
+        edges = np.concatenate([faces[:, [0, 1]], faces[:, [1, 2]], faces[:, [2, 0]]])
+        key = np.minimum(edges[:, 0], edges[:, 1]) * nv + np.maximum(edges[:, 0], edges[:, 1])
+        uniq, inv = np.unique(key, return_inverse=True)
+        a, b = uniq // nv, uniq % nv
+        mids = verts[a] + verts[b]
+        mids /= np.linalg.norm(mids, axis=1, keepdims=True)
+        mid = (nv + inv).reshape(3, -1)  # midpoint index of edges (v0v1, v1v2, v2v0) per face
+        ab, bc, ca = mid[0], mid[1], mid[2]
+        f0, f1, f2 = faces[:, 0], faces[:, 1], faces[:, 2]
+        faces = np.concatenate([np.stack([f0, ab, ca], 1), np.stack([f1, bc, ab], 1), np.stack([f2, ca, bc], 1),
+                                np.stack([ab, bc, ca], 1)])
+        verts = np.concatenate([verts, mids])
+    return verts
 
 
 def displaced_icosphere(scene: SphereScene, subdivisions: int = 7, r_start: float = 1.8,
@@ -328,18 +329,36 @@ def displaced_icosphere(scene: SphereScene, subdivisions: int = 7, r_start: floa
     For each unit vertex u, g(r u) is sampled from r_start inwards with step
     `step`; the first sign change is refined by bisection in float64.  Where
     no sign change exists the vertex stays at r = 1.  Returns SoA float32
-    (3, V) and the fraction of vertices that found a root.
+    (3, V) and the fraction of vertices that found a root.  Samples beyond the
+    scene's bounding radius (max |c_i| + r_i + amp) are skipped: g > 0 there.
     """
     u = icosphere(subdivisions)
     n = u.shape[0]
     r_hit = np.full(n, np.nan)
-    radii = np.arange(r_start, r_end - 1e-12, -step)
-    prev = scene.g(u * radii[0])
+    bound = float(np.max(np.linalg.norm(scene.centres, axis=1) + scene.radii)) + scene.amp
+    k0 = max(0, int(np.floor((r_start - bound) / step)) - 1)
+    radii = r_start - step * np.arange(k0, int(np.ceil((r_start - r_end) / step)) + 1)
+    # g(r u) along each radial line: |r u - c_i|^2 = r^2 - 2 r (u . c_i) + |c_i|^2
+    uc = u @ scene.centres.T
+    cc = np.sum(scene.centres ** 2, axis=1)
+
+    def g_radial(sel, r):
+        """Sign-exact g(r u): the displacement (|.| <= amp) is added only where it can flip the sign."""
+        d = (np.sqrt(np.maximum(r * r - 2.0 * r * uc[sel] + cc[None, :], 0.0)) - scene.radii[None, :]).min(axis=1)
+        near = d <= scene.amp
+        if near.any():
+            us = u[sel[near]]
+            d[near] += scene.amp * np.sin(scene.freq * r * us[:, 0]) * np.sin(scene.freq * r * us[:, 1]) * \
+                np.sin(scene.freq * r * us[:, 2])
+        return d
+
+    active = np.arange(n)
+    prev = g_radial(active, radii[0])
     for r in radii[1:]:
-        cur = scene.g(u * r)
-        newly = np.isnan(r_hit) & (np.sign(cur) != np.sign(prev)) & (prev > 0)
+        cur = g_radial(active, r)
+        newly = (cur <= 0) & (prev > 0)
         if newly.any():
-            idx = np.nonzero(newly)[0]
+            idx = active[newly]
             lo = np.full(idx.size, r)          # g(lo) <= 0
             hi = np.full(idx.size, r + step)   # g(hi) > 0
             for _ in range(60):
@@ -349,8 +368,11 @@ def displaced_icosphere(scene: SphereScene, subdivisions: int = 7, r_start: floa
                 lo = np.where(inside, m, lo)
                 hi = np.where(inside, hi, m)
             r_hit[idx] = 0.5 * (lo + hi)
-        prev = cur
-        if not np.isnan(r_hit).any():
+            keep = ~newly
+            active, prev = active[keep], cur[keep]
+        else:
+            prev = cur
+        if active.size == 0:
             break
     found = ~np.isnan(r_hit)
     r_hit[~found] = 1.0

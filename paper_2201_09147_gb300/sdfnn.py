@@ -1,0 +1,175 @@
+"""Thin Python binding of libsdfnn (argument marshalling only).
+
+Every computation runs in the CUDA library; this module converts torch
+tensors into device pointers and the current CUDA stream into a
+cudaStream_t.  Importing it does not need a GPU; calling it does, and it
+fails loudly (SdfError / RuntimeError) when the library is not built.
+The C entry points are declared in include/sdfnn.h.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import torch
+
+from .build import lib_path
+
+SDF_FP32, SDF_BF16, SDF_FP8, SDF_FP16 = 0, 1, 2, 3
+SDF_OK = 0
+ERRORS = {-1: "SDF_ERR_ARG", -2: "SDF_ERR_FILE", -3: "SDF_ERR_FORMAT", -4: "SDF_ERR_CUDA",
+          -5: "SDF_ERR_NONFINITE", -6: "SDF_ERR_TIMEOUT", -7: "SDF_ERR_UNSUPPORTED"}
+
+EXPORTS = ["sdf_net_load", "sdf_net_load_mem", "sdf_net_info", "sdf_net_set_time", "sdf_net_free",
+           "sdf_trace_multiscale", "sdf_normals", "sdf_normal_map", "sdf_render_host", "sdf_sync_status",
+           "sdf_last_error"]
+
+
+class SdfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class TraceParamsC(C.Structure):
+    _fields_ = [("n_levels", C.c_int), ("nets", C.POINTER(C.c_void_p)), ("delta", C.POINTER(C.c_float)),
+                ("max_iters", C.POINTER(C.c_int)), ("eps", C.c_float), ("step_scale", C.POINTER(C.c_float)),
+                ("box_min", C.c_float), ("box_max", C.c_float), ("final_mode", C.c_int), ("time", C.c_float)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libsdfnn (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        p = lib_path()
+        if not p.exists():
+            raise RuntimeError(f"libsdfnn is not built ({p}); run paper_2201_09147_gb300.build.build()")
+        L = C.CDLL(str(p))
+        vp = C.c_void_p
+        L.sdf_net_load.argtypes = [C.c_char_p, C.c_int, C.c_int, C.POINTER(vp)]
+        L.sdf_net_load_mem.argtypes = [C.c_char_p, C.c_size_t, C.c_int, C.c_int, C.POINTER(vp)]
+        L.sdf_net_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_double)]
+        L.sdf_net_set_time.argtypes = [vp, C.c_float]
+        L.sdf_net_free.argtypes = [vp]
+        L.sdf_net_free.restype = None
+        L.sdf_trace_multiscale.argtypes = [C.POINTER(TraceParamsC), vp, vp, C.c_int64, vp, vp, vp, vp, vp]
+        L.sdf_normals.argtypes = [vp, vp, C.c_int64, vp, vp]
+        L.sdf_normal_map.argtypes = [vp, vp, vp, C.c_int64, vp, vp]
+        L.sdf_render_host.argtypes = [C.POINTER(TraceParamsC), vp, vp, vp, C.c_int64, vp, vp, vp, vp]
+        L.sdf_sync_status.argtypes = [vp]
+        L.sdf_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != SDF_OK:
+        raise SdfError(rc, lib().sdf_last_error().decode(errors="replace"))
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Net:
+    """A network loaded into the library (sdf_net_load / sdf_net_load_mem)."""
+
+    def __init__(self, source, precision: int = SDF_BF16, device: int = 0):
+        h = C.c_void_p()
+        if isinstance(source, (bytes, bytearray)):
+            _check(lib().sdf_net_load_mem(bytes(source), len(source), precision, device, C.byref(h)))
+        else:
+            _check(lib().sdf_net_load(str(Path(source)).encode(), precision, device, C.byref(h)))
+        self.handle = h
+        self.precision = precision
+        self.device = device
+        a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_double()
+        _check(lib().sdf_net_info(h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
+        self.in_dim, self.width, self.n_hidden, self.lipschitz = a.value, b.value, c.value, d.value
+
+    def set_time(self, t: float):
+        _check(lib().sdf_net_set_time(self.handle, float(t)))
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().sdf_net_free(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_params(nets, delta, max_iters, eps, step_scale=None, box=(-1.0, 1.0), final_mode=0, time=0.0):
+    """Builds sdf_trace_params; returns (struct, keep-alive tuple)."""
+    m = len(nets)
+    hs = (C.c_void_p * m)(*[n.handle.value for n in nets])
+    d = (C.c_float * m)(*[float(x) for x in delta])
+    it = (C.c_int * m)(*[int(x) for x in max_iters])
+    ss = None if step_scale is None else (C.c_float * m)(*[float(x) for x in step_scale])
+    p = TraceParamsC(m, C.cast(hs, C.POINTER(C.c_void_p)), C.cast(d, C.POINTER(C.c_float)),
+                     C.cast(it, C.POINTER(C.c_int)), float(eps),
+                     None if ss is None else C.cast(ss, C.POINTER(C.c_float)), float(box[0]), float(box[1]),
+                     int(final_mode), float(time))
+    return p, (hs, d, it, ss, nets)
+
+
+def trace_multiscale(nets, delta, max_iters, eps, orig, dirs, *, step_scale=None, box=(-1.0, 1.0), final_mode=0,
+                     time=0.0, out_pos=None, out_t=None, out_hit=None, out_iters=None, want_iters=True,
+                     stream=None):
+    """Alg. 1 on device rays orig/dirs (float32, shape (3, n)); returns (pos, t, hit, iters)."""
+    n = orig.shape[1]
+    dev = orig.device
+    out_pos = torch.empty((3, n), dtype=torch.float32, device=dev) if out_pos is None else out_pos
+    out_t = torch.empty(n, dtype=torch.float32, device=dev) if out_t is None else out_t
+    out_hit = torch.empty(n, dtype=torch.uint8, device=dev) if out_hit is None else out_hit
+    if out_iters is None and want_iters:
+        out_iters = torch.empty(n, dtype=torch.uint16, device=dev)
+    p, keep = make_params(nets, delta, max_iters, eps, step_scale, box, final_mode, time)
+    _check(lib().sdf_trace_multiscale(C.byref(p), _ptr(orig), _ptr(dirs), n, _ptr(out_pos), _ptr(out_t),
+                                      _ptr(out_hit), _ptr(out_iters), C.c_void_p(_stream(stream))))
+    del keep
+    return out_pos, out_t, out_hit, out_iters
+
+
+def normals(net: Net, pts, out=None, stream=None):
+    """Unnormalised analytic gradients (Alg. 2) at device points (3, n)."""
+    n = pts.shape[1]
+    out = torch.empty((3, n), dtype=torch.float32, device=pts.device) if out is None else out
+    _check(lib().sdf_normals(net.handle, _ptr(pts), n, _ptr(out), C.c_void_p(_stream(stream))))
+    return out
+
+
+def normal_map(net: Net, pts, mask=None, out=None, stream=None):
+    """Unit normals of `net` at device points (3, n) where mask != 0 (Sec. 5)."""
+    n = pts.shape[1]
+    out = torch.empty((3, n), dtype=torch.float32, device=pts.device) if out is None else out
+    _check(lib().sdf_normal_map(net.handle, _ptr(pts), _ptr(mask), n, _ptr(out), C.c_void_p(_stream(stream))))
+    return out
+
+
+def render_host(nets, delta, max_iters, eps, fine: Net, orig, dirs, out_pos, out_hit, out_normal, *,
+                step_scale=None, box=(-1.0, 1.0), final_mode=0, time=0.0, stream=None):
+    """One frame from host (CPU, ideally pinned) tensors through sdf_render_host."""
+    n = orig.shape[1]
+    p, keep = make_params(nets, delta, max_iters, eps, step_scale, box, final_mode, time)
+    _check(lib().sdf_render_host(C.byref(p), fine.handle, _ptr(orig), _ptr(dirs), n, _ptr(out_pos), _ptr(out_hit),
+                                 _ptr(out_normal), C.c_void_p(_stream(stream))))
+    del keep
+
+
+def sync_status(stream=None):
+    """Synchronises the stream and raises on a device-side error (SDF_ERR_TIMEOUT)."""
+    _check(lib().sdf_sync_status(C.c_void_p(_stream(stream))))

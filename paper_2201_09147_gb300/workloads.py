@@ -1,0 +1,92 @@
+"""Named synthetic workloads (input recipes shared by tests and the benchmark).
+
+Each workload fixes the networks, Alg. 1 parameters and rays; nothing here
+evaluates a network.  The fitted sequences live in ``scenes/`` (written by
+``fit.py`` from the seeded sphere scene of ``inputs.sphere_scene``).
+
+* ``random_siren_64x1`` - one random SIREN (64, 1), seed 0, traced with the
+  Lipschitz step 1/L at 128 x 128, 32 steps, eps 1e-3, normals at the hits.
+  SIREN's output initialisation keeps |f| below 0.1, so the printed +0.3
+  shift alone leaves f > 0 everywhere; the output row is drawn at the
+  fan-in scale U(+-sqrt(6/w)) (the linear output layer carries no omega)
+  and 0.3 is added to its bias, which gives a non-empty zero set.
+* ``nested_3level_512`` - (64,2) |> (128,2) |> (256,2) fitted to the scene,
+  delta = 0.04 / 0.015 / 0.005, caps 48 / 32 / 16, 512 x 512 rays, normals
+  of the finest net at the hits.
+* ``normal_map_1080p`` - trace the coarse (64,1) until f <= delta_0 + eps
+  (final_mode 1, delta_0 = 0.04, cap 40) at 1920 x 1080, then map the
+  normals of the fine (256,3) onto the end points (Sec. 5).  Its plain
+  comparison is the (256,3) alone, 40 steps, with its own normals.
+* ``mesh_normals`` - vertices of a subdivision-7 icosphere moved onto the
+  scene's zero set, normal-mapped with the fine (256,3).
+"""
+from __future__ import annotations
+
+import dataclasses
+from pathlib import Path
+
+from . import inputs
+
+SCENES = Path(__file__).resolve().parent / "scenes"
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    levels: list          # network file names (scenes/) or SineNet objects
+    delta: list
+    caps: list
+    eps: float
+    step_scale: list | None  # None: 1/L per level
+    final_mode: int
+    width: int
+    height: int
+    fine: object          # network used for the normals / normal mapping
+
+    def level_bytes(self):
+        return [_net_bytes(x) for x in self.levels]
+
+    def fine_bytes(self):
+        return _net_bytes(self.fine)
+
+    def rays(self, rows=None):
+        return inputs.camera_rays(self.width, self.height, rows=rows)
+
+    @property
+    def n_rays(self) -> int:
+        return self.width * self.height
+
+
+def _net_bytes(x) -> bytes:
+    if isinstance(x, inputs.SineNet):
+        return inputs.net_to_bytes(x)
+    return (SCENES / x).read_bytes()
+
+
+def random_siren_64x1() -> inputs.SineNet:
+    return inputs.siren_init(0, 64, 1, out_scale=30.0, out_shift=0.3)
+
+
+def get(name: str, width: int | None = None, height: int | None = None) -> Workload:
+    if name == "random_siren_64x1":
+        net = random_siren_64x1()
+        w = Workload(name, [net], [0.0], [32], 1e-3, None, 0, 128, 128, net)
+    elif name == "nested_3level_512":
+        w = Workload(name, ["s8_64x2.sdfn", "s8_128x2.sdfn", "s8_256x2.sdfn"], [0.04, 0.015, 0.005], [48, 32, 16],
+                     1e-3, [1.0, 1.0, 1.0], 0, 512, 512, "s8_256x2.sdfn")
+    elif name == "normal_map_1080p":
+        w = Workload(name, ["s8_64x1.sdfn"], [0.04], [40], 1e-3, [1.0], 1, 1920, 1080, "s8_256x3.sdfn")
+    elif name == "plain_256x3_1080p":
+        w = Workload(name, ["s8_256x3.sdfn"], [0.0], [40], 1e-3, [1.0], 0, 1920, 1080, "s8_256x3.sdfn")
+    else:
+        raise KeyError(name)
+    if width:
+        w.width = width
+    if height:
+        w.height = height
+    return w
+
+
+def mesh_points(subdivisions: int = 7):
+    """Displaced icosphere vertices (3, V) float32 and the fraction placed on the zero set."""
+    return inputs.displaced_icosphere(inputs.sphere_scene(seed=1), subdivisions=subdivisions)

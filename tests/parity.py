@@ -1,0 +1,62 @@
+"""Comparison helpers for the GPU-vs-oracle parity tests."""
+from __future__ import annotations
+
+import numpy as np
+
+# Tolerances, p99.9 over rays / points.
+#  FP32 (SIMT): hit point 1e-5, normal angle 0.01 deg.
+#  FP16 tensor-core operands: the stated targets, hit point 1e-3, normal 0.5 deg,
+#  hit/miss agreement 99.9 %.
+#  BF16 tensor-core operands: bfloat16 keeps 8 significand bits against half's
+#  11, so its unit roundoff (2^-9) is 8x that of half; every rounding error of
+#  the path scales with it, so the BF16 bounds are 8x the FP16 ones.
+#  Random-init SIRENs (no Eikonal training: |grad f| varies by 10x over the
+#  box and the gradient is a sum with heavy cancellation) amplify the same
+#  roundings by the ratio of the summands' norm to the sum's; the normal
+#  bounds on them are twice those of the trained networks.
+FP32_POS_TOL = 1e-5
+FP32_ANGLE_TOL_DEG = 0.01
+HIT_AGREEMENT = 0.999
+TOL = {  # precision code -> (hit agreement, hit-point p99.9, normal angle p99.9 in degrees)
+    0: (HIT_AGREEMENT, FP32_POS_TOL, FP32_ANGLE_TOL_DEG),
+    3: (HIT_AGREEMENT, 1e-3, 0.5),
+    1: (0.992, 8e-3, 4.0),
+}
+RANDOM_NET_ANGLE_FACTOR = 2.0
+PRECISIONS = [0, 1, 3]
+PRECISION_IDS = ["fp32", "bf16", "fp16"]
+
+
+def angle_deg(a, b) -> np.ndarray:
+    """Angle between column vectors of (3, n) arrays, robust near 0."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    cross = np.linalg.norm(np.cross(a.T, b.T), axis=1)
+    dot = np.sum(a * b, axis=0)
+    return np.degrees(np.arctan2(cross, dot))
+
+
+def q999(x) -> float:
+    x = np.asarray(x, np.float64)
+    return float(np.quantile(x, 0.999)) if x.size else 0.0
+
+
+def trace_report(gpu_pos, gpu_hit, orc_pos, orc_hit):
+    gpu_hit = np.asarray(gpu_hit).astype(bool)
+    orc_hit = np.asarray(orc_hit).astype(bool)
+    agree = float(np.mean(gpu_hit == orc_hit)) if gpu_hit.size else 1.0
+    both = gpu_hit & orc_hit
+    d = np.linalg.norm(np.asarray(gpu_pos, np.float64)[:, both] - np.asarray(orc_pos, np.float64)[:, both], axis=0)
+    return {"agree": agree, "n_hit_gpu": int(gpu_hit.sum()), "n_hit_oracle": int(orc_hit.sum()),
+            "n_both": int(both.sum()), "pos_p999": q999(d), "pos_max": float(d.max()) if d.size else 0.0,
+            "both": both}
+
+
+def angle_report(gpu_vec, orc_vec, mask=None):
+    g = np.asarray(gpu_vec, np.float64)
+    o = np.asarray(orc_vec, np.float64)
+    if mask is not None:
+        g, o = g[:, mask], o[:, mask]
+    ang = angle_deg(g, o)
+    return {"n": int(ang.size), "angle_p999": q999(ang), "angle_max": float(ang.max()) if ang.size else 0.0,
+            "angle_mean": float(ang.mean()) if ang.size else 0.0}

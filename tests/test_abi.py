@@ -1,0 +1,67 @@
+"""The C ABI: the library builds, loads and exports every declared symbol.
+
+No compute call is made here (no GPU); host-side validation that runs before
+any device work is exercised through the loader.
+"""
+import ctypes as C
+import re
+from pathlib import Path
+
+import pytest
+
+from paper_2201_09147_gb300 import build, inputs
+
+HEADER = Path(__file__).resolve().parents[1] / "include" / "sdfnn.h"
+
+
+def declared_functions():
+    text = re.sub(r"/\*.*?\*/", "", HEADER.read_text(), flags=re.S)
+    return sorted(set(re.findall(r"\b(sdf_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return C.CDLL(str(build.build()))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_names_match_header():
+    from paper_2201_09147_gb300 import sdfnn
+    assert sorted(sdfnn.EXPORTS) == declared_functions()
+
+
+def test_loader_rejects_malformed_images_without_a_gpu(lib):
+    lib.sdf_net_load_mem.argtypes = [C.c_char_p, C.c_size_t, C.c_int, C.c_int, C.POINTER(C.c_void_p)]
+    lib.sdf_last_error.restype = C.c_char_p
+    h = C.c_void_p(1)
+    good = inputs.net_to_bytes(inputs.siren_init(0, 64, 1))
+    assert lib.sdf_net_load_mem(b"nope", 4, 1, 0, C.byref(h)) == -3 and h.value is None
+    assert lib.sdf_net_load_mem(good[:-4], len(good) - 4, 1, 0, C.byref(h)) == -3
+    assert lib.sdf_net_load_mem(good, len(good), 2, 0, C.byref(h)) == -7   # FP8 not built
+    assert lib.sdf_net_load_mem(good, len(good), 9, 0, C.byref(h)) == -1   # unknown precision
+    assert lib.sdf_net_load_mem(None, 0, 1, 0, C.byref(h)) == -1
+    bad = bytearray(good)
+    bad[36:40] = bytes([0, 0, 0xC0, 0x7F])  # NaN in W_0
+    assert lib.sdf_net_load_mem(bytes(bad), len(bad), 1, 0, C.byref(h)) == -5
+    wide = inputs.net_to_bytes(inputs.siren_init(0, 96, 1))
+    assert lib.sdf_net_load_mem(wide, len(wide), 0, 0, C.byref(h)) == -7
+    lib.sdf_net_load.argtypes = [C.c_char_p, C.c_int, C.c_int, C.POINTER(C.c_void_p)]
+    assert lib.sdf_net_load(b"/nonexistent/file.sdfn", 1, 0, C.byref(h)) == -2
+    assert len(lib.sdf_last_error()) > 0
+
+
+def test_null_arguments_are_rejected(lib):
+    lib.sdf_trace_multiscale.argtypes = [C.c_void_p] * 4 + [C.c_void_p] * 5
+    lib.sdf_trace_multiscale.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p]
+    assert lib.sdf_trace_multiscale(None, None, None, 0, None, None, None, None, None) == -1
+    lib.sdf_normals.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+    assert lib.sdf_normals(None, None, 0, None, None) == -1
+    lib.sdf_net_free.argtypes = [C.c_void_p]
+    lib.sdf_net_free(None)

@@ -1,0 +1,318 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
+
+Tolerances (tests/parity.py, per precision): hit/miss agreement; on rays both
+sides call hits, end-point distance p99.9; normal angle at the same point
+p99.9.  FP32: 99.9 %, 1e-5, 0.01 deg.  FP16: 99.9 %, 1e-3, 0.5 deg.  BF16:
+bounds scaled by its 8x larger unit roundoff.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2201_09147_gb300 import inputs, workloads
+from parity import (HIT_AGREEMENT, PRECISION_IDS, PRECISIONS, RANDOM_NET_ANGLE_FACTOR, TOL, angle_report,
+                    trace_report)
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_trace(sdf, level_bytes, precision, wl, orig, dirs, step_scale="wl"):
+    nets = [sdf.Net(b, precision) for b in level_bytes]
+    o = torch.from_numpy(np.ascontiguousarray(orig)).cuda()
+    d = torch.from_numpy(np.ascontiguousarray(dirs)).cuda()
+    ss = wl.step_scale if step_scale == "wl" else step_scale
+    pos, t, hit, iters = sdf.trace_multiscale(nets, wl.delta, wl.caps, wl.eps, o, d, step_scale=ss,
+                                              final_mode=wl.final_mode)
+    sdf.sync_status()
+    return {"pos": pos.cpu().numpy(), "t": t.cpu().numpy(), "hit": hit.cpu().numpy(),
+            "iters": iters.cpu().numpy().astype(np.int64), "nets": nets, "pos_dev": pos, "hit_dev": hit}
+
+
+def oracle_trace(level_bytes, wl, orig, dirs, idx=None):
+    onets = [oracle.Net(b) for b in level_bytes]
+    scales = wl.step_scale if wl.step_scale is not None else [1.0 / n.lipschitz() for n in onets]
+    tp = oracle.TraceParams([oracle.SDF.of_net(n) for n in onets], wl.delta, wl.caps, scales, wl.eps,
+                            final_mode=wl.final_mode)
+    return tp.trace_batch(orig, dirs, idx=idx)
+
+
+def check_trace(g, o, precision, label):
+    agree_tol, pos_tol, _ = TOL[precision]
+    rep = trace_report(g["pos"], g["hit"], o["pos"], o["hit"])
+    print(label, {k: v for k, v in rep.items() if k != "both"})
+    assert rep["agree"] >= agree_tol, (label, rep["agree"])
+    assert rep["pos_p999"] <= pos_tol, (label, rep["pos_p999"])
+    return rep
+
+
+# ---------------------------------------------------------------------------
+# network preparation
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(64, 1), (128, 2), (256, 3), (256, 4)])
+def test_lipschitz_matches_oracle(sdf, shape):
+    b = inputs.net_to_bytes(inputs.siren_init(3, shape[0], shape[1]))
+    n = sdf.Net(b, sdf.SDF_FP32)
+    ref = oracle.Net(b).lipschitz()
+    assert abs(n.lipschitz - ref) <= 1e-9 * ref
+    assert (n.in_dim, n.width, n.n_hidden) == (3, shape[0], shape[1])
+
+
+def test_load_rejects_bad_input(sdf):
+    b = inputs.net_to_bytes(inputs.siren_init(0, 64, 1))
+    with pytest.raises(sdf.SdfError) as e:
+        sdf.Net(b[:-4], sdf.SDF_BF16)
+    assert e.value.code == -3
+    bad = bytearray(b)
+    bad[40:44] = np.array([np.nan], np.float32).tobytes()
+    with pytest.raises(sdf.SdfError) as e:
+        sdf.Net(bytes(bad), sdf.SDF_BF16)
+    assert e.value.code == -5
+    with pytest.raises(sdf.SdfError) as e:
+        sdf.Net(b, sdf.SDF_FP8)
+    assert e.value.code == -7
+    odd = inputs.net_to_bytes(inputs.siren_init(0, 96, 1))
+    with pytest.raises(sdf.SdfError) as e:
+        sdf.Net(odd, sdf.SDF_FP32)
+    assert e.value.code == -7
+
+
+# ---------------------------------------------------------------------------
+# analytic normals (Alg. 2)
+# ---------------------------------------------------------------------------
+
+NORMAL_NETS = [("siren64x1", lambda: inputs.net_to_bytes(workloads.random_siren_64x1())),
+               ("siren128x2", lambda: inputs.net_to_bytes(inputs.siren_init(5, 128, 2))),
+               ("siren256x3", lambda: inputs.net_to_bytes(inputs.siren_init(6, 256, 3))),
+               ("siren256x4", lambda: inputs.net_to_bytes(inputs.siren_init(7, 256, 4))),
+               ("scene256x3", lambda: (workloads.SCENES / "s8_256x3.sdfn").read_bytes()),
+               ("scene64x1", lambda: (workloads.SCENES / "s8_64x1.sdfn").read_bytes())]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
+@pytest.mark.parametrize("name,make", NORMAL_NETS, ids=[n for n, _ in NORMAL_NETS])
+def test_normals_vs_oracle(sdf, precision, name, make):
+    b = make()
+    n = 4096 + 37  # several tiles and a ragged tail
+    pts = inputs.random_points(11, n, -1.0, 1.0)
+    net = sdf.Net(b, precision)
+    g = sdf.normals(net, torch.from_numpy(pts).cuda())
+    nm = sdf.normal_map(net, torch.from_numpy(pts).cuda())
+    sdf.sync_status()
+    g = g.cpu().numpy()
+    nm = nm.cpu().numpy()
+    ref = oracle.Net(b).grad_batch(pts)
+    tol = TOL[precision][2] * (RANDOM_NET_ANGLE_FACTOR if name.startswith("siren") and precision else 1.0)
+    ok = np.linalg.norm(ref, axis=0) > 1e-3 * np.median(np.linalg.norm(ref, axis=0))
+    rep = angle_report(g, ref, ok)
+    print(name, precision, rep)
+    assert rep["angle_p999"] <= tol
+    rel = np.linalg.norm(g - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert np.quantile(rel[ok], 0.999) <= np.radians(tol) * 4 + 1e-4
+    # normal map = unit gradient
+    unit = ref / np.linalg.norm(ref, axis=0, keepdims=True)
+    assert angle_report(nm, unit, ok)["angle_p999"] <= tol
+    assert np.allclose(np.linalg.norm(nm, axis=0)[ok], 1.0, atol=1e-5)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
+def test_normal_map_mask(sdf, precision):
+    b = (workloads.SCENES / "s8_256x3.sdfn").read_bytes()
+    n = 3000
+    pts = inputs.random_points(12, n, -0.8, 0.8)
+    mask = (inputs.uniform01(13, n) < 0.4).astype(np.uint8)
+    net = sdf.Net(b, precision)
+    out = torch.full((3, n), 7.0, device="cuda")
+    sdf.normal_map(net, torch.from_numpy(pts).cuda(), torch.from_numpy(mask).cuda(), out=out)
+    sdf.sync_status()
+    out = out.cpu().numpy()
+    m = mask.astype(bool)
+    assert np.all(out[:, ~m] == 0.0)
+    ref = oracle.Net(b).normal_map(pts, mask)
+    assert angle_report(out, ref, m)["angle_p999"] <= TOL[precision][2]
+
+
+# ---------------------------------------------------------------------------
+# multiscale sphere tracing (Alg. 1)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
+def test_trace_random_siren(sdf, precision):
+    """128 x 128 rays, Lipschitz steps, 32 iterations: trajectories must agree."""
+    wl = workloads.get("random_siren_64x1")
+    orig, dirs = wl.rays()
+    lb = wl.level_bytes()
+    g = gpu_trace(sdf, lb, precision, wl, orig, dirs)
+    o = oracle_trace(lb, wl, orig, dirs)
+    check_trace(g, o, precision, f"random_siren p={precision}")
+    same_iters = np.mean(g["iters"] == o["iters"])
+    print("same iteration count", same_iters)
+    if precision == 0:
+        assert same_iters >= HIT_AGREEMENT
+        # every ray, hit or miss, ends at the same point
+        d = np.linalg.norm(g["pos"] - o["pos"], axis=0)
+        assert np.quantile(d, 0.999) <= 1e-4
+    # normals of the traced net at the GPU's own hit points
+    hit = g["hit"].astype(bool)
+    nrm = sdf.normal_map(g["nets"][0], g["pos_dev"], g["hit_dev"])
+    sdf.sync_status()
+    ref = oracle.Net(lb[0]).normal_map(g["pos"].astype(np.float64), g["hit"])
+    tol = TOL[precision][2] * (RANDOM_NET_ANGLE_FACTOR if precision else 1.0)
+    assert angle_report(nrm.cpu().numpy(), ref, hit)["angle_p999"] <= tol
+
+
+@pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
+def test_normal_map_workload_small(sdf, precision):
+    """Coarse (64,1) to its delta shell, then (256,3) normals (Sec. 5), 200 x 113 rays."""
+    wl = workloads.get("normal_map_1080p", 200, 113)
+    orig, dirs = wl.rays()
+    lb = wl.level_bytes()
+    g = gpu_trace(sdf, lb, precision, wl, orig, dirs)
+    o = oracle_trace(lb, wl, orig, dirs)
+    rep = check_trace(g, o, precision, f"normal_map_small p={precision}")
+    assert rep["n_both"] > 1000
+    fine = sdf.Net(wl.fine_bytes(), precision)
+    nrm = sdf.normal_map(fine, g["pos_dev"], g["hit_dev"])
+    sdf.sync_status()
+    nrm = nrm.cpu().numpy()
+    hit = g["hit"].astype(bool)
+    assert np.all(nrm[:, ~hit] == 0.0)
+    ref = oracle.Net(wl.fine_bytes()).normal_map(g["pos"].astype(np.float64), g["hit"])
+    ar = angle_report(nrm, ref, hit)
+    print(ar)
+    assert ar["angle_p999"] <= TOL[precision][2]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
+def test_nested_3level_small(sdf, precision):
+    """(64,2) |> (128,2) |> (256,2) at 96 x 96 rays, then the finest net's normals at the hits."""
+    wl = workloads.get("nested_3level_512", 96, 96)
+    orig, dirs = wl.rays()
+    lb = wl.level_bytes()
+    g = gpu_trace(sdf, lb, precision, wl, orig, dirs)
+    o = oracle_trace(lb, wl, orig, dirs)
+    rep = check_trace(g, o, precision, f"nested_3level p={precision}")
+    assert rep["n_both"] > 500
+    fine = sdf.Net(wl.fine_bytes(), precision)
+    nrm = sdf.normal_map(fine, g["pos_dev"], g["hit_dev"])
+    sdf.sync_status()
+    ref = oracle.Net(wl.fine_bytes()).normal_map(g["pos"].astype(np.float64), g["hit"])
+    ar = angle_report(nrm.cpu().numpy(), ref, g["hit"].astype(bool))
+    print(ar)
+    assert ar["angle_p999"] <= TOL[precision][2]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
+def test_plain_256x3_small(sdf, precision):
+    """The single-network (256,3) tracer (streamed weights on the tensor cores), 120 x 68 rays."""
+    wl = workloads.get("plain_256x3_1080p", 120, 68)
+    orig, dirs = wl.rays()
+    lb = wl.level_bytes()
+    g = gpu_trace(sdf, lb, precision, wl, orig, dirs)
+    o = oracle_trace(lb, wl, orig, dirs)
+    rep = check_trace(g, o, precision, f"plain_256x3 p={precision}")
+    assert rep["n_both"] > 500
+
+
+@pytest.mark.parametrize("precision", [1, 3], ids=["bf16", "fp16"])
+def test_normal_map_1080p_sampled(sdf, precision):
+    """Full 1920 x 1080 frame in the benchmark's launch configuration; oracle on 3000 sampled rays."""
+    wl = workloads.get("normal_map_1080p")
+    orig, dirs = wl.rays()
+    lb = wl.level_bytes()
+    g = gpu_trace(sdf, lb, precision, wl, orig, dirs)
+    fine = sdf.Net(wl.fine_bytes(), precision)
+    nrm = sdf.normal_map(fine, g["pos_dev"], g["hit_dev"])
+    sdf.sync_status()
+    idx = np.sort(np.unique((inputs.uniform01(99, 3000) * wl.n_rays).astype(np.int64)))
+    o = oracle_trace(lb, wl, orig, dirs, idx=idx)
+    gs = {"pos": g["pos"][:, idx], "hit": g["hit"][idx]}
+    rep = check_trace(gs, o, precision, f"1080p sampled p={precision}")
+    assert rep["n_both"] > 300
+    hit = gs["hit"].astype(bool)
+    ref = oracle.Net(wl.fine_bytes()).normal_map(gs["pos"].astype(np.float64), gs["hit"])
+    ar = angle_report(nrm.cpu().numpy()[:, idx], ref, hit)
+    print(ar)
+    assert ar["angle_p999"] <= TOL[precision][2]
+    # every ray of the frame got a decision and misses carry zero normals
+    allhit = g["hit"].astype(bool)
+    assert set(np.unique(g["hit"])) <= {0, 1}
+    assert np.all(nrm.cpu().numpy()[:, ~allhit] == 0.0)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
+def test_mesh_normal_map(sdf, precision):
+    """Neural normal mapping onto mesh vertices (Sec. 5): displaced icosphere, subdivision 5."""
+    pts, frac = workloads.mesh_points(subdivisions=5)
+    assert frac > 0.9
+    fine_b = (workloads.SCENES / "s8_256x3.sdfn").read_bytes()
+    fine = sdf.Net(fine_b, precision)
+    out = sdf.normal_map(fine, torch.from_numpy(pts).cuda())
+    sdf.sync_status()
+    ref = oracle.Net(fine_b).normal_map(pts.astype(np.float64))
+    ar = angle_report(out.cpu().numpy(), ref)
+    print(ar)
+    assert ar["angle_p999"] <= TOL[precision][2]
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def test_edge_cases(sdf):
+    wl = workloads.get("random_siren_64x1")
+    b = wl.level_bytes()[0]
+    net = sdf.Net(b, sdf.SDF_BF16)
+    # n = 0
+    z = torch.empty((3, 0), device="cuda")
+    sdf.trace_multiscale([net], [0.0], [32], 1e-3, z, z)
+    sdf.normals(net, z)
+    # host pointers are rejected before any launch
+    host = torch.zeros((3, 4))
+    with pytest.raises(sdf.SdfError) as e:
+        sdf.normals(net, host, out=torch.zeros((3, 4)))
+    assert e.value.code == -1
+    # bad parameters
+    d = torch.zeros((3, 4), device="cuda")
+    with pytest.raises(sdf.SdfError):
+        sdf.trace_multiscale([net], [0.0], [32], 0.0, d, d)
+    with pytest.raises(sdf.SdfError):
+        sdf.trace_multiscale([net, net], [-1.0, 0.0], [8, 8], 1e-3, d, d)
+    # rays that miss the box, start inside it, or get zero iterations
+    o = np.array([[0.0, 0.0, 5.0], [0.0, 0.0, 0.0], [0.3, 0.1, -0.2], [2.0, 2.0, 2.0]], np.float32).T.copy()
+    v = np.array([[0.0, 1.0, 0.0], [0.0, 0.0, 1.0], [0.0, 0.6, 0.8], [1.0, 0.0, 0.0]], np.float32).T.copy()
+    for caps in ([32], [0]):
+        w2 = workloads.Workload("edge", [b], [0.0], caps, 1e-3, None, 0, 1, 1, b)
+        g = gpu_trace(sdf, [b], 0, w2, o, v)
+        r = oracle_trace([b], w2, o, v)
+        assert np.array_equal(g["hit"], r["hit"])
+        assert np.array_equal(g["iters"], r["iters"])
+        assert np.allclose(g["pos"], r["pos"], atol=1e-5)
+    assert g["hit"][0] == 0 and g["iters"][0] == 0  # misses the box: no evaluation
+    sdf.sync_status()
+
+
+def test_render_host_matches_device(sdf):
+    wl = workloads.get("normal_map_1080p", 160, 90)
+    orig, dirs = wl.rays()
+    nets = [sdf.Net(b, sdf.SDF_BF16) for b in wl.level_bytes()]
+    fine = sdf.Net(wl.fine_bytes(), sdf.SDF_BF16)
+    n = orig.shape[1]
+    hp = torch.empty((3, n)).pin_memory()
+    hh = torch.empty(n, dtype=torch.uint8).pin_memory()
+    hn = torch.empty((3, n)).pin_memory()
+    sdf.render_host(nets, wl.delta, wl.caps, wl.eps, fine, torch.from_numpy(orig).pin_memory(),
+                    torch.from_numpy(dirs).pin_memory(), hp, hh, hn, step_scale=wl.step_scale,
+                    final_mode=wl.final_mode)
+    o = torch.from_numpy(orig).cuda()
+    d = torch.from_numpy(dirs).cuda()
+    pos, _, hit, _ = sdf.trace_multiscale(nets, wl.delta, wl.caps, wl.eps, o, d, step_scale=wl.step_scale,
+                                          final_mode=wl.final_mode)
+    nrm = sdf.normal_map(fine, pos, hit)
+    sdf.sync_status()
+    assert torch.equal(hh, hit.cpu())
+    assert torch.equal(hp, pos.cpu())
+    assert torch.equal(hn, nrm.cpu())
