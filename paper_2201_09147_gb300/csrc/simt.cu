@@ -327,6 +327,10 @@ template <class Kernel>
 cudaError_t launch_persistent(Kernel k, size_t smem, int num_sms, cudaStream_t s, const void* arg) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
+    // ask for the largest shared-memory carveout, so that the occupancy query
+    // (and the launch) can place as many CTAs per SM as shared memory allows
+    e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kSimtThreads, smem);
     if (e != cudaSuccess) return e;

@@ -13,16 +13,18 @@
 //   dot product of the last sine layer straight from TMEM, so the step
 //   t = f - d is never rounded to 16 bits.
 //
-// grad_tc : analytic gradients (Alg. 2).  Tiles of 64 points; the MMA runs
-//   with the features as rows (M = 128 per TMEM tile, width/128 tiles) and
-//   N = 256 columns = 64 points x {forward, G^x, G^y, G^z}, so one weight
-//   tile feeds the forward pass and the three tangents at once and the
+// grad_tc : analytic gradients (Alg. 2).  Tiles of 64 points in two halves;
+//   the MMA runs with the features as rows (M = 128 per TMEM tile,
+//   width/128 tiles) and N = 128 columns = 32 points x {forward, G^x, G^y,
+//   G^z} per half, so one weight tile feeds the forward pass and the three
+//   tangents at once and the
 //   thread that owns feature m finds A_i[m] and the three G_i[m] of a point
 //   in its own TMEM lane: the epilogue P_i = sin(A_i), G_i = cos(A_i) (.)
 //   (W_i G_{i-1}) needs no data exchange.  Hidden weights stream from L2
 //   through a ring of shared-memory stages filled by bulk copies (TMA); the
 //   output layer W_n G_{n-1} is one more small MMA (rows = the 256
 //   point-streams, N = 16, w_out as a head row plus a remainder row).
+#include <algorithm>
 #include <cstdint>
 
 #include "common.cuh"
@@ -511,21 +513,30 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
 // ---------------------------------------------------------------------------
 // gradient kernel
 // ---------------------------------------------------------------------------
+// A tile of 64 points is processed as two halves of 32 points (128 X rows =
+// 32 points x 4 streams each).  Each half has its own epilogue warp group,
+// TMEM columns and barriers; the MMA warp alternates between the halves, so
+// the tensor core works on one half while the other half's epilogue
+// (sin/cos, tangent scaling, 16-bit stores) runs.  The producer warp streams
+// every hidden layer's K blocks once per half.
 template <int W>
 struct GradCfg {
     static constexpr int MT = (W + 127) / 128;      // TMEM tiles of 128 feature rows
     static constexpr int ROWS = MT * 128;           // feature rows incl. zero padding
     static constexpr int KB = W / 64;               // 64-wide K blocks
     static constexpr int NPTS = 64;                 // points per tile
-    static constexpr int NROWS = 4 * NPTS;          // point-streams = MMA N = rows of X
-    static constexpr int NS = (W == 256) ? 2 : 3;   // weight ring stages
-    static constexpr int EPI_WARPS = 4 * MT;
-    static constexpr int EPI_THREADS = EPI_WARPS * 32;
+    static constexpr int HPTS = 32;                 // points per half
+    static constexpr int NROWS = 4 * NPTS;          // rows of X (point-streams)
+    static constexpr int HROWS = 4 * HPTS;          // rows of X per half = MMA N
+    static constexpr int NS = (W == 256) ? 2 : 4;   // weight ring stages
+    static constexpr int GROUP_WARPS = 4 * MT;      // epilogue warps per half
+    static constexpr int GROUP_THREADS = GROUP_WARPS * 32;
+    static constexpr int EPI_WARPS = 2 * GROUP_WARPS;
     static constexpr int PRODUCER_WARP = EPI_WARPS;
     static constexpr int MMA_WARP = EPI_WARPS + 1;
     static constexpr int THREADS = (EPI_WARPS + 2) * 32;
     static constexpr uint32_t STAGE_BYTES = ROWS * 128u;
-    static constexpr int TMEM_COLS = MT * 256;
+    static constexpr int TMEM_COLS = MT * 256;      // per TMEM tile: half 0 at +0, half 1 at +128
 };
 
 struct GradLayout {
@@ -554,7 +565,7 @@ __host__ __device__ inline GradLayout grad_layout(int KH) {
     L.idx = o;
     o += C::NPTS * 4u;
     L.bars = o;
-    o += (2 * C::NS + 2) * 8u;
+    o += (2 * C::NS + 4) * 8u;
     o = (o + 15u) & ~15u;
     L.misc = o;
     o += 32u;
@@ -562,8 +573,8 @@ __host__ __device__ inline GradLayout grad_layout(int KH) {
     return L;
 }
 
-__device__ __forceinline__ void epi_barrier(int nthreads) {
-    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+__device__ __forceinline__ void named_barrier(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 template <int W, bool F16>
@@ -581,10 +592,10 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
     float* bhs = reinterpret_cast<float*>(base + L.bh);
     float* pts = reinterpret_cast<float*>(base + L.pts);
     int* idxs = reinterpret_cast<int*>(base + L.idx);
-    const uint32_t bar_full = base_s + L.bars;            // NS barriers
-    const uint32_t bar_empty = bar_full + 8u * C::NS;     // NS barriers
-    const uint32_t bar_xready = bar_empty + 8u * C::NS;
-    const uint32_t bar_dfull = bar_xready + 8u;
+    const uint32_t bar_full = base_s + L.bars;             // NS barriers
+    const uint32_t bar_empty = bar_full + 8u * C::NS;      // NS barriers
+    const uint32_t bar_xready = bar_empty + 8u * C::NS;    // 2 barriers (one per half)
+    const uint32_t bar_dfull = bar_xready + 16u;           // 2 barriers (one per half)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.misc);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(base + L.misc + 4);
     long long* tile_slot = reinterpret_cast<long long*>(base + L.misc + 8);
@@ -596,8 +607,10 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
             mbar_init(bar_full + 8u * s, 1);
             mbar_init(bar_empty + 8u * s, 1);
         }
-        mbar_init(bar_xready, C::EPI_THREADS);
-        mbar_init(bar_dfull, 1);
+        for (int h = 0; h < 2; ++h) {
+            mbar_init(bar_xready + 8u * h, C::GROUP_THREADS);
+            mbar_init(bar_dfull + 8u * h, 1);
+        }
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -632,7 +645,8 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
     const uint32_t tmem = *tmem_slot;
 
     const long long n_work = a.list ? static_cast<long long>(*a.count) : a.n;
-    uint32_t g_prod = 0, g_mma = 0, xr_phase = 0, df_phase = 0;
+    uint32_t g_prod = 0, g_mma = 0;
+    uint32_t xr_phase[2] = {0u, 0u}, df_phase = 0;
     bool ok = true;
 
     while (true) {
@@ -643,11 +657,12 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
 
         if (warp == C::PRODUCER_WARP) {
             if (lane == 0) {
-                for (int st = 0; st < KH * C::KB && ok; ++st, ++g_prod) {
+                // K blocks in MMA order: layer by layer, each layer once per half
+                for (int st = 0; st < KH * 2 * C::KB && ok; ++st, ++g_prod) {
                     const uint32_t stage = g_prod % C::NS, use = g_prod / C::NS;
                     if (use > 0) ok = mbar_wait_bounded(bar_empty + 8u * stage, (use - 1) & 1u, a.status, abort_flag);
                     if (!ok) break;
-                    const int l = st / C::KB, kb = st % C::KB;
+                    const int l = st / (2 * C::KB), kb = st % C::KB;
                     mbar_arrive_expect_tx(bar_full + 8u * stage, C::STAGE_BYTES);
                     bulk_g2s(ring_s + stage * C::STAGE_BYTES,
                              net.wbf + static_cast<size_t>(l) * net.wbf_layer_bytes +
@@ -657,65 +672,69 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
             }
         } else if (warp == C::MMA_WARP) {
             if (lane == 0) {
-                constexpr uint32_t idesc_h = idesc_f32acc(128, 256, F16);
+                constexpr uint32_t idesc_h = idesc_f32acc(128, C::HROWS, F16);
                 constexpr uint32_t idesc_o = idesc_f32acc(128, 16, F16);
                 for (int l = 0; l <= KH && ok; ++l) {
-                    ok = mbar_wait_bounded(bar_xready, xr_phase, a.status, abort_flag);
-                    xr_phase ^= 1u;
-                    if (!ok) break;
-                    tc_fence_after();
-                    if (l < KH) {
-                        // D[mt] = W_l[mt rows] . X^T over all K blocks
-                        for (int kb = 0; kb < C::KB && ok; ++kb, ++g_mma) {
-                            const uint32_t stage = g_mma % C::NS, use = g_mma / C::NS;
-                            ok = mbar_wait_bounded(bar_full + 8u * stage, use & 1u, a.status, abort_flag);
-                            if (!ok) break;
-                            tc_fence_after();
+                    for (int h = 0; h < 2 && ok; ++h) {
+                        ok = mbar_wait_bounded(bar_xready + 8u * h, xr_phase[h], a.status, abort_flag);
+                        xr_phase[h] ^= 1u;
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint32_t xh = x_s + h * C::HROWS * 128u;  // rows of this half within each K block
+                        if (l < KH) {
+                            // D[mt][h] = W_l[mt rows] . X_h^T over all K blocks
+                            for (int kb = 0; kb < C::KB && ok; ++kb, ++g_mma) {
+                                const uint32_t stage = g_mma % C::NS, use = g_mma / C::NS;
+                                ok = mbar_wait_bounded(bar_full + 8u * stage, use & 1u, a.status, abort_flag);
+                                if (!ok) break;
+                                tc_fence_after();
 #pragma unroll
-                            for (int mt = 0; mt < C::MT; ++mt)
+                                for (int mt = 0; mt < C::MT; ++mt)
 #pragma unroll
-                                for (int kk = 0; kk < 4; ++kk)
-                                    mma_f16kind(tmem + mt * 256u,
-                                             desc_kmajor_sw128(ring_s + stage * C::STAGE_BYTES + mt * 128u * 128u + kk * 32u),
-                                             desc_kmajor_sw128(x_s + kb * C::NROWS * 128u + kk * 32u), idesc_h,
-                                             (kb | kk) != 0);
-                            mma_commit(bar_empty + 8u * stage);
-                        }
-                        if (ok) mma_commit(bar_dfull);
-                    } else {
-                        // output layer: D_out[h] (columns 16h) = X[128h .. 128h+127] . w_out^T
-#pragma unroll
-                        for (int h = 0; h < 2; ++h)
+                                    for (int kk = 0; kk < 4; ++kk)
+                                        mma_f16kind(tmem + mt * 256u + h * 128u,
+                                                    desc_kmajor_sw128(ring_s + stage * C::STAGE_BYTES +
+                                                                      mt * 128u * 128u + kk * 32u),
+                                                    desc_kmajor_sw128(xh + kb * C::NROWS * 128u + kk * 32u), idesc_h,
+                                                    (kb | kk) != 0);
+                                mma_commit(bar_empty + 8u * stage);
+                            }
+                        } else {
+                            // output layer of this half: rows = its 128 point-streams, N = 16 (w_out head, remainder)
                             for (int kb = 0; kb < C::KB; ++kb)
 #pragma unroll
                                 for (int kk = 0; kk < 4; ++kk)
-                                    mma_f16kind(tmem + 16u * h,
-                                             desc_kmajor_sw128(x_s + kb * C::NROWS * 128u + h * 128u * 128u + kk * 32u),
-                                             desc_kmajor_sw128(wo_s + kb * 16u * 128u + kk * 32u), idesc_o,
-                                             (kb | kk) != 0);
-                        mma_commit(bar_dfull);
+                                    mma_f16kind(tmem + h * 128u,
+                                                desc_kmajor_sw128(xh + kb * C::NROWS * 128u + kk * 32u),
+                                                desc_kmajor_sw128(wo_s + kb * 16u * 128u + kk * 32u), idesc_o,
+                                                (kb | kk) != 0);
+                        }
+                        if (ok) mma_commit(bar_dfull + 8u * h);
                     }
                 }
             }
         } else {
-            // epilogue warps: thread <-> feature row m of TMEM tile mt
-            const int mt = warp >> 2, quad = warp & 3;
+            // epilogue group h: thread <-> feature row m of TMEM tile mt, points 32h .. 32h+31
+            const int h = warp / C::GROUP_WARPS, ge = warp % C::GROUP_WARPS;
+            const int mt = ge >> 2, quad = ge & 3;
             const int m = mt * 128 + quad * 32 + lane;
-            const uint32_t lane_addr = tmem + (static_cast<uint32_t>(quad * 32) << 16) + mt * 256u;
-            if (tid < C::NPTS) {
-                const long long k = base_pt + tid;
+            const int gt = ge * 32 + lane;  // thread index within the group
+            const uint32_t lane_addr = tmem + (static_cast<uint32_t>(quad * 32) << 16) + mt * 256u + h * 128u;
+            const int p0 = h * C::HPTS;
+            if (gt < C::HPTS) {
+                const long long k = base_pt + p0 + gt;
                 int i = -1;
                 if (k < n_work) i = a.list ? a.list[k] : static_cast<int>(k);
-                idxs[tid] = i;
-                pts[tid * 3 + 0] = i >= 0 ? a.pts[i] : 0.0f;
-                pts[tid * 3 + 1] = i >= 0 ? a.pts[a.n + i] : 0.0f;
-                pts[tid * 3 + 2] = i >= 0 ? a.pts[2 * a.n + i] : 0.0f;
+                idxs[p0 + gt] = i;
+                pts[(p0 + gt) * 3 + 0] = i >= 0 ? a.pts[i] : 0.0f;
+                pts[(p0 + gt) * 3 + 1] = i >= 0 ? a.pts[a.n + i] : 0.0f;
+                pts[(p0 + gt) * 3 + 2] = i >= 0 ? a.pts[2 * a.n + i] : 0.0f;
             }
-            epi_barrier(C::EPI_THREADS);
+            named_barrier(1 + h, C::GROUP_THREADS);
             // input layer: P_0 = sin(A_0), G_0^c = W_0[:, c] (.) cos(A_0)
             if (m < W) {
                 const float wx = w0s[m * 4 + 0], wy = w0s[m * 4 + 1], wz = w0s[m * 4 + 2], bb = b0s[m];
-                for (int p = 0; p < C::NPTS; ++p) {
+                for (int p = p0; p < p0 + C::HPTS; ++p) {
                     const float z = fmaf(wx, pts[p * 3 + 0], fmaf(wy, pts[p * 3 + 1], fmaf(wz, pts[p * 3 + 2], bb)));
                     float s, c;
                     sincos_r(z, &s, &c);
@@ -727,15 +746,16 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
             }
             fence_proxy_async_smem();
             tc_fence_before();
-            mbar_arrive(bar_xready);
+            mbar_arrive(bar_xready + 8u * h);
 
             for (int l = 0; l < KH && ok; ++l) {
-                ok = mbar_wait_bounded(bar_dfull, df_phase, a.status, abort_flag);
+                ok = mbar_wait_bounded(bar_dfull + 8u * h, df_phase, a.status, abort_flag);
                 df_phase ^= 1u;
                 if (!ok) break;
                 tc_fence_after();
                 const float bb = m < W ? bhs[l * W + m] : 0.0f;
-                for (int q = 0; q < C::NROWS / 32; ++q) {
+#pragma unroll 1
+                for (int q = 0; q < C::HROWS / 32; ++q) {
                     float v[32];
                     tmem_ld32(lane_addr + q * 32u, v);
                     tmem_wait_ld();
@@ -743,7 +763,7 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
 #pragma unroll
                         for (int pp = 0; pp < 8; ++pp) {
                             // P_i = sin(A_i);  G_i = (W_i G_{i-1}) (.) cos(A_i)
-                            const int p = q * 8 + pp;
+                            const int p = p0 + q * 8 + pp;
                             float s, c;
                             sincos_r(v[pp * 4] + bb, &s, &c);
                             st_shared_u16(x_s + sw128_offset(p * 4 + 0, m, C::NROWS), bits16<F16>(s));
@@ -755,39 +775,36 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
                 }
                 fence_proxy_async_smem();
                 tc_fence_before();
-                mbar_arrive(bar_xready);
+                mbar_arrive(bar_xready + 8u * h);
             }
-            if (ok) ok = mbar_wait_bounded(bar_dfull, df_phase, a.status, abort_flag);
+            if (ok) ok = mbar_wait_bounded(bar_dfull + 8u * h, df_phase, a.status, abort_flag);
             df_phase ^= 1u;
             if (ok && mt == 0) {
                 tc_fence_after();
                 float v[32];
-                tmem_ld32(tmem + (static_cast<uint32_t>(quad * 32) << 16), v);
+                tmem_ld32(tmem + (static_cast<uint32_t>(quad * 32) << 16) + h * 128u, v);
                 tmem_wait_ld();
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    // row n = 128h + 32quad + lane = 4 * point + stream; head + remainder of w_out
-                    const float val = v[16 * h] + v[16 * h + 1];
-                    const int g = lane & ~3;
-                    const float gx = __shfl_sync(0xffffffffu, val, g + 1);
-                    const float gy = __shfl_sync(0xffffffffu, val, g + 2);
-                    const float gz = __shfl_sync(0xffffffffu, val, g + 3);
-                    const int p = (128 * h + 32 * quad + lane) >> 2;
-                    if ((lane & 3) == 0) {
-                        const int i = idxs[p];
-                        if (i >= 0) {
-                            float ox = gx, oy = gy, oz = gz;
-                            if (a.normalize) {
-                                const float len = sqrtf(gx * gx + gy * gy + gz * gz);
-                                const float inv = len >= 1e-12f ? 1.0f / len : 0.0f;
-                                ox *= inv;
-                                oy *= inv;
-                                oz *= inv;
-                            }
-                            a.out[i] = ox;
-                            a.out[a.n + i] = oy;
-                            a.out[2 * a.n + i] = oz;
+                // lane row r = 32 quad + lane of this half = 4 * point + stream; head + remainder of w_out
+                const float val = v[0] + v[1];
+                const int g = lane & ~3;
+                const float gx = __shfl_sync(0xffffffffu, val, g + 1);
+                const float gy = __shfl_sync(0xffffffffu, val, g + 2);
+                const float gz = __shfl_sync(0xffffffffu, val, g + 3);
+                const int p = p0 + ((32 * quad + lane) >> 2);
+                if ((lane & 3) == 0) {
+                    const int i = idxs[p];
+                    if (i >= 0) {
+                        float ox = gx, oy = gy, oz = gz;
+                        if (a.normalize) {
+                            const float len = sqrtf(gx * gx + gy * gy + gz * gz);
+                            const float inv = len >= 1e-12f ? 1.0f / len : 0.0f;
+                            ox *= inv;
+                            oy *= inv;
+                            oz *= inv;
                         }
+                        a.out[i] = ox;
+                        a.out[a.n + i] = oy;
+                        a.out[2 * a.n + i] = oz;
                     }
                 }
             }
@@ -804,17 +821,42 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
     }
 }
 
+// CTAs of `k` that fit on one SM, from its registers, shared memory, threads
+// and TMEM columns (the runtime's occupancy query reports 1 for kernels that
+// use tcgen05, whatever their footprint).
+template <class Kernel>
+cudaError_t resident_ctas(Kernel k, int threads, size_t smem, int tmem_cols, int* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int smem_sm = 0, reserved = 0, regs_sm = 0, threads_sm = 0;
+    if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev)) != cudaSuccess)
+        return e;
+    cudaFuncAttributes at;
+    if ((e = cudaFuncGetAttributes(&at, k)) != cudaSuccess) return e;
+    const int warps = (threads + 31) / 32;
+    const int regs_warp = ((at.numRegs * 32 + 255) / 256) * 256;  // allocated per warp in units of 256
+    int n = 32;
+    n = std::min(n, static_cast<int>(smem_sm / (smem + at.sharedSizeBytes + reserved)));
+    n = std::min(n, regs_sm / std::max(1, regs_warp * warps));
+    n = std::min(n, threads_sm / threads);
+    n = std::min(n, 512 / tmem_cols);
+    *out = n;
+    return n >= 1 ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
 template <class Kernel>
 cudaError_t launch_tc(Kernel k, int threads, size_t smem, int tmem_cols, int num_sms, cudaStream_t s,
                       const void* arg) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+    e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int tmem_cap = 512 / tmem_cols;
-    if (per_sm > tmem_cap) per_sm = tmem_cap;
+    int per_sm = 0;
+    if ((e = resident_ctas(k, threads, smem, tmem_cols, &per_sm)) != cudaSuccess) return e;
     void* args[] = {const_cast<void*>(arg)};
     return cudaLaunchKernel(reinterpret_cast<const void*>(k), dim3(num_sms * per_sm), dim3(threads), args, smem, s);
 }
