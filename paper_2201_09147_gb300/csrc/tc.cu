@@ -124,9 +124,9 @@ __global__ void __launch_bounds__(kTraceThreads) trace_level_tc_kernel(const Lev
     for (int i = tid; i < W; i += kTraceThreads) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) w0s[i * 4 + c] = net.w0[i * net.in_dim + c];
-        w0s[i * 4 + 3] = 0.0f;
         float bb = net.b0[i];
         if (net.in_dim == 4) bb = fmaf(net.w0[i * 4 + 3], a.time, bb);
+        w0s[i * 4 + 3] = bb;  // layer 0 as float4 (w_x, w_y, w_z, b), time folded into b
         b0s[i] = bb;
         wos[i] = net.wout[i];
         for (int l = 0; l < KH; ++l) bhs[l * W + i] = net.bh[l][i];
@@ -166,14 +166,14 @@ __global__ void __launch_bounds__(kTraceThreads) trace_level_tc_kernel(const Lev
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int e0 = k8 * 8 + 2 * q, e1 = e0 + 1;
-                const float z0 = fmaf(w0s[e0 * 4 + 0], ray.px,
-                                      fmaf(w0s[e0 * 4 + 1], ray.py, fmaf(w0s[e0 * 4 + 2], ray.pz, b0s[e0])));
-                const float z1 = fmaf(w0s[e1 * 4 + 0], ray.px,
-                                      fmaf(w0s[e1 * 4 + 1], ray.py, fmaf(w0s[e1 * 4 + 2], ray.pz, b0s[e1])));
+                const float4 u0 = reinterpret_cast<const float4*>(w0s)[e0];
+                const float4 u1 = reinterpret_cast<const float4*>(w0s)[e1];
+                const float z0 = fmaf(u0.x, ray.px, fmaf(u0.y, ray.py, fmaf(u0.z, ray.pz, u0.w)));
+                const float z1 = fmaf(u1.x, ray.px, fmaf(u1.y, ray.py, fmaf(u1.z, ray.pz, u1.w)));
                 if (SPLIT)
-                    pack_split<F16>(sin_r(z0), sin_r(z1), pk[q], pl[q]);
+                    pack_split<F16>(sin_fast(z0), sin_fast(z1), pk[q], pl[q]);
                 else
-                    pk[q] = pack16x2<F16>(sin_r(z0), sin_r(z1));
+                    pk[q] = pack16x2<F16>(sin_fast(z0), sin_fast(z1));
             }
             const uint32_t off = sw128_chunk_offset(tid, k8, 128);
             st_shared_v4(x_s + off, pk[0], pk[1], pk[2], pk[3]);
@@ -216,10 +216,13 @@ __global__ void __launch_bounds__(kTraceThreads) trace_level_tc_kernel(const Lev
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         uint32_t pk[4], pl[4];
+                        const float4 ba = reinterpret_cast<const float4*>(bl + c0)[2 * q];
+                        const float4 bb = reinterpret_cast<const float4*>(bl + c0)[2 * q + 1];
+                        const float b8[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const int j = q * 8 + 2 * e;
-                            const float s0 = sin_r(v[j] + bl[c0 + j]), s1 = sin_r(v[j + 1] + bl[c0 + j + 1]);
+                            const float s0 = sin_fast(v[j] + b8[2 * e]), s1 = sin_fast(v[j + 1] + b8[2 * e + 1]);
                             if (SPLIT)
                                 pack_split<F16>(s0, s1, pk[e], pl[e]);
                             else
@@ -241,7 +244,14 @@ __global__ void __launch_bounds__(kTraceThreads) trace_level_tc_kernel(const Lev
                     tmem_ld32(tmem + lane_base + c0, v);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) dot = fmaf(wos[c0 + j], sin_r(v[j] + bl[c0 + j]), dot);
+                    for (int j4 = 0; j4 < 8; ++j4) {
+                        const float4 b4 = reinterpret_cast<const float4*>(bl + c0)[j4];
+                        const float4 w4 = reinterpret_cast<const float4*>(wos + c0)[j4];
+                        dot = fmaf(w4.x, sin_fast(v[4 * j4 + 0] + b4.x), dot);
+                        dot = fmaf(w4.y, sin_fast(v[4 * j4 + 1] + b4.y), dot);
+                        dot = fmaf(w4.z, sin_fast(v[4 * j4 + 2] + b4.z), dot);
+                        dot = fmaf(w4.w, sin_fast(v[4 * j4 + 3] + b4.w), dot);
+                    }
                 }
                 f = dot + net.bout;
             }
@@ -359,9 +369,9 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
     for (int i = tid; i < W; i += kStreamThreads) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) w0s[i * 4 + c] = net.w0[i * net.in_dim + c];
-        w0s[i * 4 + 3] = 0.0f;
         float bb = net.b0[i];
         if (net.in_dim == 4) bb = fmaf(net.w0[i * 4 + 3], a.time, bb);
+        w0s[i * 4 + 3] = bb;  // layer 0 as float4 (w_x, w_y, w_z, b), time folded into b
         b0s[i] = bb;
         wos[i] = net.wout[i];
         for (int l = 0; l < KH; ++l) bhs[l * W + i] = net.bh[l][i];
@@ -423,11 +433,11 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int e0 = k8 * 8 + 2 * q, e1 = e0 + 1;
-                    const float z0 = fmaf(w0s[e0 * 4 + 0], ray.px,
-                                          fmaf(w0s[e0 * 4 + 1], ray.py, fmaf(w0s[e0 * 4 + 2], ray.pz, b0s[e0])));
-                    const float z1 = fmaf(w0s[e1 * 4 + 0], ray.px,
-                                          fmaf(w0s[e1 * 4 + 1], ray.py, fmaf(w0s[e1 * 4 + 2], ray.pz, b0s[e1])));
-                    pk[q] = pack16x2<F16>(sin_r(z0), sin_r(z1));
+                    const float4 u0 = reinterpret_cast<const float4*>(w0s)[e0];
+                    const float4 u1 = reinterpret_cast<const float4*>(w0s)[e1];
+                    const float z0 = fmaf(u0.x, ray.px, fmaf(u0.y, ray.py, fmaf(u0.z, ray.pz, u0.w)));
+                    const float z1 = fmaf(u1.x, ray.px, fmaf(u1.y, ray.py, fmaf(u1.z, ray.pz, u1.w)));
+                    pk[q] = pack16x2<F16>(sin_fast(z0), sin_fast(z1));
                 }
                 st_shared_v4(x_s + sw128_chunk_offset(tid, k8, 128), pk[0], pk[1], pk[2], pk[3]);
             }
@@ -466,10 +476,13 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             uint32_t pk[4];
+                            const float4 ba = reinterpret_cast<const float4*>(bl + c0)[2 * q];
+                            const float4 bb = reinterpret_cast<const float4*>(bl + c0)[2 * q + 1];
+                            const float b8[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
                                 const int j = q * 8 + 2 * e;
-                                pk[e] = pack16x2<F16>(sin_r(v[j] + bl[c0 + j]), sin_r(v[j + 1] + bl[c0 + j + 1]));
+                                pk[e] = pack16x2<F16>(sin_fast(v[j] + b8[2 * e]), sin_fast(v[j + 1] + b8[2 * e + 1]));
                             }
                             st_shared_v4(x_s + sw128_chunk_offset(tid, (c0 >> 3) + q, 128), pk[0], pk[1], pk[2],
                                          pk[3]);
@@ -485,7 +498,14 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
                         tmem_ld32(tmem + lane_base + c0, v);
                         tmem_wait_ld();
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) dot = fmaf(wos[c0 + j], sin_r(v[j] + bl[c0 + j]), dot);
+                        for (int j4 = 0; j4 < 8; ++j4) {
+                            const float4 b4 = reinterpret_cast<const float4*>(bl + c0)[j4];
+                            const float4 w4 = reinterpret_cast<const float4*>(wos + c0)[j4];
+                            dot = fmaf(w4.x, sin_fast(v[4 * j4 + 0] + b4.x), dot);
+                            dot = fmaf(w4.y, sin_fast(v[4 * j4 + 1] + b4.y), dot);
+                            dot = fmaf(w4.z, sin_fast(v[4 * j4 + 2] + b4.z), dot);
+                            dot = fmaf(w4.w, sin_fast(v[4 * j4 + 3] + b4.w), dot);
+                        }
                     }
                     f = dot + net.bout;
                 }
@@ -528,19 +548,19 @@ struct GradCfg {
     static constexpr int HPTS = 32;                 // points per half
     static constexpr int NROWS = 4 * NPTS;          // rows of X (point-streams)
     static constexpr int HROWS = 4 * HPTS;          // rows of X per half = MMA N
-    static constexpr int NS = (W == 256) ? 2 : 4;   // weight ring stages
+    static constexpr int NS = (W == 256) ? 5 : 8;   // weight ring stages (one K block of one TMEM tile each)
     static constexpr int GROUP_WARPS = 4 * MT;      // epilogue warps per half
     static constexpr int GROUP_THREADS = GROUP_WARPS * 32;
     static constexpr int EPI_WARPS = 2 * GROUP_WARPS;
     static constexpr int PRODUCER_WARP = EPI_WARPS;
     static constexpr int MMA_WARP = EPI_WARPS + 1;
     static constexpr int THREADS = (EPI_WARPS + 2) * 32;
-    static constexpr uint32_t STAGE_BYTES = ROWS * 128u;
+    static constexpr uint32_t STAGE_BYTES = 128u * 128u;  // 128 feature rows x 64 K (16-bit)
     static constexpr int TMEM_COLS = MT * 256;      // per TMEM tile: half 0 at +0, half 1 at +128
 };
 
 struct GradLayout {
-    uint32_t x, ring, woutb, w0, b0, bh, pts, idx, bars, misc, total;
+    uint32_t x, ring, woutb, w0, bh, pts, idx, bars, misc, total;
 };
 
 template <int W>
@@ -556,8 +576,6 @@ __host__ __device__ inline GradLayout grad_layout(int KH) {
     o += C::KB * 16u * 128u;
     L.w0 = o;
     o += W * 4u * 4u;
-    L.b0 = o;
-    o += W * 4u;
     L.bh = o;
     o += static_cast<uint32_t>(KH) * W * 4u;
     L.pts = o;
@@ -577,6 +595,35 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// Stores the four stream values of two points (pe = even point, po = pe + 1)
+// of this thread's feature m into X as 32-bit words, together with lane m^1:
+// the even lane writes the rows of pe, the odd lane those of po, each word
+// holding features (m & ~1, m | 1).  One exchange of two packed words per
+// point pair; rows of pe and po fall in different 64-byte halves of the
+// swizzled layout, so a warp's store is a single conflict-free wavefront.
+template <bool F16, int NROWS>
+__device__ __forceinline__ void store_pair(uint32_t x_s, int m, int lane, int pe, const float (&ve)[4],
+                                           const float (&vo)[4]) {
+    const bool odd = lane & 1;
+    const uint32_t e01 = pack16x2<F16>(ve[0], ve[1]), e23 = pack16x2<F16>(ve[2], ve[3]);
+    const uint32_t o01 = pack16x2<F16>(vo[0], vo[1]), o23 = pack16x2<F16>(vo[2], vo[3]);
+    // the even lane keeps its even-point values and sends its odd-point values; the odd lane the reverse
+    const uint32_t k01 = odd ? o01 : e01, k23 = odd ? o23 : e23;
+    const uint32_t r01 = __shfl_xor_sync(0xffffffffu, odd ? e01 : o01, 1);
+    const uint32_t r23 = __shfl_xor_sync(0xffffffffu, odd ? e23 : o23, 1);
+    // low half of a word = feature m & ~1 (the even lane), high half = m | 1
+    const uint32_t lo01 = odd ? r01 : k01, hi01 = odd ? k01 : r01;
+    const uint32_t lo23 = odd ? r23 : k23, hi23 = odd ? k23 : r23;
+    const uint32_t w0 = prmt(lo01, hi01, 0x5410u), w1 = prmt(lo01, hi01, 0x7632u);
+    const uint32_t w2 = prmt(lo23, hi23, 0x5410u), w3 = prmt(lo23, hi23, 0x7632u);
+    const int p = pe + (odd ? 1 : 0);
+    const int m0 = m & ~1;
+    st_shared_u32(x_s + sw128_offset(p * 4 + 0, m0, NROWS), w0);
+    st_shared_u32(x_s + sw128_offset(p * 4 + 1, m0, NROWS), w1);
+    st_shared_u32(x_s + sw128_offset(p * 4 + 2, m0, NROWS), w2);
+    st_shared_u32(x_s + sw128_offset(p * 4 + 3, m0, NROWS), w3);
+}
+
 template <int W, bool F16>
 __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const GradArgs a) {
     using C = GradCfg<W>;
@@ -588,7 +635,6 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
     const int KH = net.n_hidden;
     const GradLayout L = grad_layout<W>(KH);
     float* w0s = reinterpret_cast<float*>(base + L.w0);
-    float* b0s = reinterpret_cast<float*>(base + L.b0);
     float* bhs = reinterpret_cast<float*>(base + L.bh);
     float* pts = reinterpret_cast<float*>(base + L.pts);
     int* idxs = reinterpret_cast<int*>(base + L.idx);
@@ -618,13 +664,13 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
         tmem_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
         tmem_relinquish();
     }
+    // layer 0 as float4 (w_x, w_y, w_z, b) per unit, the time input folded into b
     for (int i = tid; i < W; i += C::THREADS) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) w0s[i * 4 + c] = net.w0[i * net.in_dim + c];
-        w0s[i * 4 + 3] = 0.0f;
         float bb = net.b0[i];
         if (net.in_dim == 4) bb = fmaf(net.w0[i * 4 + 3], a.time, bb);
-        b0s[i] = bb;
+        w0s[i * 4 + 3] = bb;
         for (int l = 0; l < KH; ++l) bhs[l * W + i] = net.bh[l][i];
     }
     // w_out split into a 16-bit head (row 0) and the 16-bit rounding of its
@@ -657,16 +703,18 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
 
         if (warp == C::PRODUCER_WARP) {
             if (lane == 0) {
-                // K blocks in MMA order: layer by layer, each layer once per half
-                for (int st = 0; st < KH * 2 * C::KB && ok; ++st, ++g_prod) {
+                // stages in MMA order: layer, half, K block, TMEM tile
+                const int per_layer = 2 * C::KB * C::MT;
+                for (int st = 0; st < KH * per_layer && ok; ++st, ++g_prod) {
                     const uint32_t stage = g_prod % C::NS, use = g_prod / C::NS;
                     if (use > 0) ok = mbar_wait_bounded(bar_empty + 8u * stage, (use - 1) & 1u, a.status, abort_flag);
                     if (!ok) break;
-                    const int l = st / (2 * C::KB), kb = st % C::KB;
+                    const int l = st / per_layer, r = st % (C::KB * C::MT);
+                    const int kb = r / C::MT, mt = r % C::MT;
                     mbar_arrive_expect_tx(bar_full + 8u * stage, C::STAGE_BYTES);
                     bulk_g2s(ring_s + stage * C::STAGE_BYTES,
                              net.wbf + static_cast<size_t>(l) * net.wbf_layer_bytes +
-                                 static_cast<size_t>(kb) * net.rows_pad * 128u,
+                                 static_cast<size_t>(kb) * net.rows_pad * 128u + static_cast<size_t>(mt) * 128u * 128u,
                              C::STAGE_BYTES, bar_full + 8u * stage);
                 }
             }
@@ -683,21 +731,20 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
                         const uint32_t xh = x_s + h * C::HROWS * 128u;  // rows of this half within each K block
                         if (l < KH) {
                             // D[mt][h] = W_l[mt rows] . X_h^T over all K blocks
-                            for (int kb = 0; kb < C::KB && ok; ++kb, ++g_mma) {
-                                const uint32_t stage = g_mma % C::NS, use = g_mma / C::NS;
-                                ok = mbar_wait_bounded(bar_full + 8u * stage, use & 1u, a.status, abort_flag);
-                                if (!ok) break;
-                                tc_fence_after();
-#pragma unroll
-                                for (int mt = 0; mt < C::MT; ++mt)
+                            for (int kb = 0; kb < C::KB && ok; ++kb) {
+                                for (int mt = 0; mt < C::MT && ok; ++mt, ++g_mma) {
+                                    const uint32_t stage = g_mma % C::NS, use = g_mma / C::NS;
+                                    ok = mbar_wait_bounded(bar_full + 8u * stage, use & 1u, a.status, abort_flag);
+                                    if (!ok) break;
+                                    tc_fence_after();
 #pragma unroll
                                     for (int kk = 0; kk < 4; ++kk)
                                         mma_f16kind(tmem + mt * 256u + h * 128u,
-                                                    desc_kmajor_sw128(ring_s + stage * C::STAGE_BYTES +
-                                                                      mt * 128u * 128u + kk * 32u),
+                                                    desc_kmajor_sw128(ring_s + stage * C::STAGE_BYTES + kk * 32u),
                                                     desc_kmajor_sw128(xh + kb * C::NROWS * 128u + kk * 32u), idesc_h,
                                                     (kb | kk) != 0);
-                                mma_commit(bar_empty + 8u * stage);
+                                    mma_commit(bar_empty + 8u * stage);
+                                }
                             }
                         } else {
                             // output layer of this half: rows = its 128 point-streams, N = 16 (w_out head, remainder)
@@ -718,6 +765,7 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
             const int h = warp / C::GROUP_WARPS, ge = warp % C::GROUP_WARPS;
             const int mt = ge >> 2, quad = ge & 3;
             const int m = mt * 128 + quad * 32 + lane;
+            const bool live = m < W;  // warp-uniform: W is a multiple of 32
             const int gt = ge * 32 + lane;  // thread index within the group
             const uint32_t lane_addr = tmem + (static_cast<uint32_t>(quad * 32) << 16) + mt * 256u + h * 128u;
             const int p0 = h * C::HPTS;
@@ -732,16 +780,24 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
             }
             named_barrier(1 + h, C::GROUP_THREADS);
             // input layer: P_0 = sin(A_0), G_0^c = W_0[:, c] (.) cos(A_0)
-            if (m < W) {
-                const float wx = w0s[m * 4 + 0], wy = w0s[m * 4 + 1], wz = w0s[m * 4 + 2], bb = b0s[m];
-                for (int p = p0; p < p0 + C::HPTS; ++p) {
-                    const float z = fmaf(wx, pts[p * 3 + 0], fmaf(wy, pts[p * 3 + 1], fmaf(wz, pts[p * 3 + 2], bb)));
-                    float s, c;
-                    sincos_r(z, &s, &c);
-                    st_shared_u16(x_s + sw128_offset(p * 4 + 0, m, C::NROWS), bits16<F16>(s));
-                    st_shared_u16(x_s + sw128_offset(p * 4 + 1, m, C::NROWS), bits16<F16>(wx * c));
-                    st_shared_u16(x_s + sw128_offset(p * 4 + 2, m, C::NROWS), bits16<F16>(wy * c));
-                    st_shared_u16(x_s + sw128_offset(p * 4 + 3, m, C::NROWS), bits16<F16>(wz * c));
+            if (live) {
+                const float4 u = reinterpret_cast<const float4*>(w0s)[m];
+                for (int p = p0; p < p0 + C::HPTS; p += 2) {
+                    float ve[4], vo[4];
+                    {
+                        const float z = fmaf(u.x, pts[p * 3 + 0], fmaf(u.y, pts[p * 3 + 1], fmaf(u.z, pts[p * 3 + 2], u.w)));
+                        float s, c;
+                        sincos_fast(z, &s, &c);
+                        ve[0] = s; ve[1] = u.x * c; ve[2] = u.y * c; ve[3] = u.z * c;
+                    }
+                    {
+                        const int q = p + 1;
+                        const float z = fmaf(u.x, pts[q * 3 + 0], fmaf(u.y, pts[q * 3 + 1], fmaf(u.z, pts[q * 3 + 2], u.w)));
+                        float s, c;
+                        sincos_fast(z, &s, &c);
+                        vo[0] = s; vo[1] = u.x * c; vo[2] = u.y * c; vo[3] = u.z * c;
+                    }
+                    store_pair<F16, C::NROWS>(x_s, m, lane, p, ve, vo);
                 }
             }
             fence_proxy_async_smem();
@@ -753,23 +809,22 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
                 df_phase ^= 1u;
                 if (!ok) break;
                 tc_fence_after();
-                const float bb = m < W ? bhs[l * W + m] : 0.0f;
+                const float bb = live ? bhs[l * W + m] : 0.0f;
 #pragma unroll 1
                 for (int q = 0; q < C::HROWS / 32; ++q) {
                     float v[32];
                     tmem_ld32(lane_addr + q * 32u, v);
                     tmem_wait_ld();
-                    if (m < W) {
+                    if (live) {
 #pragma unroll
-                        for (int pp = 0; pp < 8; ++pp) {
+                        for (int pp = 0; pp < 8; pp += 2) {
                             // P_i = sin(A_i);  G_i = (W_i G_{i-1}) (.) cos(A_i)
-                            const int p = p0 + q * 8 + pp;
-                            float s, c;
-                            sincos_r(v[pp * 4] + bb, &s, &c);
-                            st_shared_u16(x_s + sw128_offset(p * 4 + 0, m, C::NROWS), bits16<F16>(s));
-                            st_shared_u16(x_s + sw128_offset(p * 4 + 1, m, C::NROWS), bits16<F16>(c * v[pp * 4 + 1]));
-                            st_shared_u16(x_s + sw128_offset(p * 4 + 2, m, C::NROWS), bits16<F16>(c * v[pp * 4 + 2]));
-                            st_shared_u16(x_s + sw128_offset(p * 4 + 3, m, C::NROWS), bits16<F16>(c * v[pp * 4 + 3]));
+                            float ve[4], vo[4], s, c;
+                            sincos_fast(v[pp * 4] + bb, &s, &c);
+                            ve[0] = s; ve[1] = c * v[pp * 4 + 1]; ve[2] = c * v[pp * 4 + 2]; ve[3] = c * v[pp * 4 + 3];
+                            sincos_fast(v[pp * 4 + 4] + bb, &s, &c);
+                            vo[0] = s; vo[1] = c * v[pp * 4 + 5]; vo[2] = c * v[pp * 4 + 6]; vo[3] = c * v[pp * 4 + 7];
+                            store_pair<F16, C::NROWS>(x_s, m, lane, p0 + q * 8 + pp, ve, vo);
                         }
                     }
                 }
