@@ -644,7 +644,6 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
     const uint32_t bar_dfull = bar_xready + 16u;           // 2 barriers (one per half)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.misc);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(base + L.misc + 4);
-    long long* tile_slot = reinterpret_cast<long long*>(base + L.misc + 8);
     const uint32_t x_s = base_s + L.x, ring_s = base_s + L.ring, wo_s = base_s + L.woutb;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -690,38 +689,43 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
+    // Static schedule: half-tiles of 32 points; CTA b takes the pairs b, b + G,
+    // b + 2G, ... (G = grid size) and half h of each pair is half-tile
+    // 2 * pair + h.  Both halves run the same number of pairs, so the MMA warp
+    // and the producer can follow a fixed alternation h0, h1 per layer; a
+    // half-tile beyond the work is computed with no valid points.
     const long long n_work = a.list ? static_cast<long long>(*a.count) : a.n;
-    uint32_t g_prod = 0, g_mma = 0;
-    uint32_t xr_phase[2] = {0u, 0u}, df_phase = 0;
+    const long long n_pairs = (n_work + 2 * C::HPTS - 1) / (2 * C::HPTS);
+    const long long G = gridDim.x;
+    const long long my_pairs = n_pairs > blockIdx.x ? (n_pairs - blockIdx.x + G - 1) / G : 0;
     bool ok = true;
 
-    while (true) {
-        if (tid == 0) *tile_slot = static_cast<long long>(atomicAdd(a.grab, 1ull));
-        const int stop = __syncthreads_or(*abort_flag != 0);
-        const long long base_pt = *tile_slot * C::NPTS;
-        if (stop || base_pt >= n_work) break;
-
-        if (warp == C::PRODUCER_WARP) {
-            if (lane == 0) {
-                // stages in MMA order: layer, half, K block, TMEM tile
-                const int per_layer = 2 * C::KB * C::MT;
-                for (int st = 0; st < KH * per_layer && ok; ++st, ++g_prod) {
-                    const uint32_t stage = g_prod % C::NS, use = g_prod / C::NS;
-                    if (use > 0) ok = mbar_wait_bounded(bar_empty + 8u * stage, (use - 1) & 1u, a.status, abort_flag);
-                    if (!ok) break;
-                    const int l = st / per_layer, r = st % (C::KB * C::MT);
-                    const int kb = r / C::MT, mt = r % C::MT;
-                    mbar_arrive_expect_tx(bar_full + 8u * stage, C::STAGE_BYTES);
-                    bulk_g2s(ring_s + stage * C::STAGE_BYTES,
-                             net.wbf + static_cast<size_t>(l) * net.wbf_layer_bytes +
-                                 static_cast<size_t>(kb) * net.rows_pad * 128u + static_cast<size_t>(mt) * 128u * 128u,
-                             C::STAGE_BYTES, bar_full + 8u * stage);
-                }
+    if (warp == C::PRODUCER_WARP) {
+        if (lane == 0) {
+            // stages in MMA order: per pair, per layer, per half, K block, TMEM tile
+            const int per_layer = 2 * C::KB * C::MT;
+            const long long total = my_pairs * KH * per_layer;
+            uint32_t g = 0;
+            for (long long st = 0; st < total && ok; ++st, ++g) {
+                const uint32_t stage = g % C::NS, use = g / C::NS;
+                if (use > 0) ok = mbar_wait_bounded(bar_empty + 8u * stage, (use - 1) & 1u, a.status, abort_flag);
+                if (!ok) break;
+                const int sl = static_cast<int>(st % (KH * per_layer));
+                const int l = sl / per_layer, r = sl % (C::KB * C::MT);
+                const int kb = r / C::MT, mt = r % C::MT;
+                mbar_arrive_expect_tx(bar_full + 8u * stage, C::STAGE_BYTES);
+                bulk_g2s(ring_s + stage * C::STAGE_BYTES,
+                         net.wbf + static_cast<size_t>(l) * net.wbf_layer_bytes +
+                             static_cast<size_t>(kb) * net.rows_pad * 128u + static_cast<size_t>(mt) * 128u * 128u,
+                         C::STAGE_BYTES, bar_full + 8u * stage);
             }
-        } else if (warp == C::MMA_WARP) {
-            if (lane == 0) {
-                constexpr uint32_t idesc_h = idesc_f32acc(128, C::HROWS, F16);
-                constexpr uint32_t idesc_o = idesc_f32acc(128, 16, F16);
+        }
+    } else if (warp == C::MMA_WARP) {
+        if (lane == 0) {
+            constexpr uint32_t idesc_h = idesc_f32acc(128, C::HROWS, F16);
+            constexpr uint32_t idesc_o = idesc_f32acc(128, 16, F16);
+            uint32_t g = 0, xr_phase[2] = {0u, 0u};
+            for (long long i = 0; i < my_pairs && ok; ++i) {
                 for (int l = 0; l <= KH && ok; ++l) {
                     for (int h = 0; h < 2 && ok; ++h) {
                         ok = mbar_wait_bounded(bar_xready + 8u * h, xr_phase[h], a.status, abort_flag);
@@ -732,8 +736,8 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
                         if (l < KH) {
                             // D[mt][h] = W_l[mt rows] . X_h^T over all K blocks
                             for (int kb = 0; kb < C::KB && ok; ++kb) {
-                                for (int mt = 0; mt < C::MT && ok; ++mt, ++g_mma) {
-                                    const uint32_t stage = g_mma % C::NS, use = g_mma / C::NS;
+                                for (int mt = 0; mt < C::MT && ok; ++mt, ++g) {
+                                    const uint32_t stage = g % C::NS, use = g / C::NS;
                                     ok = mbar_wait_bounded(bar_full + 8u * stage, use & 1u, a.status, abort_flag);
                                     if (!ok) break;
                                     tc_fence_after();
@@ -760,23 +764,27 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
                     }
                 }
             }
-        } else {
-            // epilogue group h: thread <-> feature row m of TMEM tile mt, points 32h .. 32h+31
-            const int h = warp / C::GROUP_WARPS, ge = warp % C::GROUP_WARPS;
-            const int mt = ge >> 2, quad = ge & 3;
-            const int m = mt * 128 + quad * 32 + lane;
-            const bool live = m < W;  // warp-uniform: W is a multiple of 32
-            const int gt = ge * 32 + lane;  // thread index within the group
-            const uint32_t lane_addr = tmem + (static_cast<uint32_t>(quad * 32) << 16) + mt * 256u + h * 128u;
-            const int p0 = h * C::HPTS;
+        }
+    } else {
+        // epilogue group h: thread <-> feature row m of TMEM tile mt, points 32h .. 32h+31 of X
+        const int h = warp / C::GROUP_WARPS, ge = warp % C::GROUP_WARPS;
+        const int mt = ge >> 2, quad = ge & 3;
+        const int m = mt * 128 + quad * 32 + lane;
+        const bool live = m < W;  // warp-uniform: W is a multiple of 32
+        const int gt = ge * 32 + lane;  // thread index within the group
+        const uint32_t lane_addr = tmem + (static_cast<uint32_t>(quad * 32) << 16) + mt * 256u + h * 128u;
+        const int p0 = h * C::HPTS;
+        uint32_t df_phase = 0;
+        for (long long i = 0; i < my_pairs; ++i) {
+            const long long base_pt = ((i * G + blockIdx.x) * 2 + h) * C::HPTS;
             if (gt < C::HPTS) {
-                const long long k = base_pt + p0 + gt;
-                int i = -1;
-                if (k < n_work) i = a.list ? a.list[k] : static_cast<int>(k);
-                idxs[p0 + gt] = i;
-                pts[(p0 + gt) * 3 + 0] = i >= 0 ? a.pts[i] : 0.0f;
-                pts[(p0 + gt) * 3 + 1] = i >= 0 ? a.pts[a.n + i] : 0.0f;
-                pts[(p0 + gt) * 3 + 2] = i >= 0 ? a.pts[2 * a.n + i] : 0.0f;
+                const long long k = base_pt + gt;
+                int idx = -1;
+                if (k < n_work) idx = a.list ? a.list[k] : static_cast<int>(k);
+                idxs[p0 + gt] = idx;
+                pts[(p0 + gt) * 3 + 0] = idx >= 0 ? a.pts[idx] : 0.0f;
+                pts[(p0 + gt) * 3 + 1] = idx >= 0 ? a.pts[a.n + idx] : 0.0f;
+                pts[(p0 + gt) * 3 + 2] = idx >= 0 ? a.pts[2 * a.n + idx] : 0.0f;
             }
             named_barrier(1 + h, C::GROUP_THREADS);
             // input layer: P_0 = sin(A_0), G_0^c = W_0[:, c] (.) cos(A_0)
@@ -786,16 +794,16 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
                     float ve[4], vo[4];
                     {
                         const float z = fmaf(u.x, pts[p * 3 + 0], fmaf(u.y, pts[p * 3 + 1], fmaf(u.z, pts[p * 3 + 2], u.w)));
-                        float s, c;
-                        sincos_fast(z, &s, &c);
-                        ve[0] = s; ve[1] = u.x * c; ve[2] = u.y * c; ve[3] = u.z * c;
+                        float sn, cs;
+                        sincos_fast(z, &sn, &cs);
+                        ve[0] = sn; ve[1] = u.x * cs; ve[2] = u.y * cs; ve[3] = u.z * cs;
                     }
                     {
                         const int q = p + 1;
                         const float z = fmaf(u.x, pts[q * 3 + 0], fmaf(u.y, pts[q * 3 + 1], fmaf(u.z, pts[q * 3 + 2], u.w)));
-                        float s, c;
-                        sincos_fast(z, &s, &c);
-                        vo[0] = s; vo[1] = u.x * c; vo[2] = u.y * c; vo[3] = u.z * c;
+                        float sn, cs;
+                        sincos_fast(z, &sn, &cs);
+                        vo[0] = sn; vo[1] = u.x * cs; vo[2] = u.y * cs; vo[3] = u.z * cs;
                     }
                     store_pair<F16, C::NROWS>(x_s, m, lane, p, ve, vo);
                 }
@@ -819,11 +827,11 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
 #pragma unroll
                         for (int pp = 0; pp < 8; pp += 2) {
                             // P_i = sin(A_i);  G_i = (W_i G_{i-1}) (.) cos(A_i)
-                            float ve[4], vo[4], s, c;
-                            sincos_fast(v[pp * 4] + bb, &s, &c);
-                            ve[0] = s; ve[1] = c * v[pp * 4 + 1]; ve[2] = c * v[pp * 4 + 2]; ve[3] = c * v[pp * 4 + 3];
-                            sincos_fast(v[pp * 4 + 4] + bb, &s, &c);
-                            vo[0] = s; vo[1] = c * v[pp * 4 + 5]; vo[2] = c * v[pp * 4 + 6]; vo[3] = c * v[pp * 4 + 7];
+                            float ve[4], vo[4], sn, cs;
+                            sincos_fast(v[pp * 4] + bb, &sn, &cs);
+                            ve[0] = sn; ve[1] = cs * v[pp * 4 + 1]; ve[2] = cs * v[pp * 4 + 2]; ve[3] = cs * v[pp * 4 + 3];
+                            sincos_fast(v[pp * 4 + 4] + bb, &sn, &cs);
+                            vo[0] = sn; vo[1] = cs * v[pp * 4 + 5]; vo[2] = cs * v[pp * 4 + 6]; vo[3] = cs * v[pp * 4 + 7];
                             store_pair<F16, C::NROWS>(x_s, m, lane, p0 + q * 8 + pp, ve, vo);
                         }
                     }
@@ -847,8 +855,8 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
                 const float gz = __shfl_sync(0xffffffffu, val, g + 3);
                 const int p = p0 + ((32 * quad + lane) >> 2);
                 if ((lane & 3) == 0) {
-                    const int i = idxs[p];
-                    if (i >= 0) {
+                    const int idx = idxs[p];
+                    if (idx >= 0) {
                         float ox = gx, oy = gy, oz = gz;
                         if (a.normalize) {
                             const float len = sqrtf(gx * gx + gy * gy + gz * gz);
@@ -857,15 +865,17 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
                             oy *= inv;
                             oz *= inv;
                         }
-                        a.out[i] = ox;
-                        a.out[a.n + i] = oy;
-                        a.out[2 * a.n + i] = oz;
+                        a.out[idx] = ox;
+                        a.out[a.n + idx] = oy;
+                        a.out[2 * a.n + idx] = oz;
                     }
                 }
             }
             tc_fence_before();
+            // the next half-tile's point load overwrites idxs/pts of this half;
+            // the OR-barrier also makes the stop decision uniform over the group
+            if (bar_or(1 + h, C::GROUP_THREADS, !ok || *abort_flag != 0)) break;
         }
-        __syncthreads();
     }
 
     tc_fence_before();
