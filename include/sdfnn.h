@@ -151,6 +151,31 @@ int sdf_normal_map(sdf_net_t fine, const float *pts, const uint8_t *mask, int64_
 int sdf_render_host(const sdf_trace_params *params, sdf_net_t fine, const float *orig, const float *dir,
                     int64_t n, float *out_pos, uint8_t *out_hit, float *out_normal, void *cuda_stream);
 
+/* Multiscale sphere tracing that allocates no device memory.
+ *
+ * The paper has no counterpart: this is a convenience of the library.
+ * sdf_trace_multiscale takes the scratch it needs (work counters and the
+ * ray queues between levels) from the stream-ordered allocator on every
+ * call.  Some callers cannot allow that: render loops that forbid device
+ * allocation once they are running, or hosts whose device memory is owned
+ * by an allocator of their own.  This entry point has the same arguments,
+ * semantics and errors, but its scratch is one static device array inside
+ * the library (16 MB, present on every device that loads the library until
+ * the process exits).
+ *   - n may not exceed 2,097,152 rays (one 1920 x 1080 frame fits); a larger
+ *     n returns SDF_ERR_ARG before anything is launched.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current (cudaGetSymbolAddress); make that first call
+ *     before capturing any stream.
+ *   - Every call uses the same array: it zeroes the counters at its start,
+ *     and calls whose work overlaps on the GPU (other streams, other host
+ *     threads) race on it and corrupt each other's results.  Serialise them.
+ *   - Device-side timeouts of these launches are latched in the array, not
+ *     in the status word sdf_sync_status reads. */
+int sdf_trace_multiscale_noalloc(const sdf_trace_params *params, const float *orig, const float *dir, int64_t n,
+                                 float *out_pos, float *out_t, uint8_t *out_hit, uint16_t *out_iters,
+                                 void *cuda_stream);
+
 /* Synchronises the stream, then returns and clears the status word of the
  * current device (SDF_OK, or the first device-side error since the last call). */
 int sdf_sync_status(void *cuda_stream);

@@ -460,6 +460,55 @@ int grad_impl(sdf_net_t net, const float* pts, const uint8_t* mask, int64_t n, f
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Scratch for sdf_trace_multiscale_noalloc: work counters, a status word and
+// the two ray-index queues between levels, for at most kNoAllocMaxRays rays.
+// It is a static device array, so it exists on every device that loads this
+// library, from module load until the process exits (16 MB + 256 bytes).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoAllocMaxRays = int64_t(1) << 21;  // 2,097,152 rays: one 1920 x 1080 frame fits
+
+struct NoAllocLayout {
+    unsigned long long counters[2 * kMaxLevels];  // grab_j, count_j; zeroed at the start of every call
+    int status;                                   // device-side timeouts of this entry point
+    int pad[63];
+    int32_t lists[2][kNoAllocMaxRays];            // ping-pong ray-index queues between levels
+};
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocLayout)];
+
+struct NoAllocDevice {
+    bool ready = false;
+    int num_sms = 0;
+    NoAllocLayout* scratch = nullptr;  // device address of g_noalloc_scratch on this device
+};
+
+std::mutex g_noalloc_mutex;
+NoAllocDevice g_noalloc_dev[64];
+
+// Device address of the static scratch and the SM count of `dev`, looked up
+// once per device with that device current.  Allocates nothing.
+int noalloc_setup(int dev, NoAllocDevice* out) {
+    if (dev < 0 || dev >= 64) return fail(SDF_ERR_ARG, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    NoAllocDevice& d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
+        e = cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+        d.scratch = static_cast<NoAllocLayout*>(p);
+        d.ready = true;
+    }
+    *out = d;
+    return SDF_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int sdf_net_load_mem(const void* bytes, size_t n_bytes, int precision, int device, sdf_net_t* out) {
@@ -573,6 +622,91 @@ int sdf_sync_status(void* cuda_stream) {
         const int zero = 0;
         cudaMemcpy(di.d_status, &zero, sizeof(int), cudaMemcpyHostToDevice);
         return fail(status, "device reported status %d (a bounded wait expired)", status);
+    }
+    return SDF_OK;
+}
+
+int sdf_trace_multiscale_noalloc(const sdf_trace_params* P, const float* orig, const float* dir, int64_t n,
+                                 float* out_pos, float* out_t, uint8_t* out_hit, uint16_t* out_iters,
+                                 void* cuda_stream) {
+    // Same contract as sdf_trace_multiscale, with the scratch taken from the
+    // static array above instead of the stream-ordered allocator.
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (!P) return fail(SDF_ERR_ARG, "params is NULL");
+    if (n < 0 || n > kNoAllocMaxRays)
+        return fail(SDF_ERR_ARG, "n = %lld: sdf_trace_multiscale_noalloc handles at most %lld rays per call",
+                    static_cast<long long>(n), static_cast<long long>(kNoAllocMaxRays));
+    const int m = P->n_levels;
+    if (m < 1 || m > kMaxLevels) return fail(SDF_ERR_ARG, "n_levels = %d out of range 1..%d", m, kMaxLevels);
+    if (!P->nets || !P->delta || !P->max_iters) return fail(SDF_ERR_ARG, "nets, delta and max_iters are required");
+    if (!finite_pos(P->eps)) return fail(SDF_ERR_ARG, "eps must be finite and > 0");
+    if (!std::isfinite(P->box_min) || !std::isfinite(P->box_max) || !(P->box_min < P->box_max))
+        return fail(SDF_ERR_ARG, "box_min < box_max required");
+    if (P->final_mode != 0 && P->final_mode != 1) return fail(SDF_ERR_ARG, "final_mode must be 0 or 1");
+    if (!std::isfinite(P->time)) return fail(SDF_ERR_ARG, "time must be finite");
+    const int dev = P->nets[0] ? P->nets[0]->device : -1;
+    for (int j = 0; j < m; ++j) {
+        const sdf_net* net = P->nets[j];
+        if (!net) return fail(SDF_ERR_ARG, "nets[%d] is NULL", j);
+        if (net->device != dev) return fail(SDF_ERR_ARG, "networks live on different devices");
+        if (net->in_dim != P->nets[0]->in_dim) return fail(SDF_ERR_ARG, "networks differ in input dimension");
+        if (P->max_iters[j] < 0) return fail(SDF_ERR_ARG, "max_iters[%d] < 0", j);
+        const bool uses_delta = (j < m - 1) || P->final_mode == 1;
+        if (uses_delta && !finite_pos(P->delta[j])) return fail(SDF_ERR_ARG, "delta[%d] must be finite and > 0", j);
+        if (P->step_scale && !finite_pos(P->step_scale[j]))
+            return fail(SDF_ERR_ARG, "step_scale[%d] must be finite and > 0", j);
+        if (!P->step_scale && !(net->lipschitz > 0.0))
+            return fail(SDF_ERR_ARG, "nets[%d] has a zero Lipschitz bound; pass step_scale", j);
+        if (net->precision != SDF_FP32 && !tc_trace_supported(net->width, net->n_hidden))
+            return fail(SDF_ERR_UNSUPPORTED, "tensor-core tracing of a (%d,%d) network is not built", net->width,
+                        net->n_hidden);
+    }
+    DeviceGuard g(dev);
+    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", dev);
+    if (n == 0) return SDF_OK;
+    int rc;
+    if ((rc = check_device_ptr(orig, dev, "orig")) || (rc = check_device_ptr(dir, dev, "dir")) ||
+        (rc = check_device_ptr(out_pos, dev, "out_pos")) || (rc = check_device_ptr(out_t, dev, "out_t")) ||
+        (rc = check_device_ptr(out_hit, dev, "out_hit")))
+        return rc;
+    if (out_iters && (rc = check_device_ptr(out_iters, dev, "out_iters"))) return rc;
+    NoAllocDevice nd;
+    if ((rc = noalloc_setup(dev, &nd))) return rc;
+
+    // every call starts from zeroed counters; the queues need no clearing
+    cudaError_t e = cudaMemsetAsync(nd.scratch->counters, 0, sizeof(nd.scratch->counters), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(noalloc counters)");
+    unsigned long long* counters = nd.scratch->counters;
+    int32_t* lists[2] = {nd.scratch->lists[0], nd.scratch->lists[1]};
+    for (int j = 0; j < m; ++j) {
+        const sdf_net* net = P->nets[j];
+        const bool last = (j == m - 1);
+        LevelArgs la{};
+        la.net = view_of(net);
+        la.d = (last && P->final_mode == 0) ? 0.0f : P->delta[j];
+        la.scale = P->step_scale ? P->step_scale[j] : static_cast<float>(1.0 / net->lipschitz);
+        la.cap = P->max_iters[j];
+        la.is_last = last ? 1 : 0;
+        la.time = P->time;
+        la.eps = P->eps;
+        la.box_lo = P->box_min;
+        la.box_hi = P->box_max;
+        la.orig = orig;
+        la.dir = dir;
+        la.n = n;
+        la.out_pos = out_pos;
+        la.out_t = out_t;
+        la.out_hit = out_hit;
+        la.out_iters = out_iters;
+        la.in_list = j == 0 ? nullptr : lists[(j - 1) & 1];
+        la.in_count = j == 0 ? nullptr : &counters[kMaxLevels + j - 1];
+        la.out_list = last ? nullptr : lists[j & 1];
+        la.out_count = last ? nullptr : &counters[kMaxLevels + j];
+        la.grab = &counters[j];
+        la.status = &nd.scratch->status;
+        e = (net->precision != SDF_FP32) ? launch_trace_level_tc(la, nd.num_sms, s)
+                                         : launch_trace_level_simt(la, nd.num_sms, s);
+        if (e != cudaSuccess) return cuda_fail(e, "launching trace level");
     }
     return SDF_OK;
 }

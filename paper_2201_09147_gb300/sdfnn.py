@@ -22,7 +22,7 @@ ERRORS = {-1: "SDF_ERR_ARG", -2: "SDF_ERR_FILE", -3: "SDF_ERR_FORMAT", -4: "SDF_
 
 EXPORTS = ["sdf_net_load", "sdf_net_load_mem", "sdf_net_info", "sdf_net_set_time", "sdf_net_free",
            "sdf_trace_multiscale", "sdf_normals", "sdf_normal_map", "sdf_render_host", "sdf_sync_status",
-           "sdf_last_error"]
+           "sdf_last_error", "sdf_trace_multiscale_noalloc"]
 
 
 class SdfError(RuntimeError):
@@ -57,6 +57,7 @@ def lib():
         L.sdf_net_free.argtypes = [vp]
         L.sdf_net_free.restype = None
         L.sdf_trace_multiscale.argtypes = [C.POINTER(TraceParamsC), vp, vp, C.c_int64, vp, vp, vp, vp, vp]
+        L.sdf_trace_multiscale_noalloc.argtypes = [C.POINTER(TraceParamsC), vp, vp, C.c_int64, vp, vp, vp, vp, vp]
         L.sdf_normals.argtypes = [vp, vp, C.c_int64, vp, vp]
         L.sdf_normal_map.argtypes = [vp, vp, vp, C.c_int64, vp, vp]
         L.sdf_render_host.argtypes = [C.POINTER(TraceParamsC), vp, vp, vp, C.c_int64, vp, vp, vp, vp]
@@ -140,6 +141,27 @@ def trace_multiscale(nets, delta, max_iters, eps, orig, dirs, *, step_scale=None
     p, keep = make_params(nets, delta, max_iters, eps, step_scale, box, final_mode, time)
     _check(lib().sdf_trace_multiscale(C.byref(p), _ptr(orig), _ptr(dirs), n, _ptr(out_pos), _ptr(out_t),
                                       _ptr(out_hit), _ptr(out_iters), C.c_void_p(_stream(stream))))
+    del keep
+    return out_pos, out_t, out_hit, out_iters
+
+
+def trace_multiscale_noalloc(nets, delta, max_iters, eps, orig, dirs, *, step_scale=None, box=(-1.0, 1.0),
+                             final_mode=0, time=0.0, out_pos=None, out_t=None, out_hit=None, out_iters=None,
+                             want_iters=True, stream=None):
+    """Alg. 1 through sdf_trace_multiscale_noalloc: the library allocates no
+    device memory for the call (its scratch is a static device array, at most
+    2,097,152 rays per call; calls must not overlap on the GPU).  The output
+    tensors, if not given, are still created here by torch."""
+    n = orig.shape[1]
+    dev = orig.device
+    out_pos = torch.empty((3, n), dtype=torch.float32, device=dev) if out_pos is None else out_pos
+    out_t = torch.empty(n, dtype=torch.float32, device=dev) if out_t is None else out_t
+    out_hit = torch.empty(n, dtype=torch.uint8, device=dev) if out_hit is None else out_hit
+    if out_iters is None and want_iters:
+        out_iters = torch.empty(n, dtype=torch.uint16, device=dev)
+    p, keep = make_params(nets, delta, max_iters, eps, step_scale, box, final_mode, time)
+    _check(lib().sdf_trace_multiscale_noalloc(C.byref(p), _ptr(orig), _ptr(dirs), n, _ptr(out_pos), _ptr(out_t),
+                                              _ptr(out_hit), _ptr(out_iters), C.c_void_p(_stream(stream))))
     del keep
     return out_pos, out_t, out_hit, out_iters
 
