@@ -253,18 +253,19 @@ def main():
     total_evals = int(iters.to(torch.int64).sum().item())
     cw, ck = coarse[0].width, coarse[0].n_hidden
     sines_per_eval = (ck + 1) * cw
+    # DRAM bytes per launch from the committed ncu launch list, valid only for the kernel source it was taken on
     traffic_path = ROOT / "profiles" / "traffic.json"
-    traffic = None
+    traffic_tbl = {}
     if traffic_path.exists():
         tj = json.loads(traffic_path.read_text())
         if tj.get("source_sha") == source_sha(ROOT / "paper_2201_09147_gb300" / "csrc" / "tc.cu"):
-            traffic = tj.get("bytes_per_launch")
+            traffic_tbl = tj.get("bytes_per_launch", {})
     if nm_ms >= tr_ms:
         achieved = n_hit * normal_flops_per_point / (nm_ms / 1e3) / 1e12
         peak = pk["bf16_tflops_sustained"]
         roofline = {"kernel": "grad_tc_kernel<256> (neural normal mapping, (256,3))", "bound": "tensor",
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": traffic, "peak_source": f"{pk['source']} bf16 sustained",
+                    "traffic": traffic_tbl.get("grad_tc_kernel<256, 0>"), "peak_source": f"{pk['source']} bf16 sustained",
                     "work": f"{n_hit} points x {normal_flops_per_point} hidden-layer MMA flops"}
     else:
         # sine-bound: one MUFU sine per hidden unit per evaluation
@@ -272,7 +273,8 @@ def main():
         peak_gsin = 152 * 16 * sm_mhz * 1e6 / 1e9
         achieved = total_evals * sines_per_eval / (tr_ms / 1e3) / 1e9
         roofline = {"kernel": "trace_level_tc_kernel<64> (coarse (64,1) trace)", "bound": "alu", "achieved": achieved,
-                    "peak": peak_gsin, "unit": "Gsin/s", "frac": achieved / peak_gsin, "traffic": traffic,
+                    "peak": peak_gsin, "unit": "Gsin/s", "frac": achieved / peak_gsin,
+                    "traffic": traffic_tbl.get("trace_level_tc_kernel<64, 0, 1>"),
                     "peak_source": "152 SMs x 16 MUFU/clk x median SM clock",
                     "work": f"{total_evals} evaluations x {sines_per_eval} sines"}
 
