@@ -313,6 +313,28 @@ __device__ __forceinline__ float from16(uint16_t h) {
 }
 
 // ---------------------------------------------------------------------------
+// named barriers over a subset of the block's threads
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void bar_named(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// OR-reduction barrier over `nthreads` threads (named barrier `id`): true if
+// any participating thread passed pred.
+__device__ __forceinline__ bool bar_or(int id, int nthreads, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(static_cast<uint32_t>(pred)), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+// ---------------------------------------------------------------------------
 // warp-aggregated work distribution
 // ---------------------------------------------------------------------------
 // Every lane with `want` set receives a distinct index from *counter (one

@@ -43,17 +43,18 @@ struct TraceLayout {
     uint32_t x, xlo, w, wlo, w0, b0, bh, wout, bars, misc, total;
 };
 
-// Shared-memory layout of the resident-weight trace kernel.  With `split`
-// the activations and weights are each held as a 16-bit head plus the
-// 16-bit rounding of the remainder (two operand copies).
-__host__ __device__ inline TraceLayout trace_layout(int W, int KH, bool split = false) {
+// Shared-memory layout of the resident-weight trace kernel with T ray tiles
+// (128 rays each) sharing one copy of the weights.  With `split` the
+// activations and weights are each held as a 16-bit head plus the 16-bit
+// rounding of the remainder (two operand copies).
+__host__ __device__ inline TraceLayout trace_layout(int W, int KH, bool split, int T) {
     TraceLayout L;
     uint32_t o = 0;
     const uint32_t xbytes = 128u * W * 2u, wbytes = static_cast<uint32_t>(KH) * W * W * 2u;
     L.x = o;
-    o += xbytes;
+    o += xbytes * T;
     L.xlo = o;
-    o += split ? xbytes : 0u;
+    o += split ? xbytes * T : 0u;
     L.w = o;
     o += wbytes;
     L.wlo = o;
@@ -67,7 +68,8 @@ __host__ __device__ inline TraceLayout trace_layout(int W, int KH, bool split = 
     L.wout = o;
     o += W * 4u;
     L.bars = o;
-    o += 64u;
+    o += 8u * (1 + 8);
+    o = (o + 15u) & ~15u;
     L.misc = o;
     o += 64u;
     L.total = o;
@@ -75,13 +77,21 @@ __host__ __device__ inline TraceLayout trace_layout(int W, int KH, bool split = 
 }
 
 constexpr uint32_t kSplitSmemLimit = 200u * 1024u;
+constexpr int kMaxTraceTiles = 6;
+constexpr int kTraceMaxThreads = 128 * kMaxTraceTiles;
 
 // The trace kernel's tensor pipe is mostly idle (its time goes to the sines),
 // so whenever the doubled operands fit it computes each hidden layer as
 // hi(W) hi(X) + lo(W) hi(X) + hi(W) lo(X) with hi/lo the 16-bit head and
 // remainder: the contraction then carries ~16 (BF16) or ~22 (FP16)
 // significant bits instead of 8 or 11.
-inline bool trace_split(int W, int KH) { return trace_layout(W, KH, true).total + 1024 <= kSplitSmemLimit; }
+inline bool trace_split(int W, int KH) { return trace_layout(W, KH, true, 1).total + 1024 <= kSplitSmemLimit; }
+
+__host__ __device__ inline uint32_t tmem_cols_for(int cols) {
+    uint32_t n = 32;
+    while (n < static_cast<uint32_t>(cols)) n <<= 1;
+    return n;
+}
 
 // 16-bit head and remainder of two floats, packed as pairs.
 template <bool F16>
@@ -92,36 +102,46 @@ __device__ __forceinline__ void pack_split(float a, float b, uint32_t& hi, uint3
     lo = pack16x2<F16>(a - ah, b - bh);
 }
 
+// T = blockDim.x / 128 independent ray tiles per CTA.  Tile t owns warps
+// 4t..4t+3 (so its threads read TMEM lanes 0..127), TMEM columns
+// [t*W, (t+1)*W), its own activation buffers, MMA mbarrier and named barrier
+// 1 + t; the weights and layer parameters are shared.
 template <int W, bool F16, bool SPLIT>
-__global__ void __launch_bounds__(kTraceThreads) trace_level_tc_kernel(const LevelArgs a) {
+__global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(const LevelArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const uint32_t raw_s = smem_u32(smem_raw);
     const uint32_t base_s = (raw_s + 1023u) & ~1023u;
     uint8_t* base = smem_raw + (base_s - raw_s);
     const NetView& net = a.net;
     const int KH = net.n_hidden;
-    const TraceLayout L = trace_layout(W, KH, SPLIT);
+    const int T = blockDim.x >> 7;
+    const TraceLayout L = trace_layout(W, KH, SPLIT, T);
     float* w0s = reinterpret_cast<float*>(base + L.w0);
     float* b0s = reinterpret_cast<float*>(base + L.b0);
     float* bhs = reinterpret_cast<float*>(base + L.bh);
     float* wos = reinterpret_cast<float*>(base + L.wout);
-    const uint32_t bar_w = base_s + L.bars, bar_mma = base_s + L.bars + 8;
+    const uint32_t bar_w = base_s + L.bars;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.misc);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(base + L.misc + 8);
     const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t x_s = base_s + L.x, w_s = base_s + L.w, xlo_s = base_s + L.xlo, wlo_s = base_s + L.wlo;
+    const int tile = tid >> 7, ttid = tid & 127, twarp = ttid >> 5;
+    constexpr uint32_t xbytes = 128u * W * 2u;
+    const uint32_t bar_mma = base_s + L.bars + 8u * (1 + tile);
+    const uint32_t x_s = base_s + L.x + tile * xbytes, xlo_s = base_s + L.xlo + tile * xbytes;
+    const uint32_t w_s = base_s + L.w, wlo_s = base_s + L.wlo;
+    const uint32_t tcols = tmem_cols_for(T * W);
 
     if (tid == 0) {
         mbar_init(bar_w, 1);
-        mbar_init(bar_mma, 1);
+        for (int t = 0; t < T; ++t) mbar_init(base_s + L.bars + 8u * (1 + t), 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
     if (warp == 0) {
-        tmem_alloc(smem_u32(tmem_slot), W);
+        tmem_alloc(smem_u32(tmem_slot), tcols);
         tmem_relinquish();
     }
-    for (int i = tid; i < W; i += kTraceThreads) {
+    for (int i = tid; i < W; i += blockDim.x) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) w0s[i * 4 + c] = net.w0[i * net.in_dim + c];
         float bb = net.b0[i];
@@ -134,7 +154,7 @@ __global__ void __launch_bounds__(kTraceThreads) trace_level_tc_kernel(const Lev
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
+    const uint32_t tmem = *tmem_slot + static_cast<uint32_t>(tile * W);
 
     if (tid == 0) {
         mbar_arrive_expect_tx(bar_w, static_cast<uint32_t>(KH) * W * W * 2u * (SPLIT ? 2u : 1u));
@@ -148,19 +168,20 @@ __global__ void __launch_bounds__(kTraceThreads) trace_level_tc_kernel(const Lev
     bool ok = mbar_wait_bounded(bar_w, 0, a.status, abort_flag);
 
     const long long n_work = a.in_list ? static_cast<long long>(*a.in_count) : a.n;
-    const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+    const uint32_t lane_base = static_cast<uint32_t>(twarp * 32) << 16;
     constexpr uint32_t idesc = idesc_f32acc(128, W, F16);
     uint32_t mma_phase = 0;
+    const int bar_id = 1 + tile;
     Ray ray;
 
     while (ok) {
         refill_ray(a, ray, n_work);
-        if (!__syncthreads_or(ray.state == kSlotActive)) break;
+        if (!bar_or(bar_id, 128, ray.state == kSlotActive)) break;
         if (a.cap <= 0) {
             pass_ray(a, ray);
             continue;
         }
-        // layer 0 (FP32): row tid of X = 16-bit sin(W_0 p + b_0)
+        // layer 0 (FP32): row ttid of X = 16-bit sin(W_0 p + b_0)
         for (int k8 = 0; k8 < W / 8; ++k8) {
             uint32_t pk[4], pl[4];
 #pragma unroll
@@ -175,17 +196,17 @@ __global__ void __launch_bounds__(kTraceThreads) trace_level_tc_kernel(const Lev
                 else
                     pk[q] = pack16x2<F16>(sin_fast(z0), sin_fast(z1));
             }
-            const uint32_t off = sw128_chunk_offset(tid, k8, 128);
+            const uint32_t off = sw128_chunk_offset(ttid, k8, 128);
             st_shared_v4(x_s + off, pk[0], pk[1], pk[2], pk[3]);
             if (SPLIT) st_shared_v4(xlo_s + off, pl[0], pl[1], pl[2], pl[3]);
         }
         fence_proxy_async_smem();
         tc_fence_before();
-        __syncthreads();
+        bar_named(bar_id, 128);
 
         float f = 0.0f;
         for (int l = 0; l < KH; ++l) {
-            if (tid == 0) {
+            if (ttid == 0) {
                 tc_fence_after();
                 const uint32_t wl = w_s + l * W * W * 2u, wll = wlo_s + l * W * W * 2u;
 #pragma unroll
@@ -228,14 +249,14 @@ __global__ void __launch_bounds__(kTraceThreads) trace_level_tc_kernel(const Lev
                             else
                                 pk[e] = pack16x2<F16>(s0, s1);
                         }
-                        const uint32_t off = sw128_chunk_offset(tid, (c0 >> 3) + q, 128);
+                        const uint32_t off = sw128_chunk_offset(ttid, (c0 >> 3) + q, 128);
                         st_shared_v4(x_s + off, pk[0], pk[1], pk[2], pk[3]);
                         if (SPLIT) st_shared_v4(xlo_s + off, pl[0], pl[1], pl[2], pl[3]);
                     }
                 }
                 fence_proxy_async_smem();
                 tc_fence_before();
-                __syncthreads();
+                bar_named(bar_id, 128);
             } else {
                 // output layer in FP32: f = w_out . sin(D + b) + b_out
                 float dot = 0.0f;
@@ -265,7 +286,7 @@ __global__ void __launch_bounds__(kTraceThreads) trace_level_tc_kernel(const Lev
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, W);
+        tmem_dealloc(*tmem_slot, tcols);
     }
 }
 
@@ -309,24 +330,6 @@ __host__ __device__ inline StreamLayout stream_layout(int KH) {
     o += 32u;
     L.total = o;
     return L;
-}
-
-// OR-reduction barrier over the first `nthreads` threads (named barrier `id`).
-__device__ __forceinline__ bool bar_or(int id, int nthreads, bool pred) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 p, %1, 0;\n\t"
-        "barrier.red.or.pred q, %2, %3, p;\n\t"
-        "selp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"(static_cast<uint32_t>(pred)), "r"(id), "r"(nthreads)
-        : "memory");
-    return r != 0;
-}
-
-__device__ __forceinline__ void bar_named(int id, int nthreads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 template <bool F16>
@@ -591,10 +594,6 @@ __host__ __device__ inline GradLayout grad_layout(int KH) {
     return L;
 }
 
-__device__ __forceinline__ void named_barrier(int id, int nthreads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
 // Stores the four stream values of two points (pe = even point, po = pe + 1)
 // of this thread's feature m into X as 32-bit words, together with lane m^1:
 // the even lane writes the rows of pe, the odd lane those of po, each word
@@ -786,7 +785,7 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
                 pts[(p0 + gt) * 3 + 1] = idx >= 0 ? a.pts[a.n + idx] : 0.0f;
                 pts[(p0 + gt) * 3 + 2] = idx >= 0 ? a.pts[2 * a.n + idx] : 0.0f;
             }
-            named_barrier(1 + h, C::GROUP_THREADS);
+            bar_named(1 + h, C::GROUP_THREADS);
             // input layer: P_0 = sin(A_0), G_0^c = W_0[:, c] (.) cos(A_0)
             if (live) {
                 const float4 u = reinterpret_cast<const float4*>(w0s)[m];
@@ -936,13 +935,36 @@ bool tc_grad_supported(int width, int n_hidden) {
     return n_hidden >= 1 && n_hidden <= kMaxHidden && (width == 64 || width == 128 || width == 256);
 }
 
+// Ray tiles per CTA for the resident trace kernel: as many as shared memory,
+// registers, TMEM and the thread limit allow (all tiles share the weights).
+template <class Kernel>
+static int trace_tiles(Kernel k, int W, int KH, bool split) {
+    int dev = 0, smem_optin = 0, regs_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaFuncAttributes at;
+    if (cudaFuncGetAttributes(&at, k) != cudaSuccess) return 1;
+    const int regs_warp = ((at.numRegs * 32 + 255) / 256) * 256;
+    int T = kMaxTraceTiles;
+    while (T > 1 && (trace_layout(W, KH, split, T).total + 1024 > static_cast<uint32_t>(smem_optin) ||
+                     regs_warp * 4 * T > regs_sm || static_cast<int>(tmem_cols_for(T * W)) > 512))
+        --T;
+    return T;
+}
+
 template <int W, bool F16>
 static cudaError_t launch_trace_resident(const LevelArgs& a, int num_sms, cudaStream_t s) {
     const int KH = a.net.n_hidden;
     const bool split = a.net.wbf_lo != nullptr && trace_split(W, KH);
-    const size_t smem = trace_layout(W, KH, split).total + 1024;
-    if (split) return launch_tc(trace_level_tc_kernel<W, F16, true>, kTraceThreads, smem, W, num_sms, s, &a);
-    return launch_tc(trace_level_tc_kernel<W, F16, false>, kTraceThreads, smem, W, num_sms, s, &a);
+    if (split) {
+        auto k = trace_level_tc_kernel<W, F16, true>;
+        const int T = trace_tiles(k, W, KH, true);
+        return launch_tc(k, 128 * T, trace_layout(W, KH, true, T).total + 1024, tmem_cols_for(T * W), num_sms, s, &a);
+    }
+    auto k = trace_level_tc_kernel<W, F16, false>;
+    const int T = trace_tiles(k, W, KH, false);
+    return launch_tc(k, 128 * T, trace_layout(W, KH, false, T).total + 1024, tmem_cols_for(T * W), num_sms, s, &a);
 }
 
 cudaError_t launch_trace_level_tc(const LevelArgs& a, int num_sms, cudaStream_t s) {
