@@ -380,6 +380,69 @@ def main():
                                  "speedup_precision_only_multiscale": value / ws / ms_fp32_value}
         sdfnn.sync_status()
 
+        def timed_ms(fn, reps=5):
+            fn()
+            out = []
+            for _ in range(reps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                torch.cuda.synchronize()
+                out.append(a.elapsed_time(b))
+            return statistics.median(out)
+
+        # three-level normal mapping (the last row of Tab. 3) and its silhouette variant, 512 x 512, BF16
+        for name in ("three_level_512", "silhouette_512"):
+            w3 = workloads.get(name)
+            o3, d3 = (torch.from_numpy(x).cuda() for x in w3.rays())
+            n3 = [sdfnn.Net(b, sdfnn.SDF_BF16, local) for b in w3.level_bytes()]
+            f3 = sdfnn.Net(w3.fine_bytes(), sdfnn.SDF_BF16, local)
+            plan3 = sdfnn.Plan(n3, w3.delta, w3.caps, w3.eps, o3, d3, fine=f3, step_scale=w3.step_scale,
+                               final_mode=w3.final_mode, autotune=True, want_iters=False)
+            ms3 = timed_ms(plan3.launch, 20)
+            result["comparisons"][f"{name}_Mrays_s"] = w3.n_rays / (ms3 / 1e3) / 1e6
+            result["comparisons"][f"{name}_hits"] = int(plan3.hit.sum().item())
+            plan3.close()
+
+        # 32 animated frames of mixed sizes: one autotuned plan (CUDA graph) against per-frame calls
+        wa = workloads.get("animation_32")
+        if all((workloads.SCENES / f).exists() for f in wa.levels + [wa.fine]):
+            oa_h, da_h, ta_h, off = workloads.batch_rays(wa.frames)
+            oa, da, ta = (torch.from_numpy(x).cuda() for x in (oa_h, da_h, ta_h))
+            del oa_h, da_h
+            na = [sdfnn.Net(b, sdfnn.SDF_BF16, local) for b in wa.level_bytes()]
+            fa = sdfnn.Net(wa.fine_bytes(), sdfnn.SDF_BF16, local)
+            plan_a = sdfnn.Plan(na, wa.delta, wa.caps, wa.eps, oa, da, fine=fa, ray_time=ta,
+                                step_scale=wa.step_scale, final_mode=wa.final_mode, autotune=True, want_iters=False)
+            ms_plan = timed_ms(plan_a.launch, 5)
+            tiles, nodes = plan_a.info()
+            n_hits_a = int(plan_a.hit.sum().item())
+            plan_a.close()
+            frames = []
+            for k, (fw, fh, tk) in enumerate(wa.frames):
+                lo, hi = int(off[k]), int(off[k + 1])
+                frames.append((oa[:, lo:hi].contiguous(), da[:, lo:hi].contiguous(), float(tk)))
+
+            def per_frame():
+                for fo, fd, tk in frames:
+                    p_, _, h_, _ = sdfnn.trace_multiscale(na, wa.delta, wa.caps, wa.eps, fo, fd,
+                                                          step_scale=wa.step_scale, final_mode=wa.final_mode,
+                                                          time=tk, want_iters=False)
+                    fa.set_time(tk)
+                    sdfnn.normal_map(fa, p_, h_)
+
+            ms_frames = timed_ms(per_frame, 3)
+            result["comparisons"]["animation_32"] = {
+                "rays": wa.n_rays, "frames": "8 x 256^2, 16 x 1280x720, 8 x 1920x1080, t_k = k/31",
+                "plan_Mrays_s": wa.n_rays / (ms_plan / 1e3) / 1e6, "plan_ms": ms_plan,
+                "per_frame_calls_Mrays_s": wa.n_rays / (ms_frames / 1e3) / 1e6, "per_frame_calls_ms": ms_frames,
+                "autotuned_tiles": tiles, "graph_nodes": nodes, "hits": n_hits_a}
+            del frames, oa, da, ta
+        sdfnn.sync_status()
+
     if rank == 0 and not args.no_cpu_baseline:
         # FP64 oracle on a bounded sample of the same frame: speed, and the error of this run
         rows = np.arange(0, wl.height, ORACLE_ROW_STRIDE)

@@ -101,7 +101,10 @@ typedef struct {
     const float *step_scale;   /* m step scales s_j, or NULL for s_j = 1/L_j */
     float box_min, box_max;    /* rays are clipped to the cube [box_min, box_max]^3 */
     int final_mode;            /* 0: trace S_m (Alg. 1); 1: stop on the delta_m shell of f_m */
-    float time;                /* 4th input of 4-D networks */
+    float time;                /* 4th input of 4-D networks, the same for every ray */
+    const float *ray_time;     /* device, (n) float32: the 4th input of each ray, overriding `time`
+                                  (frames of an animation traced together, Sec. 3.2); NULL for none.
+                                  4-D networks only (SDF_ERR_ARG otherwise). */
 } sdf_trace_params;
 
 /* Multiscale sphere tracing (Sec. 4, Alg. 1) of n rays.
@@ -141,6 +144,13 @@ int sdf_normals(sdf_net_t net, const float *pts, int64_t n, float *out_grad, voi
 int sdf_normal_map(sdf_net_t fine, const float *pts, const uint8_t *mask, int64_t n, float *out_normal,
                    void *cuda_stream);
 
+/* sdf_normal_map of a 4-D network with a time per point: the 4th input of
+ * point i is pt_time[i] (device, (n) float32, not NULL).  The gradient is
+ * the spatial one (x, y, z), as for a 3-D network at that time.
+ * Errors: as sdf_normal_map; SDF_ERR_ARG for a 3-input network. */
+int sdf_normal_map_timed(sdf_net_t fine, const float *pts, const float *pt_time, const uint8_t *mask, int64_t n,
+                         float *out_normal, void *cuda_stream);
+
 /* One frame end to end from HOST memory: copies orig/dir to the device,
  * runs sdf_trace_multiscale and then sdf_normal_map(fine) on the hits, and
  * copies hit, end point and normal back.  Device buffers are taken from the
@@ -175,6 +185,65 @@ int sdf_render_host(const sdf_trace_params *params, sdf_net_t fine, const float 
 int sdf_trace_multiscale_noalloc(const sdf_trace_params *params, const float *orig, const float *dir, int64_t n,
                                  float *out_pos, float *out_t, uint8_t *out_hit, uint16_t *out_iters,
                                  void *cuda_stream);
+
+/* Frame-batch plans.
+ *
+ * The paper renders animations of 4-D networks frame by frame (Sec. 3.2,
+ * Sec. 6).  A plan renders a whole batch of frames - any mix of
+ * resolutions, each ray carrying its frame's time - as one unit: all
+ * levels of Alg. 1 over every ray of the batch (the level queues mix rays
+ * of all frames, so small frames never leave the GPU idle) followed by the
+ * normal mapping of the hits, captured once into a CUDA graph and replayed
+ * by sdf_plan_launch.  The buffers are fixed when the plan is made: write
+ * the next batch's rays into the same orig / dir / ray_time and launch
+ * again.
+ *
+ * sdf_plan_create(params, fine, batch, autotune, stream, &plan)
+ *   params   : as for sdf_trace_multiscale, copied; params->ray_time must
+ *              be NULL or equal to batch->ray_time.  The networks are not
+ *              copied: keep them alive while the plan exists.
+ *   fine     : network of the normal-mapping stage, or NULL with
+ *              batch->out_normal NULL (trace only).
+ *   batch    : the device buffers (all on the networks' device):
+ *              orig, dir (3, n); ray_time (n) or NULL; out_pos (3, n);
+ *              out_t (n); out_hit (n); out_iters (n) or NULL;
+ *              out_normal (3, n) or NULL.  The normals are those of
+ *              sdf_normal_map(_timed) with out_hit as the mask.
+ *   autotune : nonzero: before capturing, time every tile count (ray tiles
+ *              per CTA) of each tensor-core level on these buffers and keep
+ *              the fastest; the outputs are overwritten meanwhile and the
+ *              stream is synchronised.  0: the library's default counts.
+ *              The tile count changes the speed only: every ray's
+ *              arithmetic, and so every output bit, is the same.
+ *   stream   : stream of the autotuning runs (capture uses a private one).
+ *   The plan owns its scratch (device memory for the level queues and the
+ *   normal-map compaction: 8 * n + 12 * n bytes at most, from cudaMalloc).
+ * sdf_plan_launch: enqueues the graph on `stream`; device-side errors are
+ *   latched in the status word read by sdf_sync_status.  Launches of one plan
+ *   share its scratch, so launches on different streams must not overlap.
+ * sdf_plan_info: tile count per level (max_levels entries, 0 = default for
+ *   SIMT levels) and the number of graph nodes; either pointer may be NULL.
+ * sdf_plan_free: NULL is a no-op; no launch of the plan may be in flight.
+ * Errors: as sdf_trace_multiscale and sdf_normal_map, SDF_ERR_CUDA for a
+ * failed capture or instantiation; on error *plan is NULL. */
+typedef struct sdf_plan *sdf_plan_t;
+
+typedef struct {
+    const float *orig, *dir;
+    const float *ray_time;
+    int64_t n;
+    float *out_pos;
+    float *out_t;
+    uint8_t *out_hit;
+    uint16_t *out_iters;
+    float *out_normal;
+} sdf_frame_batch;
+
+int sdf_plan_create(const sdf_trace_params *params, sdf_net_t fine, const sdf_frame_batch *batch, int autotune,
+                    void *cuda_stream, sdf_plan_t *plan);
+int sdf_plan_launch(sdf_plan_t plan, void *cuda_stream);
+int sdf_plan_info(sdf_plan_t plan, int *tiles, int max_levels, int64_t *n_graph_nodes);
+void sdf_plan_free(sdf_plan_t plan);
 
 /* Synchronises the stream, then returns and clears the status word of the
  * current device (SDF_OK, or the first device-side error since the last call). */

@@ -1,5 +1,6 @@
 // C-ABI layer of libsdfnn: network loading and preparation, argument
 // validation, and orchestration of the kernels on the caller's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -325,8 +326,10 @@ struct Scratch {
     }
 };
 
-int trace_impl(const sdf_trace_params* P, const float* orig, const float* dir, int64_t n, float* out_pos,
-               float* out_t, uint8_t* out_hit, uint16_t* out_iters, cudaStream_t s) {
+// Checks the parameters and buffers of a trace; *dev receives the device of
+// the networks.  Device pointers are checked only when n > 0.
+int validate_trace(const sdf_trace_params* P, const float* orig, const float* dir, int64_t n, const float* out_pos,
+                   const float* out_t, const uint8_t* out_hit, const uint16_t* out_iters, int* dev_out) {
     if (!P) return fail(SDF_ERR_ARG, "params is NULL");
     if (n < 0 || n > 0x7fffffffLL) return fail(SDF_ERR_ARG, "n = %lld out of range", static_cast<long long>(n));
     const int m = P->n_levels;
@@ -354,31 +357,38 @@ int trace_impl(const sdf_trace_params* P, const float* orig, const float* dir, i
             return fail(SDF_ERR_UNSUPPORTED, "tensor-core tracing of a (%d,%d) network is not built", net->width,
                         net->n_hidden);
     }
+    if (P->ray_time && P->nets[0]->in_dim != 4) return fail(SDF_ERR_ARG, "ray_time given for 3-input networks");
+    *dev_out = dev;
+    if (n == 0) return SDF_OK;
     DeviceGuard g(dev);
     if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", dev);
-    if (n == 0) return SDF_OK;
     int rc;
     if ((rc = check_device_ptr(orig, dev, "orig")) || (rc = check_device_ptr(dir, dev, "dir")) ||
         (rc = check_device_ptr(out_pos, dev, "out_pos")) || (rc = check_device_ptr(out_t, dev, "out_t")) ||
         (rc = check_device_ptr(out_hit, dev, "out_hit")))
         return rc;
     if (out_iters && (rc = check_device_ptr(out_iters, dev, "out_iters"))) return rc;
-    DeviceInfo di;
-    if ((rc = device_info(dev, &di))) return rc;
+    if (P->ray_time && (rc = check_device_ptr(P->ray_time, dev, "ray_time"))) return rc;
+    return SDF_OK;
+}
 
-    // scratch: counters (grab_j, count_j) then two ray-index lists
-    const size_t counter_bytes = 2 * kMaxLevels * sizeof(unsigned long long);
-    const size_t list_bytes = (m > 1) ? static_cast<size_t>(n) * sizeof(int32_t) : 0;
-    Scratch sc;
-    sc.s = s;
-    cudaError_t e = cudaMallocAsync(&sc.ptr, counter_bytes + 2 * list_bytes + 256, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch)");
-    e = cudaMemsetAsync(sc.ptr, 0, counter_bytes, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    auto* counters = static_cast<unsigned long long*>(sc.ptr);
-    int32_t* lists[2] = {reinterpret_cast<int32_t*>(static_cast<uint8_t*>(sc.ptr) + counter_bytes),
-                         reinterpret_cast<int32_t*>(static_cast<uint8_t*>(sc.ptr) + counter_bytes + list_bytes)};
+// Bytes of trace scratch: 2 * kMaxLevels counters (grab_j, count_j), then
+// two ray-index queues of n entries when there is more than one level.
+size_t trace_scratch_bytes(int m, int64_t n) {
+    return 2 * kMaxLevels * sizeof(unsigned long long) + ((m > 1) ? 2 * static_cast<size_t>(n) * sizeof(int32_t) : 0);
+}
 
+// Zeroes the 2 * kMaxLevels counters and launches the levels of Alg. 1 on
+// `s` (the validated parameters' device current); list0 / list1 hold n
+// entries each (unused with one level).  tiles: per-level tile counts for
+// the tensor-core kernel, or NULL.
+int launch_levels_at(const sdf_trace_params* P, const float* orig, const float* dir, int64_t n, float* out_pos,
+                     float* out_t, uint8_t* out_hit, uint16_t* out_iters, unsigned long long* counters,
+                     int32_t* list0, int32_t* list1, int* status, int num_sms, const int* tiles, cudaStream_t s) {
+    const int m = P->n_levels;
+    cudaError_t e = cudaMemsetAsync(counters, 0, 2 * kMaxLevels * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");
+    int32_t* lists[2] = {list0, list1};
     for (int j = 0; j < m; ++j) {
         const sdf_net* net = P->nets[j];
         const bool last = (j == m - 1);
@@ -389,6 +399,8 @@ int trace_impl(const sdf_trace_params* P, const float* orig, const float* dir, i
         la.cap = P->max_iters[j];
         la.is_last = last ? 1 : 0;
         la.time = P->time;
+        la.ray_time = P->ray_time;
+        la.tiles = tiles ? tiles[j] : 0;
         la.eps = P->eps;
         la.box_lo = P->box_min;
         la.box_hi = P->box_max;
@@ -404,47 +416,80 @@ int trace_impl(const sdf_trace_params* P, const float* orig, const float* dir, i
         la.out_list = last ? nullptr : lists[j & 1];
         la.out_count = last ? nullptr : &counters[kMaxLevels + j];
         la.grab = &counters[j];
-        la.status = di.d_status;
-        e = (net->precision != SDF_FP32) ? launch_trace_level_tc(la, di.num_sms, s)
-                                         : launch_trace_level_simt(la, di.num_sms, s);
+        la.status = status;
+        e = (net->precision != SDF_FP32) ? launch_trace_level_tc(la, num_sms, s)
+                                         : launch_trace_level_simt(la, num_sms, s);
         if (e != cudaSuccess) return cuda_fail(e, "launching trace level");
     }
     return SDF_OK;
 }
 
-int grad_impl(sdf_net_t net, const float* pts, const uint8_t* mask, int64_t n, float* out, int normalize,
-              cudaStream_t s) {
+// launch_levels_at with the counters and queues laid out in one block of
+// trace_scratch_bytes(m, n) bytes.
+int launch_levels(const sdf_trace_params* P, const float* orig, const float* dir, int64_t n, float* out_pos,
+                  float* out_t, uint8_t* out_hit, uint16_t* out_iters, void* scratch, int* status, int num_sms,
+                  const int* tiles, cudaStream_t s) {
+    auto* counters = static_cast<unsigned long long*>(scratch);
+    int32_t* l0 = reinterpret_cast<int32_t*>(counters + 2 * kMaxLevels);
+    return launch_levels_at(P, orig, dir, n, out_pos, out_t, out_hit, out_iters, counters, l0, l0 + n, status,
+                            num_sms, tiles, s);
+}
+
+int trace_impl(const sdf_trace_params* P, const float* orig, const float* dir, int64_t n, float* out_pos,
+               float* out_t, uint8_t* out_hit, uint16_t* out_iters, cudaStream_t s) {
+    int dev = -1;
+    int rc = validate_trace(P, orig, dir, n, out_pos, out_t, out_hit, out_iters, &dev);
+    if (rc || n == 0) return rc;
+    DeviceGuard g(dev);
+    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", dev);
+    DeviceInfo di;
+    if ((rc = device_info(dev, &di))) return rc;
+    Scratch sc;
+    sc.s = s;
+    cudaError_t e = cudaMallocAsync(&sc.ptr, trace_scratch_bytes(P->n_levels, n) + 256, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch)");
+    return launch_levels(P, orig, dir, n, out_pos, out_t, out_hit, out_iters, sc.ptr, di.d_status, di.num_sms,
+                         nullptr, s);
+}
+
+// Checks a gradient / normal-map call (the network's device current when n > 0).
+int validate_grad(sdf_net_t net, const float* pts, const float* pt_time, const uint8_t* mask, int64_t n,
+                  const float* out) {
     if (!net) return fail(SDF_ERR_ARG, "net is NULL");
     if (n < 0 || n > 0x7fffffffLL) return fail(SDF_ERR_ARG, "n = %lld out of range", static_cast<long long>(n));
-    DeviceGuard g(net->device);
-    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", net->device);
+    if (pt_time && net->in_dim != 4) return fail(SDF_ERR_ARG, "per-point times given for a 3-input network");
+    if (net->precision != SDF_FP32 && !tc_grad_supported(net->width, net->n_hidden))
+        return fail(SDF_ERR_UNSUPPORTED, "tensor-core gradients of a (%d,%d) network are not built", net->width,
+                    net->n_hidden);
     if (n == 0) return SDF_OK;
     int rc;
     if ((rc = check_device_ptr(pts, net->device, "pts")) || (rc = check_device_ptr(out, net->device, "out")))
         return rc;
     if (mask && (rc = check_device_ptr(mask, net->device, "mask"))) return rc;
-    if (net->precision != SDF_FP32 && !tc_grad_supported(net->width, net->n_hidden))
-        return fail(SDF_ERR_UNSUPPORTED, "tensor-core gradients of a (%d,%d) network are not built", net->width,
-                    net->n_hidden);
-    DeviceInfo di;
-    if ((rc = device_info(net->device, &di))) return rc;
+    if (pt_time && (rc = check_device_ptr(pt_time, net->device, "time"))) return rc;
+    return SDF_OK;
+}
+
+// Bytes of gradient scratch: 4 counters, then a list of n indices with a mask.
+size_t grad_scratch_bytes(int64_t n, bool mask) {
+    return 4 * sizeof(unsigned long long) + (mask ? static_cast<size_t>(n) * sizeof(int32_t) : 0);
+}
+
+int launch_gradients(sdf_net_t net, const float* pts, const float* pt_time, const uint8_t* mask, int64_t n, float* out,
+                     int normalize, void* scratch, int* status, int num_sms, cudaStream_t s) {
     const size_t counter_bytes = 4 * sizeof(unsigned long long);
-    const size_t list_bytes = mask ? static_cast<size_t>(n) * sizeof(int32_t) : 0;
-    Scratch sc;
-    sc.s = s;
-    cudaError_t e = cudaMallocAsync(&sc.ptr, counter_bytes + list_bytes + 256, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch)");
-    e = cudaMemsetAsync(sc.ptr, 0, counter_bytes, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    auto* counters = static_cast<unsigned long long*>(sc.ptr);
-    int32_t* list = mask ? reinterpret_cast<int32_t*>(static_cast<uint8_t*>(sc.ptr) + counter_bytes) : nullptr;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, counter_bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");
+    auto* counters = static_cast<unsigned long long*>(scratch);
+    int32_t* list = mask ? reinterpret_cast<int32_t*>(static_cast<uint8_t*>(scratch) + counter_bytes) : nullptr;
     if (mask) {
-        e = launch_mask_compact(mask, n, list, &counters[1], out, di.num_sms, s);
+        e = launch_mask_compact(mask, n, list, &counters[1], out, num_sms, s);
         if (e != cudaSuccess) return cuda_fail(e, "launching mask compaction");
     }
     GradArgs ga{};
     ga.net = view_of(net);
     ga.time = net->time;
+    ga.pt_time = pt_time;
     ga.pts = pts;
     ga.n = n;
     ga.list = list;
@@ -452,10 +497,26 @@ int grad_impl(sdf_net_t net, const float* pts, const uint8_t* mask, int64_t n, f
     ga.out = out;
     ga.normalize = normalize;
     ga.grab = &counters[0];
-    ga.status = di.d_status;
-    e = (net->precision != SDF_FP32) ? launch_grad_tc(ga, di.num_sms, s) : launch_grad_simt(ga, di.num_sms, s);
+    ga.status = status;
+    e = (net->precision != SDF_FP32) ? launch_grad_tc(ga, num_sms, s) : launch_grad_simt(ga, num_sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "launching gradient kernel");
     return SDF_OK;
+}
+
+int grad_impl(sdf_net_t net, const float* pts, const float* pt_time, const uint8_t* mask, int64_t n, float* out,
+              int normalize, cudaStream_t s) {
+    if (!net) return fail(SDF_ERR_ARG, "net is NULL");
+    DeviceGuard g(net->device);
+    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", net->device);
+    int rc = validate_grad(net, pts, pt_time, mask, n, out);
+    if (rc || n == 0) return rc;
+    DeviceInfo di;
+    if ((rc = device_info(net->device, &di))) return rc;
+    Scratch sc;
+    sc.s = s;
+    cudaError_t e = cudaMallocAsync(&sc.ptr, grad_scratch_bytes(n, mask != nullptr) + 256, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch)");
+    return launch_gradients(net, pts, pt_time, mask, n, out, normalize, sc.ptr, di.d_status, di.num_sms, s);
 }
 
 }  // namespace
@@ -509,6 +570,181 @@ int noalloc_setup(int dev, NoAllocDevice* out) {
 
 }  // namespace
 
+
+// ---------------------------------------------------------------------------
+// Frame-batch plans: one CUDA graph holding the whole trace (all levels) and
+// the normal-mapping stage for a fixed set of device buffers.
+// ---------------------------------------------------------------------------
+struct sdf_plan {
+    int device = 0;
+    int n_levels = 0;
+    sdf_net_t nets[kMaxLevels] = {};
+    float delta[kMaxLevels] = {}, step_scale[kMaxLevels] = {};
+    int max_iters[kMaxLevels] = {}, tiles[kMaxLevels] = {};
+    sdf_trace_params params{};  // points into the arrays above
+    sdf_net_t fine = nullptr;
+    sdf_frame_batch batch{};
+    void* scratch = nullptr;    // trace scratch, then gradient scratch
+    size_t trace_bytes = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    size_t n_nodes = 0;
+};
+
+namespace {
+
+void free_plan(sdf_plan* p) {
+    if (!p) return;
+    DeviceGuard g(p->device);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->scratch) cudaFree(p->scratch);
+    delete p;
+}
+
+// Every launch of the plan's work on `s` (also what the graph captures).
+int plan_enqueue(sdf_plan* p, const int* tiles, int* status, int num_sms, cudaStream_t s) {
+    const sdf_frame_batch& b = p->batch;
+    int rc = launch_levels(&p->params, b.orig, b.dir, b.n, b.out_pos, b.out_t, b.out_hit, b.out_iters, p->scratch,
+                           status, num_sms, tiles, s);
+    if (rc || !p->fine) return rc;
+    return launch_gradients(p->fine, b.out_pos, b.ray_time, b.out_hit, b.n, b.out_normal, 1,
+                            static_cast<uint8_t*>(p->scratch) + p->trace_bytes, status, num_sms, s);
+}
+
+// Coordinate search over the tile count of each tensor-core level: for
+// level j every count 1..maximum is timed on the plan's own buffers (the
+// whole trace, one warm-up and the best of two runs) with the counts already
+// chosen for levels < j, and the fastest is kept.
+int plan_autotune(sdf_plan* p, int* status, int num_sms, cudaStream_t s) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    int rc = SDF_OK;
+    const sdf_frame_batch& b = p->batch;
+    for (int j = 0; j < p->n_levels && rc == SDF_OK; ++j) {
+        const sdf_net* net = p->nets[j];
+        const int tmax = net->precision == SDF_FP32 ? 0 : trace_tiles_max(view_of(net));
+        if (tmax <= 1) continue;
+        float best = INFINITY;
+        int best_t = tmax;
+        for (int t = 1; t <= tmax && rc == SDF_OK; ++t) {
+            p->tiles[j] = t;
+            float ms_min = INFINITY;
+            for (int rep = 0; rep < 3 && rc == SDF_OK; ++rep) {
+                cudaEventRecord(e0, s);
+                rc = launch_levels(&p->params, b.orig, b.dir, b.n, b.out_pos, b.out_t, b.out_hit, b.out_iters,
+                                   p->scratch, status, num_sms, p->tiles, s);
+                cudaEventRecord(e1, s);
+                if ((e = cudaEventSynchronize(e1)) != cudaSuccess) rc = cuda_fail(e, "autotune run");
+                float ms = 0.0f;
+                if (rc == SDF_OK && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+                    ms_min = std::min(ms_min, ms);
+            }
+            if (ms_min < best) {
+                best = ms_min;
+                best_t = t;
+            }
+        }
+        p->tiles[j] = best_t;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+int plan_create(const sdf_trace_params* P, sdf_net_t fine, const sdf_frame_batch* B, int autotune,
+                cudaStream_t s, sdf_plan_t* out) {
+    if (!out) return fail(SDF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!B) return fail(SDF_ERR_ARG, "batch is NULL");
+    if (!P) return fail(SDF_ERR_ARG, "params is NULL");
+    if (P->ray_time && P->ray_time != B->ray_time)
+        return fail(SDF_ERR_ARG, "pass per-ray times in the batch (params->ray_time must be NULL or equal)");
+    if ((fine == nullptr) != (B->out_normal == nullptr))
+        return fail(SDF_ERR_ARG, "fine and out_normal go together (both or neither)");
+    sdf_trace_params Q = *P;
+    Q.ray_time = B->ray_time;
+    int dev = -1;
+    int rc = validate_trace(&Q, B->orig, B->dir, B->n, B->out_pos, B->out_t, B->out_hit, B->out_iters, &dev);
+    if (rc) return rc;
+    if (fine) {
+        if (fine->device != dev) return fail(SDF_ERR_ARG, "fine network on another device");
+        if (B->ray_time && fine->in_dim != 4) return fail(SDF_ERR_ARG, "ray_time given for a 3-input fine network");
+        DeviceGuard g(dev);
+        if ((rc = validate_grad(fine, B->out_pos, B->ray_time, B->out_hit, B->n, B->out_normal))) return rc;
+    }
+    DeviceGuard g(dev);
+    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", dev);
+    DeviceInfo di;
+    if ((rc = device_info(dev, &di))) return rc;
+
+    sdf_plan* p = new sdf_plan;
+    p->device = dev;
+    p->n_levels = Q.n_levels;
+    for (int j = 0; j < Q.n_levels; ++j) {
+        p->nets[j] = Q.nets[j];
+        p->delta[j] = Q.delta[j];
+        p->max_iters[j] = Q.max_iters[j];
+        p->step_scale[j] = Q.step_scale ? Q.step_scale[j] : 0.0f;
+    }
+    p->params = Q;
+    p->params.nets = p->nets;
+    p->params.delta = p->delta;
+    p->params.max_iters = p->max_iters;
+    p->params.step_scale = Q.step_scale ? p->step_scale : nullptr;
+    p->fine = fine;
+    p->batch = *B;
+    if (B->n == 0) {
+        *out = p;
+        return SDF_OK;
+    }
+    p->trace_bytes = (trace_scratch_bytes(Q.n_levels, B->n) + 255) & ~size_t(255);
+    const size_t grad_bytes = fine ? grad_scratch_bytes(B->n, true) : 0;
+    cudaError_t e = cudaMalloc(&p->scratch, p->trace_bytes + grad_bytes + 256);
+    if (e != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(e, "cudaMalloc(plan scratch)");
+    }
+    if (autotune && (rc = plan_autotune(p, di.d_status, di.num_sms, s))) {
+        free_plan(p);
+        return rc;
+    }
+    // capture on a private stream (the legacy default stream cannot be captured)
+    cudaStream_t cs = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        free_plan(p);
+        return cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    rc = plan_enqueue(p, p->tiles, di.d_status, di.num_sms, cs);
+    e = cudaStreamEndCapture(cs, &p->graph);
+    cudaStreamDestroy(cs);
+    if (rc || e != cudaSuccess) {
+        if (!rc) rc = cuda_fail(e, "cudaStreamEndCapture");
+        free_plan(p);
+        return rc;
+    }
+    if ((e = cudaGraphGetNodes(p->graph, nullptr, &p->n_nodes)) != cudaSuccess ||
+        (e = cudaGraphInstantiate(&p->exec, p->graph, 0)) != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(e, "instantiating the plan's graph");
+    }
+    *out = p;
+    return SDF_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int sdf_net_load_mem(const void* bytes, size_t n_bytes, int precision, int device, sdf_net_t* out) {
@@ -556,12 +792,18 @@ int sdf_trace_multiscale(const sdf_trace_params* params, const float* orig, cons
 }
 
 int sdf_normals(sdf_net_t net, const float* pts, int64_t n, float* out_grad, void* cuda_stream) {
-    return grad_impl(net, pts, nullptr, n, out_grad, 0, static_cast<cudaStream_t>(cuda_stream));
+    return grad_impl(net, pts, nullptr, nullptr, n, out_grad, 0, static_cast<cudaStream_t>(cuda_stream));
 }
 
 int sdf_normal_map(sdf_net_t fine, const float* pts, const uint8_t* mask, int64_t n, float* out_normal,
                    void* cuda_stream) {
-    return grad_impl(fine, pts, mask, n, out_normal, 1, static_cast<cudaStream_t>(cuda_stream));
+    return grad_impl(fine, pts, nullptr, mask, n, out_normal, 1, static_cast<cudaStream_t>(cuda_stream));
+}
+
+int sdf_normal_map_timed(sdf_net_t fine, const float* pts, const float* pt_time, const uint8_t* mask, int64_t n,
+                         float* out_normal, void* cuda_stream) {
+    if (!pt_time) return fail(SDF_ERR_ARG, "time is NULL");
+    return grad_impl(fine, pts, pt_time, mask, n, out_normal, 1, static_cast<cudaStream_t>(cuda_stream));
 }
 
 int sdf_render_host(const sdf_trace_params* params, sdf_net_t fine, const float* orig, const float* dir, int64_t n,
@@ -596,7 +838,7 @@ int sdf_render_host(const sdf_trace_params* params, sdf_net_t fine, const float*
         return cuda_fail(e, "copying rays to the device");
     int rc = trace_impl(params, d_orig, d_dir, n, d_pos, d_t, d_hit, nullptr, s);
     if (rc) return rc;
-    rc = grad_impl(fine, d_pos, d_hit, n, d_nrm, 1, s);
+    rc = grad_impl(fine, d_pos, nullptr, d_hit, n, d_nrm, 1, s);
     if (rc) return rc;
     if ((e = cudaMemcpyAsync(out_pos, d_pos, v3, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(out_normal, d_nrm, v3, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
@@ -632,84 +874,46 @@ int sdf_trace_multiscale_noalloc(const sdf_trace_params* P, const float* orig, c
     // Same contract as sdf_trace_multiscale, with the scratch taken from the
     // static array above instead of the stream-ordered allocator.
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    if (!P) return fail(SDF_ERR_ARG, "params is NULL");
-    if (n < 0 || n > kNoAllocMaxRays)
+    if (n > kNoAllocMaxRays)
         return fail(SDF_ERR_ARG, "n = %lld: sdf_trace_multiscale_noalloc handles at most %lld rays per call",
                     static_cast<long long>(n), static_cast<long long>(kNoAllocMaxRays));
-    const int m = P->n_levels;
-    if (m < 1 || m > kMaxLevels) return fail(SDF_ERR_ARG, "n_levels = %d out of range 1..%d", m, kMaxLevels);
-    if (!P->nets || !P->delta || !P->max_iters) return fail(SDF_ERR_ARG, "nets, delta and max_iters are required");
-    if (!finite_pos(P->eps)) return fail(SDF_ERR_ARG, "eps must be finite and > 0");
-    if (!std::isfinite(P->box_min) || !std::isfinite(P->box_max) || !(P->box_min < P->box_max))
-        return fail(SDF_ERR_ARG, "box_min < box_max required");
-    if (P->final_mode != 0 && P->final_mode != 1) return fail(SDF_ERR_ARG, "final_mode must be 0 or 1");
-    if (!std::isfinite(P->time)) return fail(SDF_ERR_ARG, "time must be finite");
-    const int dev = P->nets[0] ? P->nets[0]->device : -1;
-    for (int j = 0; j < m; ++j) {
-        const sdf_net* net = P->nets[j];
-        if (!net) return fail(SDF_ERR_ARG, "nets[%d] is NULL", j);
-        if (net->device != dev) return fail(SDF_ERR_ARG, "networks live on different devices");
-        if (net->in_dim != P->nets[0]->in_dim) return fail(SDF_ERR_ARG, "networks differ in input dimension");
-        if (P->max_iters[j] < 0) return fail(SDF_ERR_ARG, "max_iters[%d] < 0", j);
-        const bool uses_delta = (j < m - 1) || P->final_mode == 1;
-        if (uses_delta && !finite_pos(P->delta[j])) return fail(SDF_ERR_ARG, "delta[%d] must be finite and > 0", j);
-        if (P->step_scale && !finite_pos(P->step_scale[j]))
-            return fail(SDF_ERR_ARG, "step_scale[%d] must be finite and > 0", j);
-        if (!P->step_scale && !(net->lipschitz > 0.0))
-            return fail(SDF_ERR_ARG, "nets[%d] has a zero Lipschitz bound; pass step_scale", j);
-        if (net->precision != SDF_FP32 && !tc_trace_supported(net->width, net->n_hidden))
-            return fail(SDF_ERR_UNSUPPORTED, "tensor-core tracing of a (%d,%d) network is not built", net->width,
-                        net->n_hidden);
-    }
+    int dev = -1;
+    int rc = validate_trace(P, orig, dir, n, out_pos, out_t, out_hit, out_iters, &dev);
+    if (rc || n == 0) return rc;
     DeviceGuard g(dev);
     if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", dev);
-    if (n == 0) return SDF_OK;
-    int rc;
-    if ((rc = check_device_ptr(orig, dev, "orig")) || (rc = check_device_ptr(dir, dev, "dir")) ||
-        (rc = check_device_ptr(out_pos, dev, "out_pos")) || (rc = check_device_ptr(out_t, dev, "out_t")) ||
-        (rc = check_device_ptr(out_hit, dev, "out_hit")))
-        return rc;
-    if (out_iters && (rc = check_device_ptr(out_iters, dev, "out_iters"))) return rc;
     NoAllocDevice nd;
     if ((rc = noalloc_setup(dev, &nd))) return rc;
+    return launch_levels_at(P, orig, dir, n, out_pos, out_t, out_hit, out_iters, nd.scratch->counters,
+                            nd.scratch->lists[0], nd.scratch->lists[1], &nd.scratch->status, nd.num_sms, nullptr, s);
+}
 
-    // every call starts from zeroed counters; the queues need no clearing
-    cudaError_t e = cudaMemsetAsync(nd.scratch->counters, 0, sizeof(nd.scratch->counters), s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(noalloc counters)");
-    unsigned long long* counters = nd.scratch->counters;
-    int32_t* lists[2] = {nd.scratch->lists[0], nd.scratch->lists[1]};
-    for (int j = 0; j < m; ++j) {
-        const sdf_net* net = P->nets[j];
-        const bool last = (j == m - 1);
-        LevelArgs la{};
-        la.net = view_of(net);
-        la.d = (last && P->final_mode == 0) ? 0.0f : P->delta[j];
-        la.scale = P->step_scale ? P->step_scale[j] : static_cast<float>(1.0 / net->lipschitz);
-        la.cap = P->max_iters[j];
-        la.is_last = last ? 1 : 0;
-        la.time = P->time;
-        la.eps = P->eps;
-        la.box_lo = P->box_min;
-        la.box_hi = P->box_max;
-        la.orig = orig;
-        la.dir = dir;
-        la.n = n;
-        la.out_pos = out_pos;
-        la.out_t = out_t;
-        la.out_hit = out_hit;
-        la.out_iters = out_iters;
-        la.in_list = j == 0 ? nullptr : lists[(j - 1) & 1];
-        la.in_count = j == 0 ? nullptr : &counters[kMaxLevels + j - 1];
-        la.out_list = last ? nullptr : lists[j & 1];
-        la.out_count = last ? nullptr : &counters[kMaxLevels + j];
-        la.grab = &counters[j];
-        la.status = &nd.scratch->status;
-        e = (net->precision != SDF_FP32) ? launch_trace_level_tc(la, nd.num_sms, s)
-                                         : launch_trace_level_simt(la, nd.num_sms, s);
-        if (e != cudaSuccess) return cuda_fail(e, "launching trace level");
-    }
+int sdf_plan_create(const sdf_trace_params* params, sdf_net_t fine, const sdf_frame_batch* batch, int autotune,
+                    void* cuda_stream, sdf_plan_t* out) {
+    return plan_create(params, fine, batch, autotune, static_cast<cudaStream_t>(cuda_stream), out);
+}
+
+int sdf_plan_launch(sdf_plan_t plan, void* cuda_stream) {
+    if (!plan) return fail(SDF_ERR_ARG, "plan is NULL");
+    if (!plan->exec) return SDF_OK;  // empty batch
+    DeviceGuard g(plan->device);
+    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", plan->device);
+    cudaError_t e = cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
     return SDF_OK;
 }
+
+int sdf_plan_info(sdf_plan_t plan, int* tiles, int max_levels, int64_t* n_graph_nodes) {
+    if (!plan) return fail(SDF_ERR_ARG, "plan is NULL");
+    if (tiles) {
+        if (max_levels < plan->n_levels) return fail(SDF_ERR_ARG, "tiles needs %d entries", plan->n_levels);
+        for (int j = 0; j < plan->n_levels; ++j) tiles[j] = plan->tiles[j];
+    }
+    if (n_graph_nodes) *n_graph_nodes = static_cast<int64_t>(plan->n_nodes);
+    return SDF_OK;
+}
+
+void sdf_plan_free(sdf_plan_t plan) { free_plan(plan); }
 
 const char* sdf_last_error(void) { return g_last_error.c_str(); }
 

@@ -32,7 +32,9 @@ struct LevelArgs {
     float scale;      // step = scale * t
     int cap;          // iteration cap of this level
     int is_last;      // last level: the hit decision is taken here
-    float time;       // 4th network input
+    float time;       // 4th network input of every ray when ray_time is NULL
+    const float* ray_time;  // 4th network input per ray (n floats, 4-input networks), or NULL
+    int tiles;        // ray tiles per CTA of the tensor-core kernel (0: the launcher's choice)
     float eps, box_lo, box_hi;
     // rays and outputs (SoA, n items)
     const float* orig;
@@ -54,7 +56,8 @@ struct LevelArgs {
 // Gradient / normal-mapping launch.
 struct GradArgs {
     NetView net;
-    float time;
+    float time;                     // 4th network input of every point when pt_time is NULL
+    const float* pt_time;           // 4th network input per point (n floats, 4-input networks), or NULL
     const float* pts;               // SoA (3, n)
     int64_t n;
     const int32_t* list;            // NULL: points 0..n-1; else list[0..*count)
@@ -70,6 +73,7 @@ cudaError_t launch_trace_level_simt(const LevelArgs& a, int num_sms, cudaStream_
 cudaError_t launch_grad_simt(const GradArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_trace_level_tc(const LevelArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_grad_tc(const GradArgs& a, int num_sms, cudaStream_t s);
+int trace_tiles_max(const NetView& net);  // largest `tiles` the tensor-core trace kernel accepts for net
 bool tc_trace_supported(int width, int n_hidden);
 bool tc_trace_split(int width, int n_hidden);  // head+remainder operands in the trace kernel
 bool tc_grad_supported(int width, int n_hidden);

@@ -36,6 +36,7 @@ struct SimtSmem {
     float ws[2 * kChunkK * W];
     float f[128];
     float px[128], py[128], pz[128];  // ray positions (trace) / points (grad)
+    float pt[128];                    // per-row time (4-input networks with per-ray / per-point times)
     int idx[128];
     long long tile;
 };
@@ -129,6 +130,7 @@ __global__ void __launch_bounds__(kSimtThreads) trace_level_simt_kernel(const Le
             S.px[tid] = ray.px;
             S.py[tid] = ray.py;
             S.pz[tid] = ray.pz;
+            S.pt[tid] = (a.ray_time && ray.state == kSlotActive) ? a.ray_time[ray.idx] : 0.0f;
         }
         if (!__syncthreads_or(tid < 128 && ray.state == kSlotActive)) break;
         if (a.cap <= 0) {
@@ -136,19 +138,24 @@ __global__ void __launch_bounds__(kSimtThreads) trace_level_simt_kernel(const Le
             continue;
         }
 
-        // layer 0 (FP32): X[r][n] = sin(W_0[n] . (p_r, time) + b_0[n])
+        // layer 0 (FP32): X[r][n] = sin(W_0[n] . (p_r, time_r) + b_0[n])
 #pragma unroll
         for (int j = 0; j < FPT; ++j) {
             const int n = feat_of(j, fg);
             const float wx = __ldg(net.w0 + n * net.in_dim + 0), wy = __ldg(net.w0 + n * net.in_dim + 1),
                         wz = __ldg(net.w0 + n * net.in_dim + 2);
-            float bb = __ldg(net.b0 + n);
-            if (net.in_dim == 4) bb = fmaf(__ldg(net.w0 + n * 4 + 3), a.time, bb);
+            float bb = __ldg(net.b0 + n), wt = 0.0f;
+            if (net.in_dim == 4) {
+                if (a.ray_time)
+                    wt = __ldg(net.w0 + n * 4 + 3);
+                else
+                    bb = fmaf(__ldg(net.w0 + n * 4 + 3), a.time, bb);
+            }
             float o[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int r = r0 + i;
-                const float z = fmaf(wx, S.px[r], fmaf(wy, S.py[r], fmaf(wz, S.pz[r], bb)));
+                const float z = fmaf(wx, S.px[r], fmaf(wy, S.py[r], fmaf(wz, S.pz[r], fmaf(wt, S.pt[r], bb))));
                 o[i] = sin_r(z);
             }
             *reinterpret_cast<float4*>(S.xt + xt_index(n, r0)) = make_float4(o[0], o[1], o[2], o[3]);
@@ -222,6 +229,7 @@ __global__ void __launch_bounds__(kSimtThreads) grad_simt_kernel(const GradArgs 
             S.px[tid] = i >= 0 ? a.pts[i] : 0.0f;
             S.py[tid] = i >= 0 ? a.pts[a.n + i] : 0.0f;
             S.pz[tid] = i >= 0 ? a.pts[2 * a.n + i] : 0.0f;
+            S.pt[tid] = (i >= 0 && a.pt_time) ? a.pt_time[i] : 0.0f;
         }
         __syncthreads();
 
@@ -231,12 +239,17 @@ __global__ void __launch_bounds__(kSimtThreads) grad_simt_kernel(const GradArgs 
             const int n = feat_of(j, fg);
             const float wx = __ldg(net.w0 + n * net.in_dim + 0), wy = __ldg(net.w0 + n * net.in_dim + 1),
                         wz = __ldg(net.w0 + n * net.in_dim + 2);
-            float bb = __ldg(net.b0 + n);
-            if (net.in_dim == 4) bb = fmaf(__ldg(net.w0 + n * 4 + 3), a.time, bb);
+            float bb = __ldg(net.b0 + n), wt = 0.0f;
+            if (net.in_dim == 4) {
+                if (a.pt_time)
+                    wt = __ldg(net.w0 + n * 4 + 3);
+                else
+                    bb = fmaf(__ldg(net.w0 + n * 4 + 3), a.time, bb);
+            }
 #pragma unroll
             for (int pp = 0; pp < 2; ++pp) {
                 const int p = p0 + pp;
-                const float z = fmaf(wx, S.px[p], fmaf(wy, S.py[p], fmaf(wz, S.pz[p], bb)));
+                const float z = fmaf(wx, S.px[p], fmaf(wy, S.py[p], fmaf(wz, S.pz[p], fmaf(wt, S.pt[p], bb))));
                 float s, c;
                 sincos_r(z, &s, &c);
                 *reinterpret_cast<float4*>(S.xt + xt_index(n, r0 + pp * 4)) = make_float4(s, wx * c, wy * c, wz * c);

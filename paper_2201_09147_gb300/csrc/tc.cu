@@ -40,7 +40,7 @@ namespace {
 constexpr int kTraceThreads = 128;
 
 struct TraceLayout {
-    uint32_t x, xlo, w, wlo, w0, b0, bh, wout, bars, misc, total;
+    uint32_t x, xlo, w, wlo, w0, wt, bh, wout, bars, misc, total;
 };
 
 // Shared-memory layout of the resident-weight trace kernel with T ray tiles
@@ -61,7 +61,7 @@ __host__ __device__ inline TraceLayout trace_layout(int W, int KH, bool split, i
     o += split ? wbytes : 0u;
     L.w0 = o;
     o += W * 4u * 4u;
-    L.b0 = o;
+    L.wt = o;
     o += W * 4u;
     L.bh = o;
     o += static_cast<uint32_t>(KH) * W * 4u;
@@ -102,6 +102,54 @@ __device__ __forceinline__ void pack_split(float a, float b, uint32_t& hi, uint3
     lo = pack16x2<F16>(a - ah, b - bh);
 }
 
+// Layer-0 parameters in shared memory: (w_x, w_y, w_z, b) per unit as a
+// float4, and the time column w_t apart.  With per-ray times (TIMED) b is
+// the plain bias and each ray adds w_t * t_ray; otherwise the launch's
+// constant time is folded into b.
+__device__ __forceinline__ void stage_layer0(const NetView& net, float time, bool timed, int i, float* w0s,
+                                             float* wts) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) w0s[i * 4 + c] = net.w0[i * net.in_dim + c];
+    float bb = net.b0[i];
+    const float wt = net.in_dim == 4 ? net.w0[i * 4 + 3] : 0.0f;
+    if (!timed) bb = fmaf(wt, time, bb);
+    w0s[i * 4 + 3] = bb;
+    wts[i] = timed ? wt : 0.0f;
+}
+
+// Layer 0 (FP32) of one ray row: X[row] = 16-bit sin(W_0 (p, t) + b_0),
+// as a head and (SPLIT) the rounding of the remainder.  With TIMED the
+// ray's time is read here (it is not kept in a register between steps).
+template <int W, bool F16, bool SPLIT, bool TIMED>
+__device__ __forceinline__ void trace_layer0(const LevelArgs& a, const float* w0s, const float* wts, const Ray& ray,
+                                             int row, uint32_t x_s, uint32_t xlo_s) {
+    const float tm = (TIMED && ray.state == kSlotActive) ? __ldg(a.ray_time + ray.idx) : 0.0f;
+    for (int k8 = 0; k8 < W / 8; ++k8) {
+        uint32_t pk[4], pl[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e0 = k8 * 8 + 2 * q, e1 = e0 + 1;
+            const float4 u0 = reinterpret_cast<const float4*>(w0s)[e0];
+            const float4 u1 = reinterpret_cast<const float4*>(w0s)[e1];
+            float c0 = u0.w, c1 = u1.w;
+            if (TIMED) {
+                const float2 t2 = reinterpret_cast<const float2*>(wts)[k8 * 4 + q];
+                c0 = fmaf(t2.x, tm, c0);
+                c1 = fmaf(t2.y, tm, c1);
+            }
+            const float z0 = fmaf(u0.x, ray.px, fmaf(u0.y, ray.py, fmaf(u0.z, ray.pz, c0)));
+            const float z1 = fmaf(u1.x, ray.px, fmaf(u1.y, ray.py, fmaf(u1.z, ray.pz, c1)));
+            if (SPLIT)
+                pack_split<F16>(sin_fast(z0), sin_fast(z1), pk[q], pl[q]);
+            else
+                pk[q] = pack16x2<F16>(sin_fast(z0), sin_fast(z1));
+        }
+        const uint32_t off = sw128_chunk_offset(row, k8, 128);
+        st_shared_v4(x_s + off, pk[0], pk[1], pk[2], pk[3]);
+        if (SPLIT) st_shared_v4(xlo_s + off, pl[0], pl[1], pl[2], pl[3]);
+    }
+}
+
 // T = blockDim.x / 128 independent ray tiles per CTA.  Tile t owns warps
 // 4t..4t+3 (so its threads read TMEM lanes 0..127), TMEM columns
 // [t*W, (t+1)*W), its own activation buffers, MMA mbarrier and named barrier
@@ -117,7 +165,7 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
     const int T = blockDim.x >> 7;
     const TraceLayout L = trace_layout(W, KH, SPLIT, T);
     float* w0s = reinterpret_cast<float*>(base + L.w0);
-    float* b0s = reinterpret_cast<float*>(base + L.b0);
+    float* wts = reinterpret_cast<float*>(base + L.wt);
     float* bhs = reinterpret_cast<float*>(base + L.bh);
     float* wos = reinterpret_cast<float*>(base + L.wout);
     const uint32_t bar_w = base_s + L.bars;
@@ -141,13 +189,9 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
         tmem_alloc(smem_u32(tmem_slot), tcols);
         tmem_relinquish();
     }
+    const bool timed = a.ray_time != nullptr && net.in_dim == 4;
     for (int i = tid; i < W; i += blockDim.x) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) w0s[i * 4 + c] = net.w0[i * net.in_dim + c];
-        float bb = net.b0[i];
-        if (net.in_dim == 4) bb = fmaf(net.w0[i * 4 + 3], a.time, bb);
-        w0s[i * 4 + 3] = bb;  // layer 0 as float4 (w_x, w_y, w_z, b), time folded into b
-        b0s[i] = bb;
+        stage_layer0(net, a.time, timed, i, w0s, wts);
         wos[i] = net.wout[i];
         for (int l = 0; l < KH; ++l) bhs[l * W + i] = net.bh[l][i];
     }
@@ -181,25 +225,11 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
             pass_ray(a, ray);
             continue;
         }
-        // layer 0 (FP32): row ttid of X = 16-bit sin(W_0 p + b_0)
-        for (int k8 = 0; k8 < W / 8; ++k8) {
-            uint32_t pk[4], pl[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int e0 = k8 * 8 + 2 * q, e1 = e0 + 1;
-                const float4 u0 = reinterpret_cast<const float4*>(w0s)[e0];
-                const float4 u1 = reinterpret_cast<const float4*>(w0s)[e1];
-                const float z0 = fmaf(u0.x, ray.px, fmaf(u0.y, ray.py, fmaf(u0.z, ray.pz, u0.w)));
-                const float z1 = fmaf(u1.x, ray.px, fmaf(u1.y, ray.py, fmaf(u1.z, ray.pz, u1.w)));
-                if (SPLIT)
-                    pack_split<F16>(sin_fast(z0), sin_fast(z1), pk[q], pl[q]);
-                else
-                    pk[q] = pack16x2<F16>(sin_fast(z0), sin_fast(z1));
-            }
-            const uint32_t off = sw128_chunk_offset(ttid, k8, 128);
-            st_shared_v4(x_s + off, pk[0], pk[1], pk[2], pk[3]);
-            if (SPLIT) st_shared_v4(xlo_s + off, pl[0], pl[1], pl[2], pl[3]);
-        }
+        // layer 0 (FP32): row ttid of X = 16-bit sin(W_0 (p, t) + b_0)
+        if (timed)
+            trace_layer0<W, F16, SPLIT, true>(a, w0s, wts, ray, ttid, x_s, xlo_s);
+        else
+            trace_layer0<W, F16, SPLIT, false>(a, w0s, wts, ray, ttid, x_s, xlo_s);
         fence_proxy_async_smem();
         tc_fence_before();
         bar_named(bar_id, 128);
@@ -305,7 +335,7 @@ constexpr uint32_t kStreamStageBytes = kStreamW * 128u;
 constexpr int kStreamThreads = 160;  // 128 ray threads + 1 producer warp
 
 struct StreamLayout {
-    uint32_t x, ring, w0, b0, bh, wout, bars, misc, total;
+    uint32_t x, ring, w0, wt, bh, wout, bars, misc, total;
 };
 
 __host__ __device__ inline StreamLayout stream_layout(int KH) {
@@ -317,7 +347,7 @@ __host__ __device__ inline StreamLayout stream_layout(int KH) {
     o += kStreamStages * kStreamStageBytes;
     L.w0 = o;
     o += kStreamW * 4u * 4u;
-    L.b0 = o;
+    L.wt = o;
     o += kStreamW * 4u;
     L.bh = o;
     o += static_cast<uint32_t>(KH) * kStreamW * 4u;
@@ -343,7 +373,7 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
     const int KH = net.n_hidden;
     const StreamLayout L = stream_layout(KH);
     float* w0s = reinterpret_cast<float*>(base + L.w0);
-    float* b0s = reinterpret_cast<float*>(base + L.b0);
+    float* wts = reinterpret_cast<float*>(base + L.wt);
     float* bhs = reinterpret_cast<float*>(base + L.bh);
     float* wos = reinterpret_cast<float*>(base + L.wout);
     const uint32_t bar_full = base_s + L.bars, bar_empty = bar_full + 8u * NS, bar_mma = bar_empty + 8u * NS;
@@ -369,13 +399,9 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
         tmem_alloc(smem_u32(tmem_slot), W);
         tmem_relinquish();
     }
+    const bool timed = a.ray_time != nullptr && net.in_dim == 4;
     for (int i = tid; i < W; i += kStreamThreads) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) w0s[i * 4 + c] = net.w0[i * net.in_dim + c];
-        float bb = net.b0[i];
-        if (net.in_dim == 4) bb = fmaf(net.w0[i * 4 + 3], a.time, bb);
-        w0s[i * 4 + 3] = bb;  // layer 0 as float4 (w_x, w_y, w_z, b), time folded into b
-        b0s[i] = bb;
+        stage_layer0(net, a.time, timed, i, w0s, wts);
         wos[i] = net.wout[i];
         for (int l = 0; l < KH; ++l) bhs[l * W + i] = net.bh[l][i];
     }
@@ -431,19 +457,10 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
                 pass_ray(a, ray);
                 continue;
             }
-            for (int k8 = 0; k8 < W / 8; ++k8) {
-                uint32_t pk[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int e0 = k8 * 8 + 2 * q, e1 = e0 + 1;
-                    const float4 u0 = reinterpret_cast<const float4*>(w0s)[e0];
-                    const float4 u1 = reinterpret_cast<const float4*>(w0s)[e1];
-                    const float z0 = fmaf(u0.x, ray.px, fmaf(u0.y, ray.py, fmaf(u0.z, ray.pz, u0.w)));
-                    const float z1 = fmaf(u1.x, ray.px, fmaf(u1.y, ray.py, fmaf(u1.z, ray.pz, u1.w)));
-                    pk[q] = pack16x2<F16>(sin_fast(z0), sin_fast(z1));
-                }
-                st_shared_v4(x_s + sw128_chunk_offset(tid, k8, 128), pk[0], pk[1], pk[2], pk[3]);
-            }
+            if (timed)
+                trace_layer0<W, F16, false, true>(a, w0s, wts, ray, tid, x_s, x_s);
+            else
+                trace_layer0<W, F16, false, false>(a, w0s, wts, ray, tid, x_s, x_s);
             fence_proxy_async_smem();
             tc_fence_before();
             bar_named(1, 128);
@@ -563,7 +580,7 @@ struct GradCfg {
 };
 
 struct GradLayout {
-    uint32_t x, ring, woutb, w0, bh, pts, idx, bars, misc, total;
+    uint32_t x, ring, woutb, w0, wt, bh, pts, idx, bars, misc, total;
 };
 
 template <int W>
@@ -579,10 +596,12 @@ __host__ __device__ inline GradLayout grad_layout(int KH) {
     o += C::KB * 16u * 128u;
     L.w0 = o;
     o += W * 4u * 4u;
+    L.wt = o;
+    o += W * 4u;
     L.bh = o;
     o += static_cast<uint32_t>(KH) * W * 4u;
     L.pts = o;
-    o += C::NPTS * 3u * 4u;
+    o += C::NPTS * 4u * 4u;
     L.idx = o;
     o += C::NPTS * 4u;
     L.bars = o;
@@ -634,8 +653,9 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
     const int KH = net.n_hidden;
     const GradLayout L = grad_layout<W>(KH);
     float* w0s = reinterpret_cast<float*>(base + L.w0);
+    float* wts = reinterpret_cast<float*>(base + L.wt);
     float* bhs = reinterpret_cast<float*>(base + L.bh);
-    float* pts = reinterpret_cast<float*>(base + L.pts);
+    float4* pts = reinterpret_cast<float4*>(base + L.pts);  // (x, y, z, t) per point
     int* idxs = reinterpret_cast<int*>(base + L.idx);
     const uint32_t bar_full = base_s + L.bars;             // NS barriers
     const uint32_t bar_empty = bar_full + 8u * C::NS;      // NS barriers
@@ -662,13 +682,9 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
         tmem_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
         tmem_relinquish();
     }
-    // layer 0 as float4 (w_x, w_y, w_z, b) per unit, the time input folded into b
+    const bool timed = a.pt_time != nullptr && net.in_dim == 4;
     for (int i = tid; i < W; i += C::THREADS) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) w0s[i * 4 + c] = net.w0[i * net.in_dim + c];
-        float bb = net.b0[i];
-        if (net.in_dim == 4) bb = fmaf(net.w0[i * 4 + 3], a.time, bb);
-        w0s[i * 4 + 3] = bb;
+        stage_layer0(net, a.time, timed, i, w0s, wts);
         for (int l = 0; l < KH; ++l) bhs[l * W + i] = net.bh[l][i];
     }
     // w_out split into a 16-bit head (row 0) and the 16-bit rounding of its
@@ -781,25 +797,28 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
                 int idx = -1;
                 if (k < n_work) idx = a.list ? a.list[k] : static_cast<int>(k);
                 idxs[p0 + gt] = idx;
-                pts[(p0 + gt) * 3 + 0] = idx >= 0 ? a.pts[idx] : 0.0f;
-                pts[(p0 + gt) * 3 + 1] = idx >= 0 ? a.pts[a.n + idx] : 0.0f;
-                pts[(p0 + gt) * 3 + 2] = idx >= 0 ? a.pts[2 * a.n + idx] : 0.0f;
+                pts[p0 + gt] = idx >= 0 ? make_float4(a.pts[idx], a.pts[a.n + idx], a.pts[2 * a.n + idx],
+                                                      timed ? a.pt_time[idx] : 0.0f)
+                                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             }
             bar_named(1 + h, C::GROUP_THREADS);
-            // input layer: P_0 = sin(A_0), G_0^c = W_0[:, c] (.) cos(A_0)
+            // input layer: P_0 = sin(A_0), G_0^c = W_0[:, c] (.) cos(A_0); the time
+            // input enters A_0 only (the tangents are spatial)
             if (live) {
                 const float4 u = reinterpret_cast<const float4*>(w0s)[m];
+                const float ut = wts[m];
                 for (int p = p0; p < p0 + C::HPTS; p += 2) {
                     float ve[4], vo[4];
                     {
-                        const float z = fmaf(u.x, pts[p * 3 + 0], fmaf(u.y, pts[p * 3 + 1], fmaf(u.z, pts[p * 3 + 2], u.w)));
+                        const float4 q4 = pts[p];
+                        const float z = fmaf(u.x, q4.x, fmaf(u.y, q4.y, fmaf(u.z, q4.z, fmaf(ut, q4.w, u.w))));
                         float sn, cs;
                         sincos_fast(z, &sn, &cs);
                         ve[0] = sn; ve[1] = u.x * cs; ve[2] = u.y * cs; ve[3] = u.z * cs;
                     }
                     {
-                        const int q = p + 1;
-                        const float z = fmaf(u.x, pts[q * 3 + 0], fmaf(u.y, pts[q * 3 + 1], fmaf(u.z, pts[q * 3 + 2], u.w)));
+                        const float4 q4 = pts[p + 1];
+                        const float z = fmaf(u.x, q4.x, fmaf(u.y, q4.y, fmaf(u.z, q4.z, fmaf(ut, q4.w, u.w))));
                         float sn, cs;
                         sincos_fast(z, &sn, &cs);
                         vo[0] = sn; vo[1] = u.x * cs; vo[2] = u.y * cs; vo[3] = u.z * cs;
@@ -953,18 +972,43 @@ static int trace_tiles(Kernel k, int W, int KH, bool split) {
     return T;
 }
 
+// The launch takes min(a.tiles, maximum) tiles per CTA when a.tiles > 0.
 template <int W, bool F16>
 static cudaError_t launch_trace_resident(const LevelArgs& a, int num_sms, cudaStream_t s) {
     const int KH = a.net.n_hidden;
     const bool split = a.net.wbf_lo != nullptr && trace_split(W, KH);
     if (split) {
         auto k = trace_level_tc_kernel<W, F16, true>;
-        const int T = trace_tiles(k, W, KH, true);
+        int T = trace_tiles(k, W, KH, true);
+        if (a.tiles > 0) T = std::min(T, a.tiles);
         return launch_tc(k, 128 * T, trace_layout(W, KH, true, T).total + 1024, tmem_cols_for(T * W), num_sms, s, &a);
     }
     auto k = trace_level_tc_kernel<W, F16, false>;
-    const int T = trace_tiles(k, W, KH, false);
+    int T = trace_tiles(k, W, KH, false);
+    if (a.tiles > 0) T = std::min(T, a.tiles);
     return launch_tc(k, 128 * T, trace_layout(W, KH, false, T).total + 1024, tmem_cols_for(T * W), num_sms, s, &a);
+}
+
+template <int W, bool F16>
+static int trace_tiles_resident(const NetView& net) {
+    const int KH = net.n_hidden;
+    if (net.wbf_lo != nullptr && trace_split(W, KH)) return trace_tiles(trace_level_tc_kernel<W, F16, true>, W, KH, true);
+    return trace_tiles(trace_level_tc_kernel<W, F16, false>, W, KH, false);
+}
+
+int trace_tiles_max(const NetView& net) {
+    if (!tc_trace_supported(net.width, net.n_hidden)) return 0;
+    const bool f16 = net.op_f16 != 0;
+    switch (net.width) {
+    case 64:
+        return f16 ? trace_tiles_resident<64, true>(net) : trace_tiles_resident<64, false>(net);
+    case 128:
+        return f16 ? trace_tiles_resident<128, true>(net) : trace_tiles_resident<128, false>(net);
+    case 256:
+        if (net.n_hidden == 1) return f16 ? trace_tiles_resident<256, true>(net) : trace_tiles_resident<256, false>(net);
+        return 1;  // the streamed-weight kernel has one tile
+    }
+    return 0;
 }
 
 cudaError_t launch_trace_level_tc(const LevelArgs& a, int num_sms, cudaStream_t s) {

@@ -37,11 +37,14 @@ from . import inputs
 
 SCENES_DIR = Path(__file__).resolve().parent / "scenes"
 
-# name -> (width, n_hidden, steps)
+# name -> (width, n_hidden, steps[, in_dim]); 4-D nets take (x, y, z, t) of the animated scene
 SEQUENCE_NETS = {
+    "a8_64x1_t": (64, 1, 3000, 4),
+    "a8_256x3_t": (256, 3, 3000, 4),
     "s8_64x1": (64, 1, 3000),
     "s8_64x2": (64, 2, 3000),
     "s8_128x2": (128, 2, 3000),
+    "s8_256x1": (256, 1, 3000),
     "s8_256x2": (256, 2, 3000),
     "s8_256x3": (256, 3, 3000),
 }
@@ -74,11 +77,11 @@ class Siren(torch.nn.Module):
                               template.omega, ws, bs, folded=False)
 
 
-def scene_torch(scene: inputs.SphereScene, p: torch.Tensor):
-    """Analytic scene value and gradient (torch, float32)."""
-    c = torch.as_tensor(scene.centres, dtype=p.dtype, device=p.device)
+def scene_torch(scene: inputs.SphereScene, p: torch.Tensor, centres=None):
+    """Analytic scene value and gradient (torch, float32); `centres` (n, m, 3) overrides per point."""
+    c = torch.as_tensor(scene.centres, dtype=p.dtype, device=p.device) if centres is None else centres
     r = torch.as_tensor(scene.radii, dtype=p.dtype, device=p.device)
-    diff = p[:, None, :] - c[None]
+    diff = p[:, None, :] - (c[None] if c.dim() == 2 else c)
     dist = diff.norm(dim=-1)
     d = dist - r[None]
     dmin, arg = d.min(dim=1)
@@ -104,20 +107,42 @@ def sample_batch(scene: inputs.SphereScene, gen: torch.Generator, n: int):
     return torch.cat([near, unif], dim=0), half
 
 
+def animated_centres(seed: int, t: torch.Tensor):
+    """Centres of inputs.sphere_scene(seed, time=t) for a batch of times, (n, m, 3)."""
+    s0 = inputs.sphere_scene(seed)
+    s1 = inputs.sphere_scene(seed, time=0.0)
+    # the phases are drawn after the centres and radii: recover them from time 0
+    delta0 = (s1.centres - s0.centres) / 0.15
+    phase = torch.as_tensor(np.arctan2(delta0[:, 1], delta0[:, 0]), dtype=torch.float32)
+    c0 = torch.as_tensor(s0.centres, dtype=torch.float32)
+    ang = 2.0 * math.pi * t[:, None] + phase[None, :]
+    off = 0.15 * torch.stack([torch.cos(ang), torch.sin(ang), torch.zeros_like(ang)], dim=-1)
+    return c0[None] + off
+
+
 def fit_net(scene, width, n_hidden, steps, seed=0, batch=1 << 14, lr=1e-4, lam_n=0.1, lam_e=0.05,
-            device="cpu", log_every=500):
+            device="cpu", log_every=500, in_dim=3, scene_seed=1):
     torch.manual_seed(seed)
     gen = torch.Generator().manual_seed(seed)
-    template = inputs.siren_init(seed, width, n_hidden)
+    template = inputs.siren_init(seed, width, n_hidden, in_dim=in_dim)
     model = Siren(template).to(device)
     opt = torch.optim.Adam(model.parameters(), lr=lr)
     sched = torch.optim.lr_scheduler.CosineAnnealingLR(opt, T_max=steps, eta_min=lr * 0.05)
     t0 = time.time()
     for it in range(steps):
         x, half = sample_batch(scene, gen, batch)
+        centres = None
+        if in_dim == 4:
+            # time in [0, 1); near-surface samples follow the moving spheres
+            tt = torch.rand(batch, generator=gen)
+            centres = animated_centres(scene_seed, tt)
+            k = torch.randint(0, len(scene.radii), (half,), generator=gen)
+            shift = centres[torch.arange(half), k] - torch.as_tensor(scene.centres, dtype=torch.float32)[k]
+            x = torch.cat([(x[:half] + shift).clamp(-1.0, 1.0), x[half:]], dim=0)
         x = x.to(device).requires_grad_(True)
-        gv, gg = scene_torch(scene, x.detach())
-        f = model(x)
+        gv, gg = scene_torch(scene, x.detach(), centres)
+        inp = torch.cat([x, tt[:, None].to(device)], dim=1) if in_dim == 4 else x
+        f = model(inp)
         (df,) = torch.autograd.grad(f.sum(), x, create_graph=True)
         l_val = (f - gv).abs().mean()
         cos = torch.nn.functional.cosine_similarity(df[:half], gg[:half], dim=1)
@@ -129,7 +154,7 @@ def fit_net(scene, width, n_hidden, steps, seed=0, batch=1 << 14, lr=1e-4, lam_n
         opt.step()
         sched.step()
         if log_every and (it % log_every == 0 or it == steps - 1):
-            print(f"  ({width},{n_hidden}) it {it:5d} loss {loss.item():.5f} val {l_val.item():.5f} "
+            print(f"  ({width},{n_hidden}) in{in_dim} it {it:5d} loss {loss.item():.5f} val {l_val.item():.5f} "
                   f"n {l_n.item():.4f} eik {l_e.item():.4f}  {time.time() - t0:.0f}s", flush=True)
     return model.cpu().to_sinenet(template)
 
@@ -147,15 +172,17 @@ def main():
     out = Path(args.out)
     out.mkdir(parents=True, exist_ok=True)
     scene = inputs.sphere_scene(seed=1)
-    meta = {}
+    meta_path = out / "fit_meta.json"
+    meta = json.loads(meta_path.read_text()) if meta_path.exists() else {}
     for name in args.nets.split(","):
-        w, k, steps = SEQUENCE_NETS[name]
+        w, k, steps, *rest = SEQUENCE_NETS[name]
+        in_dim = rest[0] if rest else 3
         steps = args.steps or steps
-        print(f"fitting {name}: ({w},{k}) {steps} steps", flush=True)
-        net = fit_net(scene, w, k, steps, device=args.device)
+        print(f"fitting {name}: ({w},{k}) in_dim {in_dim}, {steps} steps", flush=True)
+        net = fit_net(scene, w, k, steps, device=args.device, in_dim=in_dim)
         inputs.write_net(out / f"{name}.sdfn", net)
-        meta[name] = {"width": w, "n_hidden": k, "steps": steps, "seed": 0, "scene_seed": 1}
-    (out / "fit_meta.json").write_text(json.dumps(meta, indent=1) + "\n")
+        meta[name] = {"width": w, "n_hidden": k, "in_dim": in_dim, "steps": steps, "seed": 0, "scene_seed": 1}
+    meta_path.write_text(json.dumps(meta, indent=1, sort_keys=True) + "\n")
 
 
 if __name__ == "__main__":

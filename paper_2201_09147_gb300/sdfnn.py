@@ -22,7 +22,8 @@ ERRORS = {-1: "SDF_ERR_ARG", -2: "SDF_ERR_FILE", -3: "SDF_ERR_FORMAT", -4: "SDF_
 
 EXPORTS = ["sdf_net_load", "sdf_net_load_mem", "sdf_net_info", "sdf_net_set_time", "sdf_net_free",
            "sdf_trace_multiscale", "sdf_normals", "sdf_normal_map", "sdf_render_host", "sdf_sync_status",
-           "sdf_last_error", "sdf_trace_multiscale_noalloc"]
+           "sdf_last_error", "sdf_trace_multiscale_noalloc", "sdf_normal_map_timed", "sdf_plan_create",
+           "sdf_plan_launch", "sdf_plan_info", "sdf_plan_free"]
 
 
 class SdfError(RuntimeError):
@@ -34,7 +35,14 @@ class SdfError(RuntimeError):
 class TraceParamsC(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("nets", C.POINTER(C.c_void_p)), ("delta", C.POINTER(C.c_float)),
                 ("max_iters", C.POINTER(C.c_int)), ("eps", C.c_float), ("step_scale", C.POINTER(C.c_float)),
-                ("box_min", C.c_float), ("box_max", C.c_float), ("final_mode", C.c_int), ("time", C.c_float)]
+                ("box_min", C.c_float), ("box_max", C.c_float), ("final_mode", C.c_int), ("time", C.c_float),
+                ("ray_time", C.c_void_p)]
+
+
+class FrameBatchC(C.Structure):
+    _fields_ = [("orig", C.c_void_p), ("dir", C.c_void_p), ("ray_time", C.c_void_p), ("n", C.c_int64),
+                ("out_pos", C.c_void_p), ("out_t", C.c_void_p), ("out_hit", C.c_void_p), ("out_iters", C.c_void_p),
+                ("out_normal", C.c_void_p)]
 
 
 _lib = None
@@ -60,6 +68,12 @@ def lib():
         L.sdf_trace_multiscale_noalloc.argtypes = [C.POINTER(TraceParamsC), vp, vp, C.c_int64, vp, vp, vp, vp, vp]
         L.sdf_normals.argtypes = [vp, vp, C.c_int64, vp, vp]
         L.sdf_normal_map.argtypes = [vp, vp, vp, C.c_int64, vp, vp]
+        L.sdf_normal_map_timed.argtypes = [vp, vp, vp, vp, C.c_int64, vp, vp]
+        L.sdf_plan_create.argtypes = [C.POINTER(TraceParamsC), vp, C.POINTER(FrameBatchC), C.c_int, vp, C.POINTER(vp)]
+        L.sdf_plan_launch.argtypes = [vp, vp]
+        L.sdf_plan_info.argtypes = [vp, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int64)]
+        L.sdf_plan_free.argtypes = [vp]
+        L.sdf_plan_free.restype = None
         L.sdf_render_host.argtypes = [C.POINTER(TraceParamsC), vp, vp, vp, C.c_int64, vp, vp, vp, vp]
         L.sdf_sync_status.argtypes = [vp]
         L.sdf_last_error.restype = C.c_char_p
@@ -113,7 +127,8 @@ class Net:
             pass
 
 
-def make_params(nets, delta, max_iters, eps, step_scale=None, box=(-1.0, 1.0), final_mode=0, time=0.0):
+def make_params(nets, delta, max_iters, eps, step_scale=None, box=(-1.0, 1.0), final_mode=0, time=0.0,
+                ray_time=None):
     """Builds sdf_trace_params; returns (struct, keep-alive tuple)."""
     m = len(nets)
     hs = (C.c_void_p * m)(*[n.handle.value for n in nets])
@@ -123,14 +138,15 @@ def make_params(nets, delta, max_iters, eps, step_scale=None, box=(-1.0, 1.0), f
     p = TraceParamsC(m, C.cast(hs, C.POINTER(C.c_void_p)), C.cast(d, C.POINTER(C.c_float)),
                      C.cast(it, C.POINTER(C.c_int)), float(eps),
                      None if ss is None else C.cast(ss, C.POINTER(C.c_float)), float(box[0]), float(box[1]),
-                     int(final_mode), float(time))
-    return p, (hs, d, it, ss, nets)
+                     int(final_mode), float(time), None if ray_time is None else ray_time.data_ptr())
+    return p, (hs, d, it, ss, nets, ray_time)
 
 
 def trace_multiscale(nets, delta, max_iters, eps, orig, dirs, *, step_scale=None, box=(-1.0, 1.0), final_mode=0,
-                     time=0.0, out_pos=None, out_t=None, out_hit=None, out_iters=None, want_iters=True,
-                     stream=None):
-    """Alg. 1 on device rays orig/dirs (float32, shape (3, n)); returns (pos, t, hit, iters)."""
+                     time=0.0, ray_time=None, out_pos=None, out_t=None, out_hit=None, out_iters=None,
+                     want_iters=True, stream=None):
+    """Alg. 1 on device rays orig/dirs (float32, shape (3, n)); returns (pos, t, hit, iters).
+    ray_time: optional device (n,) float32, the 4th input of each ray (4-D networks)."""
     n = orig.shape[1]
     dev = orig.device
     out_pos = torch.empty((3, n), dtype=torch.float32, device=dev) if out_pos is None else out_pos
@@ -138,7 +154,7 @@ def trace_multiscale(nets, delta, max_iters, eps, orig, dirs, *, step_scale=None
     out_hit = torch.empty(n, dtype=torch.uint8, device=dev) if out_hit is None else out_hit
     if out_iters is None and want_iters:
         out_iters = torch.empty(n, dtype=torch.uint16, device=dev)
-    p, keep = make_params(nets, delta, max_iters, eps, step_scale, box, final_mode, time)
+    p, keep = make_params(nets, delta, max_iters, eps, step_scale, box, final_mode, time, ray_time)
     _check(lib().sdf_trace_multiscale(C.byref(p), _ptr(orig), _ptr(dirs), n, _ptr(out_pos), _ptr(out_t),
                                       _ptr(out_hit), _ptr(out_iters), C.c_void_p(_stream(stream))))
     del keep
@@ -146,7 +162,7 @@ def trace_multiscale(nets, delta, max_iters, eps, orig, dirs, *, step_scale=None
 
 
 def trace_multiscale_noalloc(nets, delta, max_iters, eps, orig, dirs, *, step_scale=None, box=(-1.0, 1.0),
-                             final_mode=0, time=0.0, out_pos=None, out_t=None, out_hit=None, out_iters=None,
+                             final_mode=0, time=0.0, ray_time=None, out_pos=None, out_t=None, out_hit=None, out_iters=None,
                              want_iters=True, stream=None):
     """Alg. 1 through sdf_trace_multiscale_noalloc: the library allocates no
     device memory for the call (its scratch is a static device array, at most
@@ -159,7 +175,7 @@ def trace_multiscale_noalloc(nets, delta, max_iters, eps, orig, dirs, *, step_sc
     out_hit = torch.empty(n, dtype=torch.uint8, device=dev) if out_hit is None else out_hit
     if out_iters is None and want_iters:
         out_iters = torch.empty(n, dtype=torch.uint16, device=dev)
-    p, keep = make_params(nets, delta, max_iters, eps, step_scale, box, final_mode, time)
+    p, keep = make_params(nets, delta, max_iters, eps, step_scale, box, final_mode, time, ray_time)
     _check(lib().sdf_trace_multiscale_noalloc(C.byref(p), _ptr(orig), _ptr(dirs), n, _ptr(out_pos), _ptr(out_t),
                                               _ptr(out_hit), _ptr(out_iters), C.c_void_p(_stream(stream))))
     del keep
@@ -180,6 +196,68 @@ def normal_map(net: Net, pts, mask=None, out=None, stream=None):
     out = torch.empty((3, n), dtype=torch.float32, device=pts.device) if out is None else out
     _check(lib().sdf_normal_map(net.handle, _ptr(pts), _ptr(mask), n, _ptr(out), C.c_void_p(_stream(stream))))
     return out
+
+
+def normal_map_timed(net: Net, pts, pt_time, mask=None, out=None, stream=None):
+    """normal_map of a 4-D network with a time per point (device (n,) float32)."""
+    n = pts.shape[1]
+    out = torch.empty((3, n), dtype=torch.float32, device=pts.device) if out is None else out
+    _check(lib().sdf_normal_map_timed(net.handle, _ptr(pts), _ptr(pt_time), _ptr(mask), n, _ptr(out),
+                                      C.c_void_p(_stream(stream))))
+    return out
+
+
+class Plan:
+    """A frame-batch plan (sdf_plan_create): the whole trace and the normal
+    mapping of a fixed set of device buffers, captured as one CUDA graph.
+
+    The output tensors are allocated here (torch) unless given and are
+    attributes of the plan: pos (3, n), t (n), hit (n), iters (n) or None,
+    normal (3, n) or None (no fine network)."""
+
+    def __init__(self, nets, delta, max_iters, eps, orig, dirs, *, fine: Net | None = None, ray_time=None,
+                 step_scale=None, box=(-1.0, 1.0), final_mode=0, time=0.0, autotune=False, want_iters=True,
+                 stream=None):
+        n = orig.shape[1]
+        dev = orig.device
+        self.orig, self.dirs, self.ray_time = orig, dirs, ray_time
+        self.pos = torch.empty((3, n), dtype=torch.float32, device=dev)
+        self.t = torch.empty(n, dtype=torch.float32, device=dev)
+        self.hit = torch.empty(n, dtype=torch.uint8, device=dev)
+        self.iters = torch.empty(n, dtype=torch.uint16, device=dev) if want_iters else None
+        self.normal = torch.empty((3, n), dtype=torch.float32, device=dev) if fine is not None else None
+        self.nets, self.fine, self.n_levels = list(nets), fine, len(nets)
+        p, keep = make_params(nets, delta, max_iters, eps, step_scale, box, final_mode, time)
+        b = FrameBatchC(orig.data_ptr(), dirs.data_ptr(), None if ray_time is None else ray_time.data_ptr(), n,
+                        self.pos.data_ptr(), self.t.data_ptr(), self.hit.data_ptr(),
+                        None if self.iters is None else self.iters.data_ptr(),
+                        None if self.normal is None else self.normal.data_ptr())
+        h = C.c_void_p()
+        _check(lib().sdf_plan_create(C.byref(p), None if fine is None else fine.handle, C.byref(b),
+                                     1 if autotune else 0, C.c_void_p(_stream(stream)), C.byref(h)))
+        del keep
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(lib().sdf_plan_launch(self.handle, C.c_void_p(_stream(stream))))
+
+    def info(self):
+        """(tile count per level, number of CUDA graph nodes)."""
+        tiles = (C.c_int * self.n_levels)()
+        nodes = C.c_int64()
+        _check(lib().sdf_plan_info(self.handle, tiles, self.n_levels, C.byref(nodes)))
+        return list(tiles), nodes.value
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().sdf_plan_free(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def render_host(nets, delta, max_iters, eps, fine: Net, orig, dirs, out_pos, out_hit, out_normal, *,

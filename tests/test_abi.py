@@ -65,3 +65,16 @@ def test_null_arguments_are_rejected(lib):
     assert lib.sdf_normals(None, None, 0, None, None) == -1
     lib.sdf_net_free.argtypes = [C.c_void_p]
     lib.sdf_net_free(None)
+    lib.sdf_normal_map_timed.argtypes = [C.c_void_p] * 4 + [C.c_int64, C.c_void_p, C.c_void_p]
+    assert lib.sdf_normal_map_timed(None, None, None, None, 0, None, None) == -1
+    # plans: NULL handles and arguments fail before any device work
+    h = C.c_void_p(1)
+    lib.sdf_plan_create.argtypes = [C.c_void_p] * 3 + [C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
+    assert lib.sdf_plan_create(None, None, None, 0, None, C.byref(h)) == -1 and h.value is None
+    assert lib.sdf_plan_create(None, None, None, 0, None, None) == -1
+    lib.sdf_plan_launch.argtypes = [C.c_void_p, C.c_void_p]
+    assert lib.sdf_plan_launch(None, None) == -1
+    lib.sdf_plan_info.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+    assert lib.sdf_plan_info(None, None, 0, None) == -1
+    lib.sdf_plan_free.argtypes = [C.c_void_p]
+    lib.sdf_plan_free(None)

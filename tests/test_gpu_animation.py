@@ -1,0 +1,198 @@
+"""GPU parity of the animated (4-D) path: per-ray times, frame batches and plans.
+
+The networks take (x, y, z, t) (Sec. 3.2).  A frame batch mixes frames of
+different sizes and times in one trace; the oracle traces each frame on its
+own at that frame's time.  Tolerances are those of tests/parity.py.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2201_09147_gb300 import inputs, workloads
+from parity import PRECISION_IDS, PRECISIONS, TOL, angle_report, trace_report
+
+pytestmark = pytest.mark.gpu
+
+FRAMES = [(48, 27, 0.0), (64, 36, 0.3), (40, 40, 0.55), (80, 45, 0.9)]
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _np(t):
+    return t.cpu().numpy()
+
+
+def _trace_direct(sdf, nets, fine, wl, o, d, t):
+    pos, tau, hit, iters = sdf.trace_multiscale(nets, wl.delta, wl.caps, wl.eps, o, d, step_scale=wl.step_scale,
+                                                final_mode=wl.final_mode, ray_time=t)
+    nrm = sdf.normal_map_timed(fine, pos, t, hit)
+    sdf.sync_status()
+    return pos, tau, hit, iters, nrm
+
+
+def _oracle_frames(wl, orig, dirs, off, pos, hit, idx_per_frame=None):
+    """Oracle trace of every frame at its own time, and the fine normals at the GPU's end points."""
+    onets = [oracle.Net(b) for b in wl.level_bytes()]
+    ofine = oracle.Net(wl.fine_bytes())
+    o_pos, o_hit, o_nrm = [], [], []
+    for k, (_, _, tk) in enumerate(wl.frames):
+        tk = float(np.float32(tk))  # the time as the GPU receives it
+        lo, hi = off[k], off[k + 1]
+        idx = np.arange(hi - lo) if idx_per_frame is None else idx_per_frame[k]
+        tp = oracle.TraceParams([oracle.SDF.of_net(n, time=tk) for n in onets], wl.delta, wl.caps, wl.step_scale,
+                                wl.eps, final_mode=wl.final_mode)
+        r = tp.trace_batch(orig[:, lo:hi], dirs[:, lo:hi], idx=idx)
+        o_pos.append(r["pos"])
+        o_hit.append(r["hit"])
+        gp = pos[:, lo:hi][:, idx].astype(np.float64)
+        o_nrm.append(ofine.normal_map(gp, hit[lo:hi][idx], time=tk))
+    return np.concatenate(o_pos, axis=1), np.concatenate(o_hit), np.concatenate(o_nrm, axis=1)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
+def test_frame_batch_vs_oracle(sdf, precision):
+    """Four frames of different sizes and times traced as one batch (per-ray times)."""
+    wl = workloads.get("animation_32", frames=FRAMES)
+    orig, dirs, tm, off = workloads.batch_rays(wl.frames)
+    nets = [sdf.Net(b, precision) for b in wl.level_bytes()]
+    fine = sdf.Net(wl.fine_bytes(), precision)
+    pos, _, hit, _, nrm = _trace_direct(sdf, nets, fine, wl, _dev(orig), _dev(dirs), _dev(tm))
+    pos, hit, nrm = _np(pos), _np(hit), _np(nrm)
+    o_pos, o_hit, o_nrm = _oracle_frames(wl, orig, dirs, off, pos, hit)
+    agree_tol, pos_tol, ang_tol = TOL[precision]
+    rep = trace_report(pos, hit, o_pos, o_hit)
+    print(precision, {k: v for k, v in rep.items() if k != "both"})
+    assert rep["agree"] >= agree_tol and rep["pos_p999"] <= pos_tol
+    for k in range(len(wl.frames)):  # every frame has a surface of its own
+        assert hit[off[k]:off[k + 1]].sum() > 100
+    ar = angle_report(nrm, o_nrm, hit.astype(bool))
+    print(ar)
+    assert ar["angle_p999"] <= ang_tol
+    assert np.all(nrm[:, hit == 0] == 0.0)
+
+
+def _random_4d(width, n_hidden):
+    return inputs.net_to_bytes(inputs.siren_init(3, width, n_hidden, in_dim=4, out_scale=30.0, out_shift=0.3))
+
+
+@pytest.mark.parametrize("shape", [(64, 1), (128, 2), (256, 1), (256, 3)])
+@pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
+def test_ray_time_bit_identical_to_constant_time(sdf, precision, shape):
+    """A per-ray time equal for all rays gives exactly the launch-constant result."""
+    b = _random_4d(*shape)
+    net = sdf.Net(b, precision)
+    orig, dirs = inputs.random_rays(5, 4096)
+    o, d = _dev(orig), _dev(dirs)
+    c = np.float32(0.37)
+    t = torch.full((orig.shape[1],), float(c), device="cuda")
+    a = sdf.trace_multiscale([net], [0.0], [24], 1e-3, o, d, time=float(c))
+    r = sdf.trace_multiscale([net], [0.0], [24], 1e-3, o, d, ray_time=t)
+    sdf.sync_status()
+    for x, y in zip(a, r):
+        assert torch.equal(x, y)
+    net.set_time(float(c))
+    n1 = sdf.normal_map(net, a[0], a[2])
+    n2 = sdf.normal_map_timed(net, a[0], t, a[2])
+    sdf.sync_status()
+    assert torch.equal(n1, n2)
+
+
+def test_ray_time_rejected_for_3d_networks(sdf):
+    wl = workloads.get("normal_map_1080p", 8, 8)
+    net = sdf.Net(wl.level_bytes()[0], sdf.SDF_BF16)
+    orig, dirs = wl.rays()
+    o, d = _dev(orig), _dev(dirs)
+    t = torch.zeros(orig.shape[1], device="cuda")
+    with pytest.raises(sdf.SdfError) as e:
+        sdf.trace_multiscale([net], [0.04], [8], 1e-3, o, d, final_mode=1, ray_time=t)
+    assert e.value.code == -1
+    with pytest.raises(sdf.SdfError) as e:
+        sdf.normal_map_timed(net, o, t)
+    assert e.value.code == -1
+    with pytest.raises(sdf.SdfError) as e:
+        sdf.Plan([net], [0.04], [8], 1e-3, o, d, fine=net, ray_time=t, final_mode=1)
+    assert e.value.code == -1
+
+
+@pytest.mark.parametrize("autotune", [False, True], ids=["default", "autotuned"])
+@pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
+def test_plan_matches_direct_calls(sdf, precision, autotune):
+    """The captured graph reproduces the direct calls bit for bit, launch after launch."""
+    wl = workloads.get("animation_32", frames=FRAMES)
+    orig, dirs, tm, off = workloads.batch_rays(wl.frames)
+    o, d, t = _dev(orig), _dev(dirs), _dev(tm)
+    nets = [sdf.Net(b, precision) for b in wl.level_bytes()]
+    fine = sdf.Net(wl.fine_bytes(), precision)
+    ref = _trace_direct(sdf, nets, fine, wl, o, d, t)
+    plan = sdf.Plan(nets, wl.delta, wl.caps, wl.eps, o, d, fine=fine, ray_time=t, step_scale=wl.step_scale,
+                    final_mode=wl.final_mode, autotune=autotune)
+    tiles, nodes = plan.info()
+    assert nodes >= len(nets) + 3
+    if precision == 0 or not autotune:
+        assert tiles == [0] * len(nets)
+    else:
+        assert all(1 <= x <= 6 for x in tiles)
+    for _ in range(2):
+        plan.pos.zero_()
+        plan.normal.zero_()
+        plan.launch()
+        sdf.sync_status()
+        assert torch.equal(plan.pos, ref[0]) and torch.equal(plan.t, ref[1]) and torch.equal(plan.hit, ref[2])
+        assert torch.equal(plan.iters, ref[3]) and torch.equal(plan.normal, ref[4])
+    plan.close()
+
+
+def test_plan_three_dimensional_and_trace_only(sdf):
+    """A plan of 3-D networks without times, and a trace-only plan, match the direct calls."""
+    wl = workloads.get("three_level_512", 96, 64)
+    orig, dirs = wl.rays()
+    o, d = _dev(orig), _dev(dirs)
+    nets = [sdf.Net(b, sdf.SDF_BF16) for b in wl.level_bytes()]
+    fine = sdf.Net(wl.fine_bytes(), sdf.SDF_BF16)
+    pos, tau, hit, iters = sdf.trace_multiscale(nets, wl.delta, wl.caps, wl.eps, o, d, step_scale=wl.step_scale,
+                                                final_mode=wl.final_mode)
+    nrm = sdf.normal_map(fine, pos, hit)
+    sdf.sync_status()
+    plan = sdf.Plan(nets, wl.delta, wl.caps, wl.eps, o, d, fine=fine, step_scale=wl.step_scale,
+                    final_mode=wl.final_mode, autotune=True)
+    plan.launch()
+    sdf.sync_status()
+    assert torch.equal(plan.pos, pos) and torch.equal(plan.hit, hit) and torch.equal(plan.normal, nrm)
+    tr = sdf.Plan(nets, wl.delta, wl.caps, wl.eps, o, d, step_scale=wl.step_scale, final_mode=wl.final_mode,
+                  want_iters=False)
+    tr.launch()
+    sdf.sync_status()
+    assert tr.normal is None and torch.equal(tr.pos, pos) and torch.equal(tr.hit, hit)
+
+
+@pytest.mark.parametrize("precision", [1, 3], ids=["bf16", "fp16"])
+def test_animation_32_frames_sampled(sdf, precision):
+    """All 32 frames (31,858,688 rays) in one autotuned plan, as the benchmark runs it; the
+    oracle traces 120 sampled rays of every frame."""
+    wl = workloads.get("animation_32")
+    orig, dirs, tm, off = workloads.batch_rays(wl.frames)
+    o, d, t = _dev(orig), _dev(dirs), _dev(tm)
+    nets = [sdf.Net(b, precision) for b in wl.level_bytes()]
+    fine = sdf.Net(wl.fine_bytes(), precision)
+    plan = sdf.Plan(nets, wl.delta, wl.caps, wl.eps, o, d, fine=fine, ray_time=t, step_scale=wl.step_scale,
+                    final_mode=wl.final_mode, autotune=True)
+    plan.launch()
+    sdf.sync_status()
+    pos, hit, nrm = _np(plan.pos), _np(plan.hit), _np(plan.normal)
+    assert set(np.unique(hit)) <= {0, 1}
+    assert np.all(nrm[:, hit == 0] == 0.0)
+    idx = [np.unique((inputs.uniform01(100 + k, 120) * (off[k + 1] - off[k])).astype(np.int64))
+           for k in range(len(wl.frames))]
+    o_pos, o_hit, o_nrm = _oracle_frames(wl, orig, dirs, off, pos, hit, idx)
+    flat = np.concatenate([off[k] + idx[k] for k in range(len(wl.frames))])
+    agree_tol, pos_tol, ang_tol = TOL[precision]
+    rep = trace_report(pos[:, flat], hit[flat], o_pos, o_hit)
+    print(precision, {k: v for k, v in rep.items() if k != "both"})
+    assert rep["agree"] >= agree_tol and rep["pos_p999"] <= pos_tol
+    assert rep["n_both"] > 300
+    ar = angle_report(nrm[:, flat], o_nrm, hit[flat].astype(bool))
+    print(ar)
+    assert ar["angle_p999"] <= ang_tol

@@ -205,6 +205,29 @@ def test_nested_3level_small(sdf, precision):
     assert ar["angle_p999"] <= TOL[precision][2]
 
 
+@pytest.mark.parametrize("name", ["three_level_512", "silhouette_512"])
+@pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
+def test_three_level_normal_map_small(sdf, precision, name):
+    """(64,1) |> (256,1 or 2), 20 + 5 steps to the delta shells, then (256,3) normals (Tab. 3), 128 x 128."""
+    wl = workloads.get(name, 128, 128)
+    orig, dirs = wl.rays()
+    lb = wl.level_bytes()
+    g = gpu_trace(sdf, lb, precision, wl, orig, dirs)
+    o = oracle_trace(lb, wl, orig, dirs)
+    rep = check_trace(g, o, precision, f"{name} p={precision}")
+    assert rep["n_both"] > 1500
+    assert g["iters"].max() <= sum(wl.caps)
+    if precision == 0:
+        assert np.mean(g["iters"] == o["iters"]) >= 0.99
+    fine = sdf.Net(wl.fine_bytes(), precision)
+    nrm = sdf.normal_map(fine, g["pos_dev"], g["hit_dev"])
+    sdf.sync_status()
+    ref = oracle.Net(wl.fine_bytes()).normal_map(g["pos"].astype(np.float64), g["hit"])
+    ar = angle_report(nrm.cpu().numpy(), ref, g["hit"].astype(bool))
+    print(ar)
+    assert ar["angle_p999"] <= TOL[precision][2]
+
+
 @pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
 def test_plain_256x3_small(sdf, precision):
     """The single-network (256,3) tracer (streamed weights on the tensor cores), 120 x 68 rays."""
