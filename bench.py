@@ -372,7 +372,27 @@ def main():
             ht.append((a, b))
         torch.cuda.synchronize()
         fp16_value = n / (statistics.mean([a.elapsed_time(b) for a, b in ht[args.warmup:]]) / 1e3) / 1e6
+        # BF16 coarse trace with E4M3 normal mapping (kind::f8f6f4 gradient kernel)
+        f8 = sdfnn.Net(wl.fine_bytes(), sdfnn.SDF_FP8, local)
+        et = []
+        for _ in range(args.warmup + args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            m = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sdfnn.trace_multiscale(coarse, wl.delta, wl.caps, wl.eps, orig, dirs, step_scale=wl.step_scale,
+                                   final_mode=wl.final_mode, out_pos=pos, out_t=tt, out_hit=hit, want_iters=False)
+            m.record(stream)
+            sdfnn.normal_map(f8, pos, hit, out=nrm)
+            b.record(stream)
+            et.append((a, m, b))
+        torch.cuda.synchronize()
+        fp8_value = n / (statistics.mean([a.elapsed_time(b) for a, _, b in et[args.warmup:]]) / 1e3) / 1e6
+        fp8_nm_ms = statistics.mean([m.elapsed_time(b) for _, m, b in et[args.warmup:]])
         result["comparisons"] = {"fp16_Mrays_s": fp16_value,
+                                 "fp8_normal_map_Mrays_s": fp8_value,
+                                 "fp8_normal_map_ms": fp8_nm_ms,
                                  "plain_fp32_256x3_Mrays_s": plain_value,
                                  "speedup_vs_plain_fp32": value / ws / plain_value,
                                  "multiscale_fp32_Mrays_s": ms_fp32_value,
@@ -478,6 +498,7 @@ def main():
         result["error_vs_oracle"] = error_of(coarse, fine)
         if not args.no_plain:
             result["error_vs_oracle_fp16"] = error_of(c16, f16)
+            result["error_vs_oracle_fp8_normal_map"] = error_of(coarse, f8)
     if rank == 0:
         print(json.dumps(result))
     if ws > 1:

@@ -29,6 +29,7 @@ struct sdf_net {
     size_t off_w0 = 0, off_b0 = 0, off_wt[kMaxHidden] = {}, off_bh[kMaxHidden] = {}, off_wout = 0;
     uint32_t bf16_layer_bytes = 0;
     int rows_pad = 0;
+    float q_w[kMaxHidden] = {}, q_g[kMaxHidden + 1] = {}, q_o = 1.0f;  // SDF_FP8 scales
 };
 
 namespace {
@@ -153,6 +154,73 @@ uint16_t to_bf16_rne(float x) {
     return static_cast<uint16_t>(u >> 16);
 }
 
+// E4M3: 1 sign bit, 4 exponent bits (bias 7), 3 mantissa bits; subnormals
+// below 2^-6 with spacing 2^-9; largest finite value 448; no infinities.
+// Rounds to nearest even and saturates to +-448.
+uint8_t to_e4m3(double x) {
+    const uint8_t sign = std::signbit(x) ? 0x80u : 0u;
+    const double a = std::fabs(x);
+    if (std::isnan(a)) return sign | 0x7Fu;
+    if (a >= 448.0) return sign | 0x7Eu;
+    int e = 0;
+    std::frexp(a, &e);
+    int E = std::max(e - 1, -6);                            // a in [2^E, 2^(E+1)) for normals
+    const double r = std::nearbyint(std::ldexp(a, 3 - E));  // multiples of the spacing 2^(E-3)
+    int code;
+    if (r < 8.0)
+        code = static_cast<int>(r);                          // subnormal (E = -6)
+    else if (r < 16.0)
+        code = ((E + 7) << 3) | (static_cast<int>(r) - 8);
+    else
+        code = (E + 8) << 3;                                 // rounded up to the next binade
+    return sign | static_cast<uint8_t>(std::min(code, 0x7E));
+}
+
+double from_e4m3(uint8_t c) {
+    const int biased = (c >> 3) & 15, mant = c & 7;
+    const double v = biased == 0 ? std::ldexp(mant, -9) : std::ldexp(8 + mant, biased - 10);
+    return (c & 0x80u) ? -v : v;
+}
+
+// Largest |G_l| (tangents of Alg. 2 after layer l, over the three spatial
+// directions and all units) at a 7 x 7 x 7 grid of points spanning the cube
+// [-1, 1]^3 (time 0.5 for 4-input networks), in FP64.
+void tangent_maxima(const std::vector<std::vector<double>>& Wl, const std::vector<std::vector<double>>& bl, int IN,
+                    int W, int KH, double* out) {
+    for (int l = 0; l <= KH; ++l) out[l] = 0.0;
+    std::vector<double> P(W), G(3 * W), A(W), Pn(W), Gn(3 * W);
+    for (int gi = 0; gi < 343; ++gi) {
+        const double x[4] = {-1.0 + (gi % 7) / 3.0, -1.0 + (gi / 7 % 7) / 3.0, -1.0 + (gi / 49) / 3.0, 0.5};
+        for (int i = 0; i < W; ++i) {
+            double z = bl[0][i];
+            for (int c = 0; c < IN; ++c) z += Wl[0][static_cast<size_t>(i) * IN + c] * x[c];
+            P[i] = std::sin(z);
+            for (int c = 0; c < 3; ++c) {
+                G[c * W + i] = Wl[0][static_cast<size_t>(i) * IN + c] * std::cos(z);
+                out[0] = std::max(out[0], std::fabs(G[c * W + i]));
+            }
+        }
+        for (int l = 1; l <= KH; ++l) {
+            for (int i = 0; i < W; ++i) {
+                const double* row = &Wl[l][static_cast<size_t>(i) * W];
+                double z = bl[l][i], g[3] = {0.0, 0.0, 0.0};
+                for (int k = 0; k < W; ++k) {
+                    z += row[k] * P[k];
+                    for (int c = 0; c < 3; ++c) g[c] += row[k] * G[c * W + k];
+                }
+                Pn[i] = std::sin(z);
+                const double cz = std::cos(z);
+                for (int c = 0; c < 3; ++c) {
+                    Gn[c * W + i] = cz * g[c];
+                    out[l] = std::max(out[l], std::fabs(Gn[c * W + i]));
+                }
+            }
+            P.swap(Pn);
+            G.swap(Gn);
+        }
+    }
+}
+
 NetView view_of(const sdf_net* n) {
     NetView v{};
     v.in_dim = n->in_dim;
@@ -171,6 +239,14 @@ NetView view_of(const sdf_net* n) {
     v.wbf_layer_bytes = n->bf16_layer_bytes;
     v.rows_pad = n->rows_pad;
     v.op_f16 = n->precision == SDF_FP16 ? 1 : 0;
+    if (n->precision == SDF_FP8) {
+        v.op_fp8 = 1;
+        v.wbf_lo = nullptr;
+        for (int l = 0; l < n->n_hidden; ++l) v.q_w[l] = n->q_w[l];
+        for (int l = 0; l <= n->n_hidden; ++l) v.q_g[l] = n->q_g[l];
+        v.q_o = n->q_o;
+        v.wout_q = n->d_bf16 + static_cast<size_t>(n->n_hidden) * n->bf16_layer_bytes;
+    }
     return v;
 }
 
@@ -186,8 +262,7 @@ int load_from_memory(const uint8_t* buf, size_t len, int precision, int device, 
     if (!out) return fail(SDF_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!buf) return fail(SDF_ERR_ARG, "bytes is NULL");
-    if (precision == SDF_FP8) return fail(SDF_ERR_UNSUPPORTED, "FP8 hidden layers are not built in this version");
-    if (precision != SDF_FP32 && precision != SDF_BF16 && precision != SDF_FP16)
+    if (precision != SDF_FP32 && precision != SDF_BF16 && precision != SDF_FP16 && precision != SDF_FP8)
         return fail(SDF_ERR_ARG, "unknown precision %d", precision);
     if (len < 32 || std::memcmp(buf, "SDFN", 4) != 0) return fail(SDF_ERR_FORMAT, "not an SDFN image");
     const uint32_t version = rd_u32(buf + 4), in_dim = rd_u32(buf + 8), width = rd_u32(buf + 12);
@@ -203,6 +278,8 @@ int load_from_memory(const uint8_t* buf, size_t len, int precision, int device, 
         n_hidden > static_cast<uint32_t>(kMaxHidden))
         return fail(SDF_ERR_UNSUPPORTED, "shape in=%u (w=%u, k=%u) not supported (in 3|4, w 64|128|256, 1<=k<=%d)",
                     in_dim, width, n_hidden, kMaxHidden);
+    if (precision == SDF_FP8 && width < 128)
+        return fail(SDF_ERR_UNSUPPORTED, "E4M3 hidden layers need width 128 or 256 (got %u)", width);
     if (!std::isfinite(omega0) || !std::isfinite(omega)) return fail(SDF_ERR_NONFINITE, "non-finite omega");
     const uint8_t* q = buf + 32;
     for (size_t i = 0; i < count; ++i)
@@ -290,6 +367,38 @@ int load_from_memory(const uint8_t* buf, size_t len, int precision, int device, 
         }
     }
 
+    // E4M3 hidden weights with per-layer scales 448 / max|W_l|, K-major with the
+    // 128-byte swizzle (128-element K blocks); then the output row as head and
+    // remainder; tangent scales from the calibration grid (largest |G_l| -> 64)
+    if (precision == SDF_FP8) {
+        n->rows_pad = W;
+        n->bf16_layer_bytes = static_cast<uint32_t>(W) * W;
+        bf.assign(static_cast<size_t>(KH) * n->bf16_layer_bytes + 2 * static_cast<size_t>(W), 0);
+        for (int l = 1; l <= KH; ++l) {
+            double amax = 0.0;
+            for (double v : Wl[l]) amax = std::max(amax, std::fabs(v));
+            const double qw = amax > 0.0 ? 448.0 / amax : 1.0;
+            n->q_w[l - 1] = static_cast<float>(qw);
+            uint8_t* dst = bf.data() + static_cast<size_t>(l - 1) * n->bf16_layer_bytes;
+            for (int r = 0; r < W; ++r)
+                for (int k = 0; k < W; ++k)
+                    dst[sw128_offset8(r, k, W)] = to_e4m3(Wl[l][static_cast<size_t>(r) * W + k] * qw);
+        }
+        double amax = 0.0;
+        for (double v : wout) amax = std::max(amax, std::fabs(v));
+        const double qo = amax > 0.0 ? 448.0 / amax : 1.0;
+        n->q_o = static_cast<float>(qo);
+        uint8_t* wq = bf.data() + static_cast<size_t>(KH) * n->bf16_layer_bytes;
+        for (int k = 0; k < W; ++k) {
+            const uint8_t hd = to_e4m3(wout[k] * qo);
+            wq[k] = hd;
+            wq[W + k] = to_e4m3((wout[k] * qo - from_e4m3(hd)) * 16.0);
+        }
+        double gmax[kMaxHidden + 1];
+        tangent_maxima(Wl, bl, IN, W, KH, gmax);
+        for (int l = 0; l <= KH; ++l) n->q_g[l] = static_cast<float>(gmax[l] > 0.0 ? 64.0 / gmax[l] : 1.0);
+    }
+
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();
@@ -353,6 +462,8 @@ int validate_trace(const sdf_trace_params* P, const float* orig, const float* di
             return fail(SDF_ERR_ARG, "step_scale[%d] must be finite and > 0", j);
         if (!P->step_scale && !(net->lipschitz > 0.0))
             return fail(SDF_ERR_ARG, "nets[%d] has a zero Lipschitz bound; pass step_scale", j);
+        if (net->precision == SDF_FP8)
+            return fail(SDF_ERR_UNSUPPORTED, "nets[%d]: tracing with E4M3 hidden layers is not built", j);
         if (net->precision != SDF_FP32 && !tc_trace_supported(net->width, net->n_hidden))
             return fail(SDF_ERR_UNSUPPORTED, "tensor-core tracing of a (%d,%d) network is not built", net->width,
                         net->n_hidden);

@@ -203,6 +203,19 @@ __device__ __forceinline__ void mma_f16kind(uint32_t d_tmem, uint64_t a_desc, ui
         : "memory");
 }
 
+// D[tmem] (+)= A[smem] * B[smem]^T with 8-bit operands (kind::f8f6f4).  With
+// the instruction descriptor's A/B format fields 0 both operands are E4M3;
+// one instruction covers K = 32 (32 bytes of each row).
+__device__ __forceinline__ void mma_f8kind(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Arrive once on the mbarrier when all previously issued MMAs of this thread
 // have completed.
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -247,6 +260,14 @@ __host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t row, uint32_t
     uint32_t kb = k >> 6, kk = k & 63u;
     uint32_t chunk = (kk >> 3) ^ (row & 7u);
     return kb * rows * 128u + row * 128u + chunk * 16u + (kk & 7u) * 2u;
+}
+
+// Byte offset of 8-bit element k of `row` in the same layout: 128-element
+// K blocks, 16-element chunks.
+__host__ __device__ __forceinline__ uint32_t sw128_offset8(uint32_t row, uint32_t k, uint32_t rows) {
+    uint32_t kb = k >> 7, kk = k & 127u;
+    uint32_t chunk = (kk >> 4) ^ (row & 7u);
+    return kb * rows * 128u + row * 128u + chunk * 16u + (kk & 15u);
 }
 
 // Byte offset of the 16-byte chunk holding elements k8*8 .. k8*8+7 of `row`.
@@ -298,6 +319,15 @@ template <bool F16>
 __device__ __forceinline__ uint32_t pack16x2(float lo, float hi) {
     return F16 ? pack_f16x2(lo, hi) : pack_bf16x2(lo, hi);
 }
+// Four floats as E4M3 bytes (round to nearest even, saturating to +-448),
+// a in the lowest byte.
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+    uint16_t lo, hi;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(b), "f"(a));
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(d), "f"(c));
+    return static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
+}
+
 template <bool F16>
 __device__ __forceinline__ uint16_t bits16(float x) {
     return F16 ? f16_bits(x) : bf16_bits(x);

@@ -21,8 +21,17 @@ struct NetView {
     const uint8_t* wbf;            // 16-bit hidden weights in the 128-byte-swizzled K-major layout
     const uint8_t* wbf_lo;         // 16-bit rounding of (weight - head), same layout, or NULL
     uint32_t wbf_layer_bytes;      // bytes per hidden layer in wbf
-    int rows_pad;                  // rows per 64-wide K block in wbf (max(width, 128), zero padded)
+    int rows_pad;                  // rows per 128-byte K block in wbf (max(width, 128), zero padded)
     int op_f16;                    // tensor-core operand type of wbf: 1 = IEEE half, 0 = bfloat16
+    // E4M3 networks (op_fp8 = 1): wbf holds the hidden weights as E4M3 bytes
+    // (128-element K blocks) scaled by q_w[l]; wout_q the output row as a head
+    // (W bytes, scaled by q_o) and a remainder (W bytes, scaled by 16 q_o);
+    // q_g[l] is the scale of the tangents stored after layer l (0 = input layer).
+    int op_fp8;
+    float q_w[kMaxHidden];
+    float q_g[kMaxHidden + 1];
+    float q_o;
+    const uint8_t* wout_q;
 };
 
 // One level of Alg. 1 as launched.

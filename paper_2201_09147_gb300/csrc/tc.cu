@@ -557,35 +557,47 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
 // 32 points x 4 streams each).  Each half has its own epilogue warp group,
 // TMEM columns and barriers; the MMA warp alternates between the halves, so
 // the tensor core works on one half while the other half's epilogue
-// (sin/cos, tangent scaling, 16-bit stores) runs.  The producer warp streams
+// (sin/cos, tangent scaling, operand stores) runs.  The producer warp streams
 // every hidden layer's K blocks once per half.
-template <int W>
+//
+// Operand types (OP): bfloat16 or IEEE half (kind::f16), or E4M3
+// (kind::f8f6f4, widths 128 and 256).  With E4M3 every stored operand carries
+// a scale: hidden weights W_l * q_w[l] (q_w = 448 / max|W_l|), the sine
+// stream 256 * sin, the tangent streams G_l * q_g[l] (q_g from the load-time
+// calibration), w_out * q_o as a head row plus a remainder row scaled by a
+// further 16; the epilogues divide the accumulators back.
+enum : int { kOpBF16 = 0, kOpF16 = 1, kOpE4M3 = 2 };
+constexpr float kFp8ActScale = 256.0f;
+
+template <int W, int OP>
 struct GradCfg {
+    static constexpr int EB = OP == kOpE4M3 ? 1 : 2;  // operand bytes per element
     static constexpr int MT = (W + 127) / 128;      // TMEM tiles of 128 feature rows
-    static constexpr int ROWS = MT * 128;           // feature rows incl. zero padding
-    static constexpr int KB = W / 64;               // 64-wide K blocks
+    static constexpr int KB = W * EB / 128;         // 128-byte K blocks
     static constexpr int NPTS = 64;                 // points per tile
     static constexpr int HPTS = 32;                 // points per half
     static constexpr int NROWS = 4 * NPTS;          // rows of X (point-streams)
     static constexpr int HROWS = 4 * HPTS;          // rows of X per half = MMA N
-    static constexpr int NS = (W == 256) ? 5 : 8;   // weight ring stages (one K block of one TMEM tile each)
+    // weight ring stages (one K block of one TMEM tile each)
+    static constexpr int NS = (OP != kOpE4M3 && W == 256) ? 5 : 8;
     static constexpr int GROUP_WARPS = 4 * MT;      // epilogue warps per half
     static constexpr int GROUP_THREADS = GROUP_WARPS * 32;
     static constexpr int EPI_WARPS = 2 * GROUP_WARPS;
     static constexpr int PRODUCER_WARP = EPI_WARPS;
     static constexpr int MMA_WARP = EPI_WARPS + 1;
     static constexpr int THREADS = (EPI_WARPS + 2) * 32;
-    static constexpr uint32_t STAGE_BYTES = 128u * 128u;  // 128 feature rows x 64 K (16-bit)
+    static constexpr uint32_t STAGE_BYTES = 128u * 128u;  // 128 feature rows x one K block
     static constexpr int TMEM_COLS = MT * 256;      // per TMEM tile: half 0 at +0, half 1 at +128
+    static_assert(KB >= 1, "E4M3 gradients need width >= 128");
 };
 
 struct GradLayout {
     uint32_t x, ring, woutb, w0, wt, bh, pts, idx, bars, misc, total;
 };
 
-template <int W>
+template <int W, int OP>
 __host__ __device__ inline GradLayout grad_layout(int KH) {
-    using C = GradCfg<W>;
+    using C = GradCfg<W, OP>;
     GradLayout L;
     uint32_t o = 0;
     L.x = o;
@@ -642,16 +654,62 @@ __device__ __forceinline__ void store_pair(uint32_t x_s, int m, int lane, int pe
     st_shared_u32(x_s + sw128_offset(p * 4 + 3, m0, NROWS), w3);
 }
 
-template <int W, bool F16>
-__global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const GradArgs a) {
-    using C = GradCfg<W>;
+__device__ __forceinline__ uint32_t sel4(uint32_t i, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3) {
+    return i == 0u ? a0 : (i == 1u ? a1 : (i == 2u ? a2 : a3));
+}
+
+// 8-bit counterpart of store_pair for four points p0 .. p0+3 (v[q][s]: point
+// p0 + q, stream s, already scaled), exchanged within the lane quad of
+// features m0 .. m0+3 (m0 = m & ~3): lane j = m & 3 gathers point p0 + j of
+// all four features and writes its four rows as 32-bit words of features
+// m0 .. m0+3.  At step i it writes stream (i + j) & 3, which puts the quad's
+// four rows on four different phases of the 128-byte swizzle, so each of the
+// warp's four stores is conflict free.
+template <int NROWS>
+__device__ __forceinline__ void store_quad8(uint32_t x_s, int m, int lane, int p0, const float (&v)[4][4]) {
+    const uint32_t j = static_cast<uint32_t>(lane) & 3u;
+    const uint32_t w0 = pack_e4m3x4(v[0][0], v[0][1], v[0][2], v[0][3]);
+    const uint32_t w1 = pack_e4m3x4(v[1][0], v[1][1], v[1][2], v[1][3]);
+    const uint32_t w2 = pack_e4m3x4(v[2][0], v[2][1], v[2][2], v[2][3]);
+    const uint32_t w3 = pack_e4m3x4(v[3][0], v[3][1], v[3][2], v[3][3]);
+    // lane j keeps its word of point j and swaps its word of point j ^ x with lane j ^ x
+    const uint32_t own = sel4(j, w0, w1, w2, w3);
+    const uint32_t g1 = __shfl_xor_sync(0xffffffffu, sel4(j ^ 1u, w0, w1, w2, w3), 1);
+    const uint32_t g2 = __shfl_xor_sync(0xffffffffu, sel4(j ^ 2u, w0, w1, w2, w3), 2);
+    const uint32_t g3 = __shfl_xor_sync(0xffffffffu, sel4(j ^ 3u, w0, w1, w2, w3), 3);
+    // r_i: point p0 + j of feature m0 + i (byte s = stream s)
+    const uint32_t r0 = sel4(j, own, g1, g2, g3), r1 = sel4(j ^ 1u, own, g1, g2, g3);
+    const uint32_t r2 = sel4(j ^ 2u, own, g1, g2, g3), r3 = sel4(j ^ 3u, own, g1, g2, g3);
+    const uint32_t m0 = static_cast<uint32_t>(m) & ~3u;
+#pragma unroll
+    for (uint32_t i = 0; i < 4; ++i) {
+        const uint32_t st = (i + j) & 3u;
+        const uint32_t sel = st | ((st + 4u) << 4);
+        const uint32_t word = prmt(prmt(r0, r1, sel), prmt(r2, r3, sel), 0x5410u);
+        st_shared_u32(x_s + sw128_offset8((p0 + j) * 4u + st, m0, NROWS), word);
+    }
+}
+
+template <int OP>
+__device__ __forceinline__ void mma_op(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (OP == kOpE4M3)
+        mma_f8kind(d, a, b, idesc, acc);
+    else
+        mma_f16kind(d, a, b, idesc, acc);
+}
+
+template <int W, int OP>
+__global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const GradArgs a) {
+    using C = GradCfg<W, OP>;
+    constexpr bool F16 = OP == kOpF16;
+    constexpr bool FP8 = OP == kOpE4M3;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const uint32_t raw_s = smem_u32(smem_raw);
     const uint32_t base_s = (raw_s + 1023u) & ~1023u;
     uint8_t* base = smem_raw + (base_s - raw_s);
     const NetView& net = a.net;
     const int KH = net.n_hidden;
-    const GradLayout L = grad_layout<W>(KH);
+    const GradLayout L = grad_layout<W, OP>(KH);
     float* w0s = reinterpret_cast<float*>(base + L.w0);
     float* wts = reinterpret_cast<float*>(base + L.wt);
     float* bhs = reinterpret_cast<float*>(base + L.bh);
@@ -687,16 +745,21 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
         stage_layer0(net, a.time, timed, i, w0s, wts);
         for (int l = 0; l < KH; ++l) bhs[l * W + i] = net.bh[l][i];
     }
-    // w_out split into a 16-bit head (row 0) and the 16-bit rounding of its
-    // remainder (row 1) of a 16-row K-major operand (rows 2..15 zero): the
-    // output MMA then carries w_out to about 16 significant bits.
+    // w_out as a head (row 0) and the rounding of its remainder (row 1) of a
+    // 16-row K-major operand (rows 2..15 zero): the output MMA then carries
+    // w_out to about twice the operand's significand bits.
     for (int i = tid; i < C::KB * 16 * 128 / 4; i += C::THREADS) reinterpret_cast<uint32_t*>(base + L.woutb)[i] = 0u;
     __syncthreads();
     for (int k = tid; k < W; k += C::THREADS) {
-        const float w = net.wout[k];
-        const uint16_t hi = bits16<F16>(w);
-        *reinterpret_cast<uint16_t*>(base + L.woutb + sw128_offset(0, k, 16)) = hi;
-        *reinterpret_cast<uint16_t*>(base + L.woutb + sw128_offset(1, k, 16)) = bits16<F16>(w - from16<F16>(hi));
+        if (FP8) {
+            base[L.woutb + sw128_offset8(0, k, 16)] = net.wout_q[k];
+            base[L.woutb + sw128_offset8(1, k, 16)] = net.wout_q[W + k];
+        } else {
+            const float w = net.wout[k];
+            const uint16_t hi = bits16<F16>(w);
+            *reinterpret_cast<uint16_t*>(base + L.woutb + sw128_offset(0, k, 16)) = hi;
+            *reinterpret_cast<uint16_t*>(base + L.woutb + sw128_offset(1, k, 16)) = bits16<F16>(w - from16<F16>(hi));
+        }
     }
     fence_proxy_async_smem();
     tc_fence_before();
@@ -737,8 +800,9 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
         }
     } else if (warp == C::MMA_WARP) {
         if (lane == 0) {
-            constexpr uint32_t idesc_h = idesc_f32acc(128, C::HROWS, F16);
-            constexpr uint32_t idesc_o = idesc_f32acc(128, 16, F16);
+            // E4M3: the format fields 0 of this descriptor select E4M3 under kind::f8f6f4
+            constexpr uint32_t idesc_h = idesc_f32acc(128, C::HROWS, F16 || FP8);
+            constexpr uint32_t idesc_o = idesc_f32acc(128, 16, F16 || FP8);
             uint32_t g = 0, xr_phase[2] = {0u, 0u};
             for (long long i = 0; i < my_pairs && ok; ++i) {
                 for (int l = 0; l <= KH && ok; ++l) {
@@ -758,10 +822,10 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
                                     tc_fence_after();
 #pragma unroll
                                     for (int kk = 0; kk < 4; ++kk)
-                                        mma_f16kind(tmem + mt * 256u + h * 128u,
-                                                    desc_kmajor_sw128(ring_s + stage * C::STAGE_BYTES + kk * 32u),
-                                                    desc_kmajor_sw128(xh + kb * C::NROWS * 128u + kk * 32u), idesc_h,
-                                                    (kb | kk) != 0);
+                                        mma_op<OP>(tmem + mt * 256u + h * 128u,
+                                                   desc_kmajor_sw128(ring_s + stage * C::STAGE_BYTES + kk * 32u),
+                                                   desc_kmajor_sw128(xh + kb * C::NROWS * 128u + kk * 32u), idesc_h,
+                                                   (kb | kk) != 0);
                                     mma_commit(bar_empty + 8u * stage);
                                 }
                             }
@@ -770,10 +834,9 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
                             for (int kb = 0; kb < C::KB; ++kb)
 #pragma unroll
                                 for (int kk = 0; kk < 4; ++kk)
-                                    mma_f16kind(tmem + h * 128u,
-                                                desc_kmajor_sw128(xh + kb * C::NROWS * 128u + kk * 32u),
-                                                desc_kmajor_sw128(wo_s + kb * 16u * 128u + kk * 32u), idesc_o,
-                                                (kb | kk) != 0);
+                                    mma_op<OP>(tmem + h * 128u, desc_kmajor_sw128(xh + kb * C::NROWS * 128u + kk * 32u),
+                                               desc_kmajor_sw128(wo_s + kb * 16u * 128u + kk * 32u), idesc_o,
+                                               (kb | kk) != 0);
                         }
                         if (ok) mma_commit(bar_dfull + 8u * h);
                     }
@@ -789,6 +852,9 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
         const int gt = ge * 32 + lane;  // thread index within the group
         const uint32_t lane_addr = tmem + (static_cast<uint32_t>(quad * 32) << 16) + mt * 256u + h * 128u;
         const int p0 = h * C::HPTS;
+        // E4M3 scales: sine stream, tangents after layer 0
+        const float sf = FP8 ? kFp8ActScale : 1.0f;
+        const float g0s = FP8 ? net.q_g[0] : 1.0f;
         uint32_t df_phase = 0;
         for (long long i = 0; i < my_pairs; ++i) {
             const long long base_pt = ((i * G + blockIdx.x) * 2 + h) * C::HPTS;
@@ -807,23 +873,39 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
             if (live) {
                 const float4 u = reinterpret_cast<const float4*>(w0s)[m];
                 const float ut = wts[m];
-                for (int p = p0; p < p0 + C::HPTS; p += 2) {
-                    float ve[4], vo[4];
-                    {
-                        const float4 q4 = pts[p];
-                        const float z = fmaf(u.x, q4.x, fmaf(u.y, q4.y, fmaf(u.z, q4.z, fmaf(ut, q4.w, u.w))));
-                        float sn, cs;
-                        sincos_fast(z, &sn, &cs);
-                        ve[0] = sn; ve[1] = u.x * cs; ve[2] = u.y * cs; ve[3] = u.z * cs;
+                if (FP8) {
+                    for (int p = p0; p < p0 + C::HPTS; p += 4) {
+                        float o[4][4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float4 q4 = pts[p + q];
+                            const float z = fmaf(u.x, q4.x, fmaf(u.y, q4.y, fmaf(u.z, q4.z, fmaf(ut, q4.w, u.w))));
+                            float sn, cs;
+                            sincos_fast(z, &sn, &cs);
+                            const float cg = cs * g0s;
+                            o[q][0] = sn * sf; o[q][1] = u.x * cg; o[q][2] = u.y * cg; o[q][3] = u.z * cg;
+                        }
+                        store_quad8<C::NROWS>(x_s, m, lane, p, o);
                     }
-                    {
-                        const float4 q4 = pts[p + 1];
-                        const float z = fmaf(u.x, q4.x, fmaf(u.y, q4.y, fmaf(u.z, q4.z, fmaf(ut, q4.w, u.w))));
-                        float sn, cs;
-                        sincos_fast(z, &sn, &cs);
-                        vo[0] = sn; vo[1] = u.x * cs; vo[2] = u.y * cs; vo[3] = u.z * cs;
+                } else {
+                    for (int p = p0; p < p0 + C::HPTS; p += 2) {
+                        float ve[4], vo[4];
+                        {
+                            const float4 q4 = pts[p];
+                            const float z = fmaf(u.x, q4.x, fmaf(u.y, q4.y, fmaf(u.z, q4.z, fmaf(ut, q4.w, u.w))));
+                            float sn, cs;
+                            sincos_fast(z, &sn, &cs);
+                            ve[0] = sn; ve[1] = u.x * cs; ve[2] = u.y * cs; ve[3] = u.z * cs;
+                        }
+                        {
+                            const float4 q4 = pts[p + 1];
+                            const float z = fmaf(u.x, q4.x, fmaf(u.y, q4.y, fmaf(u.z, q4.z, fmaf(ut, q4.w, u.w))));
+                            float sn, cs;
+                            sincos_fast(z, &sn, &cs);
+                            vo[0] = sn; vo[1] = u.x * cs; vo[2] = u.y * cs; vo[3] = u.z * cs;
+                        }
+                        store_pair<F16, C::NROWS>(x_s, m, lane, p, ve, vo);
                     }
-                    store_pair<F16, C::NROWS>(x_s, m, lane, p, ve, vo);
                 }
             }
             fence_proxy_async_smem();
@@ -836,21 +918,43 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
                 if (!ok) break;
                 tc_fence_after();
                 const float bb = live ? bhs[l * W + m] : 0.0f;
+                // accumulator -> value multipliers of the sine and tangent streams, and the
+                // tangent scale of the operand this layer stores (all 1 for 16-bit operands)
+                const float mf = FP8 ? 1.0f / (net.q_w[l] * sf) : 1.0f;
+                const float mg = FP8 ? net.q_g[l + 1] / (net.q_w[l] * net.q_g[l]) : 1.0f;
 #pragma unroll 1
                 for (int q = 0; q < C::HROWS / 32; ++q) {
                     float v[32];
                     tmem_ld32(lane_addr + q * 32u, v);
                     tmem_wait_ld();
                     if (live) {
+                        if (FP8) {
 #pragma unroll
-                        for (int pp = 0; pp < 8; pp += 2) {
-                            // P_i = sin(A_i);  G_i = (W_i G_{i-1}) (.) cos(A_i)
-                            float ve[4], vo[4], sn, cs;
-                            sincos_fast(v[pp * 4] + bb, &sn, &cs);
-                            ve[0] = sn; ve[1] = cs * v[pp * 4 + 1]; ve[2] = cs * v[pp * 4 + 2]; ve[3] = cs * v[pp * 4 + 3];
-                            sincos_fast(v[pp * 4 + 4] + bb, &sn, &cs);
-                            vo[0] = sn; vo[1] = cs * v[pp * 4 + 5]; vo[2] = cs * v[pp * 4 + 6]; vo[3] = cs * v[pp * 4 + 7];
-                            store_pair<F16, C::NROWS>(x_s, m, lane, p0 + q * 8 + pp, ve, vo);
+                            for (int pq = 0; pq < 8; pq += 4) {
+                                // P_i = sin(A_i);  G_i = (W_i G_{i-1}) (.) cos(A_i), rescaled
+                                float o[4][4];
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    const int c = (pq + e) * 4;
+                                    float sn, cs;
+                                    sincos_fast(fmaf(v[c], mf, bb), &sn, &cs);
+                                    const float cg = cs * mg;
+                                    o[e][0] = sn * sf; o[e][1] = cg * v[c + 1]; o[e][2] = cg * v[c + 2];
+                                    o[e][3] = cg * v[c + 3];
+                                }
+                                store_quad8<C::NROWS>(x_s, m, lane, p0 + q * 8 + pq, o);
+                            }
+                        } else {
+#pragma unroll
+                            for (int pp = 0; pp < 8; pp += 2) {
+                                // P_i = sin(A_i);  G_i = (W_i G_{i-1}) (.) cos(A_i)
+                                float ve[4], vo[4], sn, cs;
+                                sincos_fast(v[pp * 4] + bb, &sn, &cs);
+                                ve[0] = sn; ve[1] = cs * v[pp * 4 + 1]; ve[2] = cs * v[pp * 4 + 2]; ve[3] = cs * v[pp * 4 + 3];
+                                sincos_fast(v[pp * 4 + 4] + bb, &sn, &cs);
+                                vo[0] = sn; vo[1] = cs * v[pp * 4 + 5]; vo[2] = cs * v[pp * 4 + 6]; vo[3] = cs * v[pp * 4 + 7];
+                                store_pair<F16, C::NROWS>(x_s, m, lane, p0 + q * 8 + pp, ve, vo);
+                            }
                         }
                     }
                 }
@@ -866,7 +970,7 @@ __global__ void __launch_bounds__(GradCfg<W>::THREADS) grad_tc_kernel(const Grad
                 tmem_ld32(tmem + (static_cast<uint32_t>(quad * 32) << 16) + h * 128u, v);
                 tmem_wait_ld();
                 // lane row r = 32 quad + lane of this half = 4 * point + stream; head + remainder of w_out
-                const float val = v[0] + v[1];
+                const float val = FP8 ? fmaf(v[1], 1.0f / 16.0f, v[0]) * (1.0f / (net.q_o * net.q_g[KH])) : v[0] + v[1];
                 const int g = lane & ~3;
                 const float gx = __shfl_sync(0xffffffffu, val, g + 1);
                 const float gy = __shfl_sync(0xffffffffu, val, g + 2);
@@ -1033,15 +1137,25 @@ cudaError_t launch_trace_level_tc(const LevelArgs& a, int num_sms, cudaStream_t 
 
 bool tc_trace_split(int width, int n_hidden) { return width <= 128 && trace_split(width, n_hidden); }
 
+template <int W, int OP>
+static cudaError_t launch_grad_op(const GradArgs& a, int num_sms, cudaStream_t s) {
+    using C = GradCfg<W, OP>;
+    const size_t smem = grad_layout<W, OP>(a.net.n_hidden).total + 1024;
+    return launch_tc(grad_tc_kernel<W, OP>, C::THREADS, smem, C::TMEM_COLS, num_sms, s, &a);
+}
+
 template <int W>
 static cudaError_t launch_grad_w(const GradArgs& a, int num_sms, cudaStream_t s) {
-    const size_t smem = grad_layout<W>(a.net.n_hidden).total + 1024;
-    if (a.net.op_f16)
-        return launch_tc(grad_tc_kernel<W, true>, GradCfg<W>::THREADS, smem, GradCfg<W>::TMEM_COLS, num_sms, s, &a);
-    return launch_tc(grad_tc_kernel<W, false>, GradCfg<W>::THREADS, smem, GradCfg<W>::TMEM_COLS, num_sms, s, &a);
+    if (a.net.op_f16) return launch_grad_op<W, kOpF16>(a, num_sms, s);
+    return launch_grad_op<W, kOpBF16>(a, num_sms, s);
 }
 
 cudaError_t launch_grad_tc(const GradArgs& a, int num_sms, cudaStream_t s) {
+    if (a.net.op_fp8) {
+        if (a.net.width == 128) return launch_grad_op<128, kOpE4M3>(a, num_sms, s);
+        if (a.net.width == 256) return launch_grad_op<256, kOpE4M3>(a, num_sms, s);
+        return cudaErrorInvalidValue;
+    }
     switch (a.net.width) {
     case 64:
         return launch_grad_w<64>(a, num_sms, s);

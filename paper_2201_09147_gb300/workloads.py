@@ -83,8 +83,9 @@ def random_siren_64x1() -> inputs.SineNet:
     return inputs.siren_init(0, 64, 1, out_scale=30.0, out_shift=0.3)
 
 
-# delta of the 4-D (64,1) against the 4-D (256,3)
-ANIM_DELTA = 0.04
+# delta of the 4-D (64,1) against the 4-D (256,3): the largest |f_c - f_f| found near the
+# surface (|f_f| < 0.05) over 20,000 points at five times was 0.057
+ANIM_DELTA = 0.06
 
 
 def animation_frames(counts=((8, 256, 256), (16, 1280, 720), (8, 1920, 1080))):

@@ -13,8 +13,8 @@ import torch
 
 import oracle
 from paper_2201_09147_gb300 import inputs, workloads
-from parity import (HIT_AGREEMENT, PRECISION_IDS, PRECISIONS, RANDOM_NET_ANGLE_FACTOR, TOL, angle_report,
-                    trace_report)
+from parity import (FP8_ANGLE_MEDIAN_DEG, FP8_ANGLE_P999_DEG, FP8_MAGNITUDE_REL, HIT_AGREEMENT, PRECISION_IDS,
+                    PRECISIONS, RANDOM_NET_ANGLE_FACTOR, TOL, angle_report, trace_report)
 
 pytestmark = pytest.mark.gpu
 
@@ -279,6 +279,45 @@ def test_mesh_normal_map(sdf, precision):
     ar = angle_report(out.cpu().numpy(), ref)
     print(ar)
     assert ar["angle_p999"] <= TOL[precision][2]
+
+
+@pytest.mark.parametrize("name", ["s8_256x3", "s8_256x2", "s8_128x2", "s8_256x1"])
+def test_fp8_gradients_vs_oracle(sdf, name):
+    """E4M3 hidden layers (kind::f8f6f4) against FP64: surface points of the displaced
+    icosphere and uniform points of the box; the unnormalised gradient checks the scales."""
+    b = (workloads.SCENES / f"{name}.sdfn").read_bytes()
+    net = sdf.Net(b, sdf.SDF_FP8)
+    surf, _ = workloads.mesh_points(subdivisions=5)
+    box = inputs.random_points(7, 20000)
+    onet = oracle.Net(b)
+    for label, pts in (("surface", surf), ("box", box)):
+        d = torch.from_numpy(pts).cuda()
+        g = sdf.normals(net, d)
+        nm = sdf.normal_map(net, d)
+        sdf.sync_status()
+        g, nm = g.cpu().numpy(), nm.cpu().numpy()
+        ref = onet.grad_batch(pts.astype(np.float64))
+        ar = angle_report(nm, ref)
+        mag = np.abs(np.linalg.norm(g, axis=0) / np.linalg.norm(ref, axis=0) - 1.0)
+        print(name, label, ar, "mag p99.9", float(np.quantile(mag, 0.999)))
+        assert ar["angle_median"] <= FP8_ANGLE_MEDIAN_DEG
+        if label == "surface":
+            assert ar["angle_p999"] <= FP8_ANGLE_P999_DEG
+            assert float(np.quantile(mag, 0.999)) <= FP8_MAGNITUDE_REL
+        # normal_map is the normalised gradient of the same kernel
+        assert np.allclose(nm, g / np.maximum(np.linalg.norm(g, axis=0), 1e-12), atol=1e-5)
+
+
+def test_fp8_limits(sdf):
+    """E4M3 covers the gradients of width 128 / 256 networks; tracing with it is not built."""
+    with pytest.raises(sdf.SdfError) as e:
+        sdf.Net((workloads.SCENES / "s8_64x1.sdfn").read_bytes(), sdf.SDF_FP8)
+    assert e.value.code == -7
+    net = sdf.Net((workloads.SCENES / "s8_256x1.sdfn").read_bytes(), sdf.SDF_FP8)
+    d = torch.zeros((3, 16), device="cuda")
+    with pytest.raises(sdf.SdfError) as e:
+        sdf.trace_multiscale([net], [0.0], [8], 1e-3, d, d)
+    assert e.value.code == -7
 
 
 # ---------------------------------------------------------------------------
