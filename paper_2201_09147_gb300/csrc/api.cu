@@ -831,7 +831,7 @@ int plan_create(const sdf_trace_params* P, sdf_net_t fine, const sdf_frame_batch
         free_plan(p);
         return cuda_fail(e, "cudaStreamCreate");
     }
-    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) {
         cudaStreamDestroy(cs);
         free_plan(p);
