@@ -592,7 +592,7 @@ struct GradCfg {
 };
 
 struct GradLayout {
-    uint32_t x, ring, woutb, w0, wt, bh, pts, idx, bars, misc, total;
+    uint32_t x, ring, woutb, w0, wt, pts, idx, bars, misc, total;
 };
 
 template <int W, int OP>
@@ -610,8 +610,6 @@ __host__ __device__ inline GradLayout grad_layout(int KH) {
     o += W * 4u * 4u;
     L.wt = o;
     o += W * 4u;
-    L.bh = o;
-    o += static_cast<uint32_t>(KH) * W * 4u;
     L.pts = o;
     o += C::NPTS * 4u * 4u;
     L.idx = o;
@@ -712,7 +710,6 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
     const GradLayout L = grad_layout<W, OP>(KH);
     float* w0s = reinterpret_cast<float*>(base + L.w0);
     float* wts = reinterpret_cast<float*>(base + L.wt);
-    float* bhs = reinterpret_cast<float*>(base + L.bh);
     float4* pts = reinterpret_cast<float4*>(base + L.pts);  // (x, y, z, t) per point
     int* idxs = reinterpret_cast<int*>(base + L.idx);
     const uint32_t bar_full = base_s + L.bars;             // NS barriers
@@ -741,10 +738,7 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
         tmem_relinquish();
     }
     const bool timed = a.pt_time != nullptr && net.in_dim == 4;
-    for (int i = tid; i < W; i += C::THREADS) {
-        stage_layer0(net, a.time, timed, i, w0s, wts);
-        for (int l = 0; l < KH; ++l) bhs[l * W + i] = net.bh[l][i];
-    }
+    for (int i = tid; i < W; i += C::THREADS) stage_layer0(net, a.time, timed, i, w0s, wts);
     // w_out as a head (row 0) and the rounding of its remainder (row 1) of a
     // 16-row K-major operand (rows 2..15 zero): the output MMA then carries
     // w_out to about twice the operand's significand bits.
@@ -917,7 +911,7 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
                 df_phase ^= 1u;
                 if (!ok) break;
                 tc_fence_after();
-                const float bb = live ? bhs[l * W + m] : 0.0f;
+                const float bb = live ? __ldg(net.bh[l] + m) : 0.0f;  // one load per layer and half-tile
                 // accumulator -> value multipliers of the sine and tangent streams, and the
                 // tangent scale of the operand this layer stores (all 1 for 16-bit operands)
                 const float mf = FP8 ? 1.0f / (net.q_w[l] * sf) : 1.0f;
