@@ -165,6 +165,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="lean run for ncu: the timed steps only (no L2 flush buffer, no comparison legs)")
+    ap.add_argument("--profile-normals", default="bf16", choices=["bf16", "fp16", "fp8"],
+                    help="with --profile: operand type of the normal-mapping network")
     args = ap.parse_args()
     if args.profile:
         args.no_cpu_baseline = args.no_plain = True
@@ -187,7 +189,10 @@ def main():
     orig = torch.from_numpy(orig_h).cuda()
     dirs = torch.from_numpy(dirs_h).cuda()
     coarse = [sdfnn.Net(b, sdfnn.SDF_BF16, local) for b in wl.level_bytes()]
-    fine = sdfnn.Net(wl.fine_bytes(), sdfnn.SDF_BF16, local)
+    fine_prec = {"bf16": sdfnn.SDF_BF16, "fp16": sdfnn.SDF_FP16, "fp8": sdfnn.SDF_FP8}[args.profile_normals]
+    if not args.profile:
+        fine_prec = sdfnn.SDF_BF16
+    fine = sdfnn.Net(wl.fine_bytes(), fine_prec, local)
     pos = torch.empty((3, n), device="cuda")
     tt = torch.empty(n, device="cuda")
     hit = torch.empty(n, dtype=torch.uint8, device="cuda")
