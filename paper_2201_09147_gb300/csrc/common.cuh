@@ -182,6 +182,22 @@ __device__ __forceinline__ uint64_t desc_kmajor_sw128(uint32_t smem_addr) {
     return d;
 }
 
+// Shared-memory descriptor of an MN-major operand with the 128-byte swizzle:
+// atoms of 8 K rows x 128 bytes of MN; `lbo` = byte stride between atoms
+// along MN, SBO = 1024 (8-row K groups back to back).  The instruction
+// descriptor marks the operand as MN-major (bit 15 for A, bit 16 for B).
+__device__ __forceinline__ uint64_t desc_mnmajor_sw128(uint32_t smem_addr, uint32_t lbo) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((smem_addr & 0x3FFFFu) >> 4);
+    d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+    d |= static_cast<uint64_t>(1024u >> 4) << 32;
+    d |= static_cast<uint64_t>(1u) << 46;
+    d |= static_cast<uint64_t>(2u) << 61;
+    return d;
+}
+constexpr uint32_t kIdescMajorMnA = 1u << 15;
+constexpr uint32_t kIdescMajorMnB = 1u << 16;
+
 // Instruction descriptor of tcgen05.mma.kind::f16 with FP32 D and both
 // operands K-major: D format at bits 4-5 (1 = F32), A/B formats at bits
 // 7-9 / 10-12 (0 = F16, 1 = BF16; A and B always share one type), N >> 3 at

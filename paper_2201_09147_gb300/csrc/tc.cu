@@ -560,6 +560,14 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
 // (sin/cos, tangent scaling, operand stores) runs.  The producer warp streams
 // every hidden layer's K blocks once per half.
 //
+// X layout.  16-bit operands: MN-major (point-streams contiguous) with the
+// 128-byte swizzle: per half, 2 atoms of 64 point-streams at stride W * 128
+// bytes, 8-feature K groups of 1024 bytes; the thread that owns feature m
+// writes two points (8 values, 16 bytes) per vector store, with no exchange
+// between lanes.  The hidden MMAs read X as an MN-major B operand, the output
+// MMA as an MN-major A operand.  E4M3 operands: K-major (rows =
+// point-streams), written through a lane-quad byte transpose.
+//
 // Operand types (OP): bfloat16 or IEEE half (kind::f16), or E4M3
 // (kind::f8f6f4, widths 128 and 256).  With E4M3 every stored operand carries
 // a scale: hidden weights W_l * q_w[l] (q_w = 448 / max|W_l|), the sine
@@ -623,37 +631,19 @@ __host__ __device__ inline GradLayout grad_layout(int KH) {
     return L;
 }
 
-// Stores the four stream values of two points (pe = even point, po = pe + 1)
-// of this thread's feature m into X as 32-bit words, together with lane m^1:
-// the even lane writes the rows of pe, the odd lane those of po, each word
-// holding features (m & ~1, m | 1).  One exchange of two packed words per
-// point pair; rows of pe and po fall in different 64-byte halves of the
-// swizzled layout, so a warp's store is a single conflict-free wavefront.
-template <bool F16, int NROWS>
-__device__ __forceinline__ void store_pair(uint32_t x_s, int m, int lane, int pe, const float (&ve)[4],
-                                           const float (&vo)[4]) {
-    const bool odd = lane & 1;
-    const uint32_t e01 = pack16x2<F16>(ve[0], ve[1]), e23 = pack16x2<F16>(ve[2], ve[3]);
-    const uint32_t o01 = pack16x2<F16>(vo[0], vo[1]), o23 = pack16x2<F16>(vo[2], vo[3]);
-    // the even lane keeps its even-point values and sends its odd-point values; the odd lane the reverse
-    const uint32_t k01 = odd ? o01 : e01, k23 = odd ? o23 : e23;
-    const uint32_t r01 = __shfl_xor_sync(0xffffffffu, odd ? e01 : o01, 1);
-    const uint32_t r23 = __shfl_xor_sync(0xffffffffu, odd ? e23 : o23, 1);
-    // low half of a word = feature m & ~1 (the even lane), high half = m | 1
-    const uint32_t lo01 = odd ? r01 : k01, hi01 = odd ? k01 : r01;
-    const uint32_t lo23 = odd ? r23 : k23, hi23 = odd ? k23 : r23;
-    const uint32_t w0 = prmt(lo01, hi01, 0x5410u), w1 = prmt(lo01, hi01, 0x7632u);
-    const uint32_t w2 = prmt(lo23, hi23, 0x5410u), w3 = prmt(lo23, hi23, 0x7632u);
-    const int p = pe + (odd ? 1 : 0);
-    const int m0 = m & ~1;
-    st_shared_u32(x_s + sw128_offset(p * 4 + 0, m0, NROWS), w0);
-    st_shared_u32(x_s + sw128_offset(p * 4 + 1, m0, NROWS), w1);
-    st_shared_u32(x_s + sw128_offset(p * 4 + 2, m0, NROWS), w2);
-    st_shared_u32(x_s + sw128_offset(p * 4 + 3, m0, NROWS), w3);
+// Byte offset in the MN-major 16-bit X of the 16-byte chunk holding points
+// 2c, 2c + 1 (all four streams) of half h for feature m.
+template <int W>
+__device__ __forceinline__ uint32_t xoff16(int h, int m, int c) {
+    return static_cast<uint32_t>(h) * (W * 256u) + static_cast<uint32_t>(c >> 3) * (W * 128u) +
+           static_cast<uint32_t>(m >> 3) * 1024u + static_cast<uint32_t>(m & 7) * 128u +
+           (static_cast<uint32_t>((c & 7) ^ (m & 7)) << 4);
 }
 
+// a_i for i in 0..3 with two predicated selects per bit (no branch)
 __device__ __forceinline__ uint32_t sel4(uint32_t i, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3) {
-    return i == 0u ? a0 : (i == 1u ? a1 : (i == 2u ? a2 : a3));
+    const uint32_t lo = (i & 1u) ? a1 : a0, hi = (i & 1u) ? a3 : a2;
+    return (i & 2u) ? hi : lo;
 }
 
 // 8-bit counterpart of store_pair for four points p0 .. p0+3 (v[q][s]: point
@@ -795,8 +785,8 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
     } else if (warp == C::MMA_WARP) {
         if (lane == 0) {
             // E4M3: the format fields 0 of this descriptor select E4M3 under kind::f8f6f4
-            constexpr uint32_t idesc_h = idesc_f32acc(128, C::HROWS, F16 || FP8);
-            constexpr uint32_t idesc_o = idesc_f32acc(128, 16, F16 || FP8);
+            constexpr uint32_t idesc_h = idesc_f32acc(128, C::HROWS, F16 || FP8) | (FP8 ? 0u : kIdescMajorMnB);
+            constexpr uint32_t idesc_o = idesc_f32acc(128, 16, F16 || FP8) | (FP8 ? 0u : kIdescMajorMnA);
             uint32_t g = 0, xr_phase[2] = {0u, 0u};
             for (long long i = 0; i < my_pairs && ok; ++i) {
                 for (int l = 0; l <= KH && ok; ++l) {
@@ -805,7 +795,8 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
                         xr_phase[h] ^= 1u;
                         if (!ok) break;
                         tc_fence_after();
-                        const uint32_t xh = x_s + h * C::HROWS * 128u;  // rows of this half within each K block
+                        // X of this half: K-major rows (E4M3), or the MN-major half block (16-bit)
+                        const uint32_t xh = FP8 ? x_s + h * C::HROWS * 128u : x_s + h * (W * 256u);
                         if (l < KH) {
                             // D[mt][h] = W_l[mt rows] . X_h^T over all K blocks
                             for (int kb = 0; kb < C::KB && ok; ++kb) {
@@ -815,11 +806,14 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
                                     if (!ok) break;
                                     tc_fence_after();
 #pragma unroll
-                                    for (int kk = 0; kk < 4; ++kk)
+                                    for (int kk = 0; kk < 4; ++kk) {
+                                        const uint64_t xd =
+                                            FP8 ? desc_kmajor_sw128(xh + kb * C::NROWS * 128u + kk * 32u)
+                                                : desc_mnmajor_sw128(xh + (kb * 8 + kk * 2) * 1024u, W * 128u);
                                         mma_op<OP>(tmem + mt * 256u + h * 128u,
-                                                   desc_kmajor_sw128(ring_s + stage * C::STAGE_BYTES + kk * 32u),
-                                                   desc_kmajor_sw128(xh + kb * C::NROWS * 128u + kk * 32u), idesc_h,
-                                                   (kb | kk) != 0);
+                                                   desc_kmajor_sw128(ring_s + stage * C::STAGE_BYTES + kk * 32u), xd,
+                                                   idesc_h, (kb | kk) != 0);
+                                    }
                                     mma_commit(bar_empty + 8u * stage);
                                 }
                             }
@@ -827,10 +821,13 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
                             // output layer of this half: rows = its 128 point-streams, N = 16 (w_out head, remainder)
                             for (int kb = 0; kb < C::KB; ++kb)
 #pragma unroll
-                                for (int kk = 0; kk < 4; ++kk)
-                                    mma_op<OP>(tmem + h * 128u, desc_kmajor_sw128(xh + kb * C::NROWS * 128u + kk * 32u),
-                                               desc_kmajor_sw128(wo_s + kb * 16u * 128u + kk * 32u), idesc_o,
-                                               (kb | kk) != 0);
+                                for (int kk = 0; kk < 4; ++kk) {
+                                    const uint64_t xd =
+                                        FP8 ? desc_kmajor_sw128(xh + kb * C::NROWS * 128u + kk * 32u)
+                                            : desc_mnmajor_sw128(xh + (kb * 8 + kk * 2) * 1024u, W * 128u);
+                                    mma_op<OP>(tmem + h * 128u, xd, desc_kmajor_sw128(wo_s + kb * 16u * 128u + kk * 32u),
+                                               idesc_o, (kb | kk) != 0);
+                                }
                         }
                         if (ok) mma_commit(bar_dfull + 8u * h);
                     }
@@ -882,23 +879,19 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
                         store_quad8<C::NROWS>(x_s, m, lane, p, o);
                     }
                 } else {
-                    for (int p = p0; p < p0 + C::HPTS; p += 2) {
-                        float ve[4], vo[4];
-                        {
-                            const float4 q4 = pts[p];
+#pragma unroll 4
+                    for (int c = 0; c < C::HPTS / 2; ++c) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const float4 q4 = pts[p0 + 2 * c + e];
                             const float z = fmaf(u.x, q4.x, fmaf(u.y, q4.y, fmaf(u.z, q4.z, fmaf(ut, q4.w, u.w))));
                             float sn, cs;
                             sincos_fast(z, &sn, &cs);
-                            ve[0] = sn; ve[1] = u.x * cs; ve[2] = u.y * cs; ve[3] = u.z * cs;
+                            w[2 * e] = pack16x2<F16>(sn, u.x * cs);
+                            w[2 * e + 1] = pack16x2<F16>(u.y * cs, u.z * cs);
                         }
-                        {
-                            const float4 q4 = pts[p + 1];
-                            const float z = fmaf(u.x, q4.x, fmaf(u.y, q4.y, fmaf(u.z, q4.z, fmaf(ut, q4.w, u.w))));
-                            float sn, cs;
-                            sincos_fast(z, &sn, &cs);
-                            vo[0] = sn; vo[1] = u.x * cs; vo[2] = u.y * cs; vo[3] = u.z * cs;
-                        }
-                        store_pair<F16, C::NROWS>(x_s, m, lane, p, ve, vo);
+                        st_shared_v4(x_s + xoff16<W>(h, m, c), w[0], w[1], w[2], w[3]);
                     }
                 }
             }
@@ -916,41 +909,49 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
                 // tangent scale of the operand this layer stores (all 1 for 16-bit operands)
                 const float mf = FP8 ? 1.0f / (net.q_w[l] * sf) : 1.0f;
                 const float mg = FP8 ? net.q_g[l + 1] / (net.q_w[l] * net.q_g[l]) : 1.0f;
-#pragma unroll 1
+                // the next 32 columns (8 points) load from TMEM while these 32 are processed
+                float va[32], vb[32];
+                tmem_ld32(lane_addr, va);
+                tmem_wait_ld();
+#pragma unroll
                 for (int q = 0; q < C::HROWS / 32; ++q) {
-                    float v[32];
-                    tmem_ld32(lane_addr + q * 32u, v);
-                    tmem_wait_ld();
-                    if (live) {
-                        if (FP8) {
+                    float(&v)[32] = (q & 1) ? vb : va;
+                    float(&vn)[32] = (q & 1) ? va : vb;
+                    if (q + 1 < C::HROWS / 32) tmem_ld32(lane_addr + (q + 1) * 32u, vn);
+                    if (live && !FP8) {
 #pragma unroll
-                            for (int pq = 0; pq < 8; pq += 4) {
-                                // P_i = sin(A_i);  G_i = (W_i G_{i-1}) (.) cos(A_i), rescaled
-                                float o[4][4];
+                        for (int c = 0; c < 4; ++c) {
+                            // P_i = sin(A_i);  G_i = (W_i G_{i-1}) (.) cos(A_i), points 2c, 2c + 1
+                            uint32_t w[4];
 #pragma unroll
-                                for (int e = 0; e < 4; ++e) {
-                                    const int c = (pq + e) * 4;
-                                    float sn, cs;
-                                    sincos_fast(fmaf(v[c], mf, bb), &sn, &cs);
-                                    const float cg = cs * mg;
-                                    o[e][0] = sn * sf; o[e][1] = cg * v[c + 1]; o[e][2] = cg * v[c + 2];
-                                    o[e][3] = cg * v[c + 3];
-                                }
-                                store_quad8<C::NROWS>(x_s, m, lane, p0 + q * 8 + pq, o);
+                            for (int e = 0; e < 2; ++e) {
+                                const int j = (2 * c + e) * 4;
+                                float sn, cs;
+                                sincos_fast(v[j] + bb, &sn, &cs);
+                                w[2 * e] = pack16x2<F16>(sn, cs * v[j + 1]);
+                                w[2 * e + 1] = pack16x2<F16>(cs * v[j + 2], cs * v[j + 3]);
                             }
-                        } else {
-#pragma unroll
-                            for (int pp = 0; pp < 8; pp += 2) {
-                                // P_i = sin(A_i);  G_i = (W_i G_{i-1}) (.) cos(A_i)
-                                float ve[4], vo[4], sn, cs;
-                                sincos_fast(v[pp * 4] + bb, &sn, &cs);
-                                ve[0] = sn; ve[1] = cs * v[pp * 4 + 1]; ve[2] = cs * v[pp * 4 + 2]; ve[3] = cs * v[pp * 4 + 3];
-                                sincos_fast(v[pp * 4 + 4] + bb, &sn, &cs);
-                                vo[0] = sn; vo[1] = cs * v[pp * 4 + 5]; vo[2] = cs * v[pp * 4 + 6]; vo[3] = cs * v[pp * 4 + 7];
-                                store_pair<F16, C::NROWS>(x_s, m, lane, p0 + q * 8 + pp, ve, vo);
-                            }
+                            st_shared_v4(x_s + xoff16<W>(h, m, q * 4 + c), w[0], w[1], w[2], w[3]);
                         }
                     }
+                    if (live && FP8) {
+#pragma unroll
+                        for (int pq = 0; pq < 8; pq += 4) {
+                            // the same, rescaled to the stored E4M3 operands
+                            float o[4][4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int j = (pq + e) * 4;
+                                float sn, cs;
+                                sincos_fast(fmaf(v[j], mf, bb), &sn, &cs);
+                                const float cg = cs * mg;
+                                o[e][0] = sn * sf; o[e][1] = cg * v[j + 1]; o[e][2] = cg * v[j + 2];
+                                o[e][3] = cg * v[j + 3];
+                            }
+                            store_quad8<C::NROWS>(x_s, m, lane, p0 + q * 8 + pq, o);
+                        }
+                    }
+                    tmem_wait_ld();
                 }
                 fence_proxy_async_smem();
                 tc_fence_before();
