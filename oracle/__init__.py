@@ -8,6 +8,13 @@ The C library ``sdf_oracle.c`` restates the paper plainly in double
 precision: Eq. 2 (network), Alg. 2 with Eqs. 3-4 (analytic normals), Alg. 1
 (multiscale sphere tracing), the neural normal mapping of Sec. 5 and the
 threshold recurrences of Props. 1-2 (Sec. 3.3).
+
+``fit_loss`` and ``adam_step`` (FP64, numpy on top of the C network) define
+the fitting objective and the optimiser step of the training path.  The
+paper trains each network of a sequence with an external framework it only
+cites (Sec. 2, Sec. 3.3); the objective restated here is the one that
+framework's SDF fitting uses: an L1 term on the values, a (1 - cos) term on
+the gradient directions at points near the surface and an Eikonal term.
 """
 from __future__ import annotations
 
@@ -254,3 +261,38 @@ def thresholds_prop2(eps):
     d = np.zeros_like(e)
     lib().oracle_thresholds_prop2(_dp(e), e.size, _dp(d))
     return d
+
+
+def fit_loss(net_bytes: bytes, pts, target_f, target_grad, near, lam_n: float, lam_e: float, time: float = 0.0):
+    """Fitting objective of one network at SoA points (3, n), in FP64:
+
+        L = mean_i |f(p_i) - g_i|
+          + lam_n * mean_{i near} (1 - <grad f(p_i), grad g_i> / (|grad f(p_i)| |grad g_i|))
+          + lam_e * mean_i | |grad f(p_i)| - 1 |
+
+    with f and grad f from Eq. 2 and Alg. 2; `near` marks the points that
+    enter the direction term (a mean over an empty set is 0).  Returns
+    (L, (l_val, l_dir, l_eik)).
+    """
+    gf, f = Net(net_bytes).grad_batch(pts, time=time, with_value=True)
+    tf = np.asarray(target_f, np.float64)
+    tg = np.asarray(target_grad, np.float64)
+    near = np.asarray(near).astype(bool)
+    l_val = float(np.mean(np.abs(f - tf)))
+    na = np.linalg.norm(gf, axis=0)
+    nb = np.linalg.norm(tg, axis=0)
+    cos = np.sum(gf * tg, axis=0) / (na * nb)
+    l_dir = float(np.mean(1.0 - cos[near])) if near.any() else 0.0
+    l_eik = float(np.mean(np.abs(na - 1.0)))
+    return l_val + lam_n * l_dir + lam_e * l_eik, (l_val, l_dir, l_eik)
+
+
+def adam_step(theta, grad, m, v, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8):
+    """One Adam update (Kingma and Ba) in FP64: returns (theta, m, v) after step `step` (1-based)."""
+    theta, grad = np.asarray(theta, np.float64), np.asarray(grad, np.float64)
+    m = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * grad
+    v = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * grad * grad
+    mh = m / (1.0 - beta1 ** step)
+    vh = v / (1.0 - beta2 ** step)
+    return theta - lr * mh / (np.sqrt(vh) + eps), m, v

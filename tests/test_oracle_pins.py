@@ -403,3 +403,72 @@ def test_prop1_thresholds_nest_successive_differences():
     d2 = oracle.thresholds_prop1(eps[:2])
     assert _nested(adv[0], d2[0], adv[1], d2[1])
     assert not _nested(adv[0], d2[0] * 0.97, adv[1], d2[1])
+
+
+# ---------------------------------------------------------------------------
+# fitting objective and optimiser step (the training path)
+# ---------------------------------------------------------------------------
+
+def _two_layer_by_hand(net, P):
+    """f and grad f of a (w, 1) plain network (omega = 1) at points P (n, 3) by
+    reverse-mode differentiation written out: grad f = W0^T [cos A0 (.) W1^T (cos A1 (.) w)]."""
+    W0, b0 = net.weights[0].astype(np.float64), net.biases[0].astype(np.float64)
+    W1, b1 = net.weights[1].astype(np.float64), net.biases[1].astype(np.float64)
+    wo, bo = net.weights[2][0].astype(np.float64), float(net.biases[2][0])
+    f, g = [], []
+    for p in P:
+        a0 = W0 @ p + b0
+        a1 = W1 @ np.sin(a0) + b1
+        f.append(wo @ np.sin(a1) + bo)
+        g.append(W0.T @ (np.cos(a0) * (W1.T @ (np.cos(a1) * wo))))
+    return np.array(f), np.array(g).T
+
+
+def test_fit_loss_matches_hand_computation():
+    net = inputs.random_plain_net(31, 5, 1, scale=1.2)
+    b = inputs.net_to_bytes(net)
+    rng = np.random.default_rng(3)
+    P = rng.uniform(-1, 1, (40, 3))
+    f, g = _two_layer_by_hand(net, P)
+    tf = rng.normal(size=40)
+    tg = rng.normal(size=(3, 40))
+    near = rng.uniform(size=40) < 0.4
+    lam_n, lam_e = 0.1, 0.05
+    l_val = np.mean(np.abs(f - tf))
+    cos = [np.dot(g[:, i], tg[:, i]) / np.linalg.norm(g[:, i]) / np.linalg.norm(tg[:, i]) for i in range(40)]
+    l_dir = np.mean([1.0 - c for c, m in zip(cos, near) if m])
+    l_eik = np.mean(np.abs(np.linalg.norm(g, axis=0) - 1.0))
+    L, parts = oracle.fit_loss(b, P.T.copy(), tf, tg, near, lam_n, lam_e)
+    assert np.allclose(parts, (l_val, l_dir, l_eik), rtol=1e-12, atol=1e-14)
+    assert abs(L - (l_val + lam_n * l_dir + lam_e * l_eik)) <= 1e-12
+
+
+def test_fit_loss_vanishes_on_the_network_itself():
+    """Targets equal to f and to any positive multiple of grad f zero the value and
+    direction terms; with no near points the direction term is 0."""
+    net = inputs.random_plain_net(32, 6, 1, scale=1.0)
+    b = inputs.net_to_bytes(net)
+    P = np.random.default_rng(4).uniform(-1, 1, (25, 3))
+    f, g = _two_layer_by_hand(net, P)
+    L, (lv, ld, le) = oracle.fit_loss(b, P.T.copy(), f, 3.0 * g, np.ones(25, bool), 0.1, 0.05)
+    assert lv <= 1e-14 and ld <= 1e-13
+    assert abs(le - np.mean(np.abs(np.linalg.norm(g, axis=0) - 1.0))) <= 1e-13
+    _, (_, ld0, _) = oracle.fit_loss(b, P.T.copy(), f, -g, np.zeros(25, bool), 0.1, 0.05)
+    assert ld0 == 0.0
+    _, (_, ld2, _) = oracle.fit_loss(b, P.T.copy(), f, -g, np.ones(25, bool), 0.1, 0.05)
+    assert abs(ld2 - 2.0) <= 1e-12  # opposite directions: 1 - cos = 2
+
+
+def test_adam_step_matches_torch_optimizer():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    theta0 = rng.normal(size=50)
+    grads = [rng.normal(size=50) for _ in range(4)]
+    t = torch.tensor(theta0, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([t], lr=1e-3, betas=(0.9, 0.999), eps=1e-8)
+    th, m, v = theta0.copy(), np.zeros(50), np.zeros(50)
+    for k, gk in enumerate(grads, start=1):
+        t.grad = torch.tensor(gk, dtype=torch.float64)
+        opt.step()
+        th, m, v = oracle.adam_step(th, gk, m, v, k, 1e-3)
+    assert np.allclose(t.detach().numpy(), th, rtol=0, atol=1e-15)
