@@ -253,6 +253,58 @@ int sdf_plan_launch(sdf_plan_t plan, void *cuda_stream);
 int sdf_plan_info(sdf_plan_t plan, int *tiles, int max_levels, int64_t *n_graph_nodes);
 void sdf_plan_free(sdf_plan_t plan);
 
+/* Training (FP32).
+ *
+ * The paper fits every network of a sequence with an external framework
+ * (Sec. 2, Sec. 3.3).  These calls make that fitting native: the forward
+ * pass of Eq. 2 together with the tangents of Alg. 2, the fitting objective,
+ * the backward pass through both (the direction and Eikonal terms depend on
+ * grad f, so their parameter gradients are second derivatives of f) and an
+ * Adam step.
+ *
+ * theta: device float32, the folded parameters (the frequencies multiplied
+ * in) in the order of the SDFN file - W_0 [w][in_dim], b_0, then for each
+ * hidden layer W_i [w][w], b_i, then w_out [w], b_out - 16-byte aligned.  An
+ * SDFN file with flags bit 0 set stores exactly this vector.
+ * Shapes: in_dim 3 or 4, width 64, 128 or 256, 1 <= n_hidden <= 4
+ * (SDF_ERR_UNSUPPORTED otherwise).
+ *
+ * sdf_train_shape_info: the length of theta and the workspace bytes the
+ *   forward / backward pair needs for n points (either pointer may be NULL).
+ * sdf_train_forward: f (n) and the unnormalised grad f (3, n) at pts (3, n)
+ *   (pt_time (n) for 4-input networks, else NULL); saves the layers'
+ *   pre-activations in `workspace` (device, 256-byte aligned, of the size
+ *   above) for the backward.
+ * sdf_train_backward: ADDS dL/dtheta to d_theta given d_f = dL/df (n) and
+ *   d_grad = dL/d(grad f) (3, n), from the workspace of the forward call made
+ *   with the same theta, points and n (zero d_theta first for a fresh
+ *   gradient).  Points are independent: chunks of a batch may be run one
+ *   after another into the same d_theta.
+ * sdf_fit_loss: the objective over n points
+ *     L = mean |f - g| + lam_n mean_near (1 - cos(grad f, grad g)) + lam_e mean | |grad f| - 1 |
+ *   (g, grad g: target_f (n), target_grad (3, n); near (n) uint8 marks the
+ *   points of the direction term, whose mean over no point is 0).  Writes
+ *   d_f, d_grad (the inputs of sdf_train_backward) and loss (device, 4
+ *   doubles: the three means and L).  Subgradients: sign(0) = 0; points
+ *   with grad f = 0 contribute no gradient to the direction and Eikonal terms.
+ * sdf_adam_step: one Adam update of `count` parameters in place (m, v: the
+ *   moment estimates, zero before step 1; step counts from 1).
+ * Errors: SDF_ERR_ARG (NULL / host pointers, bad sizes, misalignment),
+ * SDF_ERR_UNSUPPORTED, SDF_ERR_CUDA. */
+int sdf_train_shape_info(int in_dim, int width, int n_hidden, int64_t n, int64_t *param_count,
+                         int64_t *workspace_bytes);
+int sdf_train_forward(int in_dim, int width, int n_hidden, const float *theta, const float *pts,
+                      const float *pt_time, int64_t n, float *out_f, float *out_grad, void *workspace,
+                      void *cuda_stream);
+int sdf_train_backward(int in_dim, int width, int n_hidden, const float *theta, const float *pts,
+                       const float *pt_time, int64_t n, const float *d_f, const float *d_grad, void *workspace,
+                       float *d_theta, void *cuda_stream);
+int sdf_fit_loss(const float *f, const float *grad, const float *target_f, const float *target_grad,
+                 const uint8_t *near, int64_t n, float lam_n, float lam_e, float *d_f, float *d_grad, double *loss,
+                 void *cuda_stream);
+int sdf_adam_step(float *theta, const float *grad, float *m, float *v, int64_t count, float lr, float beta1,
+                  float beta2, float eps, int step, void *cuda_stream);
+
 /* Synchronises the stream, then returns and clears the status word of the
  * current device (SDF_OK, or the first device-side error since the last call). */
 int sdf_sync_status(void *cuda_stream);

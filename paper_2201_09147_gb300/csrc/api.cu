@@ -1026,6 +1026,160 @@ int sdf_plan_info(sdf_plan_t plan, int* tiles, int max_levels, int64_t* n_graph_
 
 void sdf_plan_free(sdf_plan_t plan) { free_plan(plan); }
 
+// ---------------------------------------------------------------------------
+// training path
+// ---------------------------------------------------------------------------
+static int train_check_shape(int in_dim, int width, int n_hidden) {
+    if ((in_dim != 3 && in_dim != 4) || (width != 64 && width != 128 && width != 256) || n_hidden < 1 ||
+        n_hidden > kMaxHidden)
+        return fail(SDF_ERR_UNSUPPORTED, "training shape in=%d (w=%d, k=%d) not supported (in 3|4, w 64|128|256, "
+                                         "1<=k<=%d)",
+                    in_dim, width, n_hidden, kMaxHidden);
+    return SDF_OK;
+}
+
+// Device of a device pointer (SDF_ERR_ARG if it is not one).
+static int device_of(const void* p, const char* name, int* dev) {
+    if (!p) return fail(SDF_ERR_ARG, "%s is NULL", name);
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SDF_ERR_ARG, "%s: not a CUDA pointer", name);
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(SDF_ERR_ARG, "%s must be device memory", name);
+    *dev = at.device;
+    return SDF_OK;
+}
+
+int sdf_train_shape_info(int in_dim, int width, int n_hidden, int64_t n, int64_t* param_count,
+                         int64_t* workspace_bytes) {
+    int rc = train_check_shape(in_dim, width, n_hidden);
+    if (rc) return rc;
+    if (n < 0 || n > 0x7fffffffLL) return fail(SDF_ERR_ARG, "n = %lld out of range", static_cast<long long>(n));
+    const TrainShape sh = train_shape(in_dim, width, n_hidden);
+    if (param_count) *param_count = sh.count;
+    if (workspace_bytes) *workspace_bytes = static_cast<int64_t>(train_workspace_bytes(sh, n));
+    return SDF_OK;
+}
+
+static int train_prepare(int in_dim, int width, int n_hidden, const float* theta, const float* pts,
+                         const float* pt_time, int64_t n, void* workspace, TrainArgs* a, int* dev) {
+    int rc = train_check_shape(in_dim, width, n_hidden);
+    if (rc) return rc;
+    if (n < 0 || n > 0x7fffffffLL) return fail(SDF_ERR_ARG, "n = %lld out of range", static_cast<long long>(n));
+    if (pt_time && in_dim != 4) return fail(SDF_ERR_ARG, "per-point times given for a 3-input network");
+    if ((rc = device_of(theta, "theta", dev))) return rc;
+    if (reinterpret_cast<uintptr_t>(theta) % 16) return fail(SDF_ERR_ARG, "theta must be 16-byte aligned");
+    if (n > 0) {
+        if ((rc = check_device_ptr(pts, *dev, "pts")) || (rc = check_device_ptr(workspace, *dev, "workspace")))
+            return rc;
+        if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(SDF_ERR_ARG, "workspace must be 256-byte aligned");
+        if (pt_time && (rc = check_device_ptr(pt_time, *dev, "time"))) return rc;
+    }
+    *a = TrainArgs{};
+    a->sh = train_shape(in_dim, width, n_hidden);
+    a->theta = theta;
+    a->pts = pts;
+    a->pt_time = pt_time;
+    a->n = n;
+    a->w = train_work(a->sh, n, workspace);
+    return SDF_OK;
+}
+
+int sdf_train_forward(int in_dim, int width, int n_hidden, const float* theta, const float* pts,
+                      const float* pt_time, int64_t n, float* out_f, float* out_grad, void* workspace,
+                      void* cuda_stream) {
+    TrainArgs a;
+    int dev = -1;
+    int rc = train_prepare(in_dim, width, n_hidden, theta, pts, pt_time, n, workspace, &a, &dev);
+    if (rc || n == 0) return rc;
+    if ((rc = check_device_ptr(out_f, dev, "out_f")) || (rc = check_device_ptr(out_grad, dev, "out_grad"))) return rc;
+    DeviceGuard g(dev);
+    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", dev);
+    DeviceInfo di;
+    if ((rc = device_info(dev, &di))) return rc;
+    a.out_f = out_f;
+    a.out_grad = out_grad;
+    cudaError_t e = launch_train_forward(a, di.num_sms, static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "launching the training forward");
+    return SDF_OK;
+}
+
+int sdf_train_backward(int in_dim, int width, int n_hidden, const float* theta, const float* pts,
+                       const float* pt_time, int64_t n, const float* d_f, const float* d_grad, void* workspace,
+                       float* d_theta, void* cuda_stream) {
+    TrainArgs a;
+    int dev = -1;
+    int rc = train_prepare(in_dim, width, n_hidden, theta, pts, pt_time, n, workspace, &a, &dev);
+    if (rc || n == 0) return rc;
+    if ((rc = check_device_ptr(d_f, dev, "d_f")) || (rc = check_device_ptr(d_grad, dev, "d_grad")) ||
+        (rc = check_device_ptr(d_theta, dev, "d_theta")))
+        return rc;
+    DeviceGuard g(dev);
+    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", dev);
+    DeviceInfo di;
+    if ((rc = device_info(dev, &di))) return rc;
+    a.d_f = d_f;
+    a.d_grad = d_grad;
+    a.d_theta = d_theta;
+    cudaError_t e = launch_train_backward(a, di.num_sms, static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "launching the training backward");
+    return SDF_OK;
+}
+
+int sdf_fit_loss(const float* f, const float* grad, const float* target_f, const float* target_grad,
+                 const uint8_t* near, int64_t n, float lam_n, float lam_e, float* d_f, float* d_grad, double* loss,
+                 void* cuda_stream) {
+    if (n < 0 || n > 0x7fffffffLL) return fail(SDF_ERR_ARG, "n = %lld out of range", static_cast<long long>(n));
+    if (!std::isfinite(lam_n) || !std::isfinite(lam_e)) return fail(SDF_ERR_ARG, "weights must be finite");
+    if (n == 0) return SDF_OK;
+    int dev = -1, rc;
+    if ((rc = device_of(f, "f", &dev))) return rc;
+    if ((rc = check_device_ptr(grad, dev, "grad")) || (rc = check_device_ptr(target_f, dev, "target_f")) ||
+        (rc = check_device_ptr(target_grad, dev, "target_grad")) || (rc = check_device_ptr(near, dev, "near")) ||
+        (rc = check_device_ptr(d_f, dev, "d_f")) || (rc = check_device_ptr(d_grad, dev, "d_grad")) ||
+        (rc = check_device_ptr(loss, dev, "loss")))
+        return rc;
+    DeviceGuard g(dev);
+    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", dev);
+    DeviceInfo di;
+    if ((rc = device_info(dev, &di))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    Scratch sc;
+    sc.s = s;
+    cudaError_t e = cudaMallocAsync(&sc.ptr, 64, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(loss scratch)");
+    double* sums = static_cast<double*>(sc.ptr);
+    auto* cnt = reinterpret_cast<unsigned long long*>(sums + 4);
+    e = launch_fit_loss(f, grad, target_f, target_grad, near, n, lam_n, lam_e, d_f, d_grad, sums, cnt, loss, di.num_sms,
+                        s);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the fitting objective");
+    return SDF_OK;
+}
+
+int sdf_adam_step(float* theta, const float* grad, float* m, float* v, int64_t count, float lr, float beta1,
+                  float beta2, float eps, int step, void* cuda_stream) {
+    if (count < 0) return fail(SDF_ERR_ARG, "count < 0");
+    if (step < 1) return fail(SDF_ERR_ARG, "step counts from 1");
+    if (!(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f) || !std::isfinite(lr) || !(eps > 0.0f))
+        return fail(SDF_ERR_ARG, "bad Adam hyper-parameters");
+    if (count == 0) return SDF_OK;
+    int dev = -1, rc;
+    if ((rc = device_of(theta, "theta", &dev))) return rc;
+    if ((rc = check_device_ptr(grad, dev, "grad")) || (rc = check_device_ptr(m, dev, "m")) ||
+        (rc = check_device_ptr(v, dev, "v")))
+        return rc;
+    DeviceGuard g(dev);
+    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", dev);
+    DeviceInfo di;
+    if ((rc = device_info(dev, &di))) return rc;
+    cudaError_t e = launch_adam(theta, grad, m, v, count, lr, beta1, beta2, eps, step, di.num_sms,
+                                static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "launching Adam");
+    return SDF_OK;
+}
+
 const char* sdf_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"

@@ -87,6 +87,50 @@ bool tc_trace_supported(int width, int n_hidden);
 bool tc_trace_split(int width, int n_hidden);  // head+remainder operands in the trace kernel
 bool tc_grad_supported(int width, int n_hidden);
 
+// ---------------------------------------------------------------------------
+// training path (FP32)
+// ---------------------------------------------------------------------------
+// Parameter vector theta: the folded parameters of Eq. 2 in the order of the
+// SDFN file (W_0 [w][in], b_0, then per hidden layer W_i [w][w], b_i, then
+// w_out [w], b_out), FP32.
+struct TrainShape {
+    int in_dim, width, n_hidden;
+    int64_t off_w0, off_b0, off_w[kMaxHidden], off_b[kMaxHidden], off_wout, off_bout, count;
+};
+TrainShape train_shape(int in_dim, int width, int n_hidden);
+
+// Workspace of one forward / backward pair over n points.
+struct TrainWork {
+    float* wt;                     // [k][w][w] transposed hidden weights
+    float* z0;                     // [n][w] layer-0 pre-activations A_0
+    float* z;                      // [k][n][4][w] per hidden layer: A_i and the tangent pre-images W_i G_{i-1}
+    float* d;                      // [k][n][4][w] their adjoints (backward)
+    unsigned long long* counters;  // [4] tile counters
+};
+size_t train_workspace_bytes(const TrainShape& sh, int64_t n);
+TrainWork train_work(const TrainShape& sh, int64_t n, void* ws);
+
+struct TrainArgs {
+    TrainShape sh;
+    const float* theta;
+    const float* pts;      // SoA (3, n)
+    const float* pt_time;  // (n) or NULL (4-input networks)
+    int64_t n;
+    float* out_f;          // forward: (n)
+    float* out_grad;       // forward: SoA (3, n)
+    const float* d_f;      // backward: dL/df (n)
+    const float* d_grad;   // backward: dL/d(grad f) SoA (3, n)
+    TrainWork w;
+    float* d_theta;        // backward: accumulated dL/dtheta
+};
+cudaError_t launch_train_forward(const TrainArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_train_backward(const TrainArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_fit_loss(const float* f, const float* grad, const float* tf, const float* tgrad,
+                            const uint8_t* near, int64_t n, float lam_n, float lam_e, float* d_f, float* d_grad,
+                            double* sums, unsigned long long* n_near, double* out, int num_sms, cudaStream_t s);
+cudaError_t launch_adam(float* theta, const float* grad, float* m, float* v, int64_t count, float lr, float beta1,
+                        float beta2, float eps, int step, int num_sms, cudaStream_t s);
+
 // Builds list[] of the indices with mask[i] != 0 (order unspecified), zeroes
 // out[.][i] where mask[i] == 0, and counts into *count (zero at launch).
 cudaError_t launch_mask_compact(const uint8_t* mask, int64_t n, int32_t* list, unsigned long long* count,

@@ -268,6 +268,22 @@ class SphereScene:
     def lipschitz(self) -> float:
         return 1.0 + self.amp * self.freq * math.sqrt(3.0)
 
+    def value_and_grad(self, p: np.ndarray):
+        """g and its gradient at points p of shape (n, 3), float64 (the gradient of the
+        nearest sphere's distance plus that of the displacement)."""
+        p = np.asarray(p, np.float64)
+        diff = p[:, None, :] - self.centres[None]
+        dist = np.linalg.norm(diff, axis=-1)
+        k = np.argmin(dist - self.radii[None], axis=1)
+        rows = np.arange(p.shape[0])
+        nrm = diff[rows, k] / np.maximum(dist[rows, k], 1e-300)[:, None]
+        a, fr = self.amp, self.freq
+        sx, sy, sz = np.sin(fr * p[:, 0]), np.sin(fr * p[:, 1]), np.sin(fr * p[:, 2])
+        cx, cy, cz = np.cos(fr * p[:, 0]), np.cos(fr * p[:, 1]), np.cos(fr * p[:, 2])
+        val = dist[rows, k] - self.radii[k] + a * sx * sy * sz
+        grad = nrm + a * fr * np.stack([cx * sy * sz, sx * cy * sz, sx * sy * cz], axis=1)
+        return val, grad
+
 
 def sphere_scene(seed: int = 1, m: int = 8, time: float | None = None) -> SphereScene:
     """m spheres, centre U[-0.6, 0.6]^3 then radius U[0.15, 0.3], from SplitMix64(seed).
@@ -286,6 +302,35 @@ def sphere_scene(seed: int = 1, m: int = 8, time: float | None = None) -> Sphere
         ang = 2.0 * math.pi * time + phase
         centres = centres + 0.15 * np.stack([np.cos(ang), np.sin(ang), np.zeros(m)], axis=1)
     return SphereScene(centres, np.array(radii))
+
+
+def fit_batch(scene: SphereScene, seed: int, n: int):
+    """Training points of the fitting objective and their targets, from SplitMix64(seed):
+    the first n // 2 near the surface (a sphere picked uniformly, a uniform direction,
+    the radius plus N(0, 0.02^2) normal jitter), the rest uniform in [-1, 1]^3.
+    Returns pts (3, n), target value (n), target gradient (3, n) as float32 and the
+    near-surface flags (n) as uint8."""
+    rng = _Stream(seed)
+    half = n // 2
+    m = len(scene.radii)
+    k = np.minimum((rng.uniform(half, 0.0, 1.0) * m).astype(np.int64), m - 1)
+    z = rng.uniform(half, -1.0, 1.0)
+    phi = rng.uniform(half, 0.0, 2.0 * math.pi)
+    s = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    u = np.stack([s * np.cos(phi), s * np.sin(phi), z], axis=1)
+    # Box-Muller normal jitter of the radius
+    u1 = np.maximum(rng.uniform(half, 0.0, 1.0), 1e-300)
+    u2 = rng.uniform(half, 0.0, 1.0)
+    jit = 0.02 * np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+    near = scene.centres[k] + (scene.radii[k] + jit)[:, None] * u
+    unif = np.stack([rng.uniform(n - half, -1.0, 1.0) for _ in range(3)], axis=1)
+    p = np.clip(np.concatenate([near, unif]), -1.0, 1.0)
+    p32 = p.astype(np.float32)
+    val, grad = scene.value_and_grad(p32.astype(np.float64))
+    flags = np.zeros(n, np.uint8)
+    flags[:half] = 1
+    return (np.ascontiguousarray(p32.T), val.astype(np.float32), np.ascontiguousarray(grad.T, dtype=np.float32),
+            flags)
 
 
 # --------------------------------------------------------------------------

@@ -23,7 +23,8 @@ ERRORS = {-1: "SDF_ERR_ARG", -2: "SDF_ERR_FILE", -3: "SDF_ERR_FORMAT", -4: "SDF_
 EXPORTS = ["sdf_net_load", "sdf_net_load_mem", "sdf_net_info", "sdf_net_set_time", "sdf_net_free",
            "sdf_trace_multiscale", "sdf_normals", "sdf_normal_map", "sdf_render_host", "sdf_sync_status",
            "sdf_last_error", "sdf_trace_multiscale_noalloc", "sdf_normal_map_timed", "sdf_plan_create",
-           "sdf_plan_launch", "sdf_plan_info", "sdf_plan_free"]
+           "sdf_plan_launch", "sdf_plan_info", "sdf_plan_free", "sdf_train_shape_info", "sdf_train_forward",
+           "sdf_train_backward", "sdf_fit_loss", "sdf_adam_step"]
 
 
 class SdfError(RuntimeError):
@@ -75,6 +76,13 @@ def lib():
         L.sdf_plan_free.argtypes = [vp]
         L.sdf_plan_free.restype = None
         L.sdf_render_host.argtypes = [C.POINTER(TraceParamsC), vp, vp, vp, C.c_int64, vp, vp, vp, vp]
+        i64p = C.POINTER(C.c_int64)
+        L.sdf_train_shape_info.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, i64p, i64p]
+        L.sdf_train_forward.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_int64, vp, vp, vp, vp]
+        L.sdf_train_backward.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_int64, vp, vp, vp, vp, vp]
+        L.sdf_fit_loss.argtypes = [vp, vp, vp, vp, vp, C.c_int64, C.c_float, C.c_float, vp, vp, vp, vp]
+        L.sdf_adam_step.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int,
+                                    vp]
         L.sdf_sync_status.argtypes = [vp]
         L.sdf_last_error.restype = C.c_char_p
         _lib = L
@@ -273,3 +281,110 @@ def render_host(nets, delta, max_iters, eps, fine: Net, orig, dirs, out_pos, out
 def sync_status(stream=None):
     """Synchronises the stream and raises on a device-side error (SDF_ERR_TIMEOUT)."""
     _check(lib().sdf_sync_status(C.c_void_p(_stream(stream))))
+
+
+# ---------------------------------------------------------------------------
+# training
+# ---------------------------------------------------------------------------
+
+def train_shape_info(in_dim: int, width: int, n_hidden: int, n: int = 0):
+    """(length of theta, workspace bytes for n points)."""
+    pc, wb = C.c_int64(), C.c_int64()
+    _check(lib().sdf_train_shape_info(in_dim, width, n_hidden, n, C.byref(pc), C.byref(wb)))
+    return pc.value, wb.value
+
+
+def theta_from_sdfn(data: bytes):
+    """(shape, theta) of an SDFN image: the folded parameters as a float32 numpy vector."""
+    import numpy as np
+    hdr = np.frombuffer(data[:32], dtype="<u4")
+    in_dim, width, n_hidden, flags = int(hdr[2]), int(hdr[3]), int(hdr[4]), int(hdr[7])
+    omega0, omega = np.frombuffer(data[20:28], dtype="<f4")
+    theta = np.frombuffer(data[32:], dtype="<f4").astype(np.float64)
+    if not flags & 1:
+        n0 = width * in_dim + width
+        theta[:n0] *= omega0
+        per = width * width + width
+        theta[n0:n0 + n_hidden * per] *= omega
+    return (in_dim, width, n_hidden), theta.astype(np.float32)
+
+
+def sdfn_from_theta(shape, theta) -> bytes:
+    """SDFN image (folded, flags bit 0) of a parameter vector."""
+    import numpy as np
+    in_dim, width, n_hidden = shape
+    hdr = np.array([0, 1, in_dim, width, n_hidden, 0, 0, 1], dtype="<u4")
+    hdr[5:7] = np.array([1.0, 1.0], dtype="<f4").view("<u4")
+    return b"SDFN" + hdr[1:].tobytes() + np.asarray(theta, dtype="<f4").tobytes()
+
+
+def train_forward(shape, theta, pts, pt_time=None, workspace=None, stream=None):
+    """f (n) and grad f (3, n) at device points (3, n); returns (f, grad, workspace)."""
+    in_dim, width, n_hidden = shape
+    n = pts.shape[1]
+    _, wb = train_shape_info(in_dim, width, n_hidden, n)
+    if workspace is None:
+        workspace = torch.empty(wb, dtype=torch.uint8, device=pts.device)
+    f = torch.empty(n, dtype=torch.float32, device=pts.device)
+    g = torch.empty((3, n), dtype=torch.float32, device=pts.device)
+    _check(lib().sdf_train_forward(in_dim, width, n_hidden, _ptr(theta), _ptr(pts), _ptr(pt_time), n, _ptr(f),
+                                   _ptr(g), _ptr(workspace), C.c_void_p(_stream(stream))))
+    return f, g, workspace
+
+
+def train_backward(shape, theta, pts, d_f, d_grad, workspace, d_theta=None, pt_time=None, stream=None):
+    """Adds dL/dtheta to d_theta (allocated zero if None) and returns it."""
+    in_dim, width, n_hidden = shape
+    n = pts.shape[1]
+    if d_theta is None:
+        d_theta = torch.zeros_like(theta)
+    _check(lib().sdf_train_backward(in_dim, width, n_hidden, _ptr(theta), _ptr(pts), _ptr(pt_time), n, _ptr(d_f),
+                                    _ptr(d_grad), _ptr(workspace), _ptr(d_theta), C.c_void_p(_stream(stream))))
+    return d_theta
+
+
+def fit_loss(f, grad, target_f, target_grad, near, lam_n: float, lam_e: float, stream=None):
+    """(d_f, d_grad, loss) of the fitting objective; loss = device float64 (l_val, l_dir, l_eik, L)."""
+    n = f.shape[0]
+    d_f = torch.empty_like(f)
+    d_g = torch.empty_like(grad)
+    loss = torch.zeros(4, dtype=torch.float64, device=f.device)
+    _check(lib().sdf_fit_loss(_ptr(f), _ptr(grad), _ptr(target_f), _ptr(target_grad), _ptr(near), n, float(lam_n),
+                              float(lam_e), _ptr(d_f), _ptr(d_g), _ptr(loss), C.c_void_p(_stream(stream))))
+    return d_f, d_g, loss
+
+
+def adam_step(theta, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().sdf_adam_step(_ptr(theta), _ptr(grad), _ptr(m), _ptr(v), theta.numel(), float(lr), float(beta1),
+                               float(beta2), float(eps), int(step), C.c_void_p(_stream(stream))))
+
+
+class SineMLP(torch.autograd.Function):
+    """(f, grad f) = SineMLP.apply(theta, pts, shape[, pt_time]) through the library's
+    training kernels; backward gives dL/dtheta (the points get no gradient)."""
+
+    @staticmethod
+    def forward(ctx, theta, pts, shape, pt_time=None):
+        f, g, ws = train_forward(shape, theta.detach(), pts, pt_time)
+        ctx.save_for_backward(theta.detach(), pts, ws)
+        ctx.shape, ctx.pt_time = shape, pt_time
+        return f, g
+
+    @staticmethod
+    def backward(ctx, d_f, d_grad):
+        theta, pts, ws = ctx.saved_tensors
+        d_f = torch.zeros(pts.shape[1], device=pts.device) if d_f is None else d_f.contiguous()
+        d_grad = torch.zeros_like(pts) if d_grad is None else d_grad.contiguous()
+        d_theta = train_backward(ctx.shape, theta, pts, d_f, d_grad, ws, pt_time=ctx.pt_time)
+        return d_theta, None, None, None
+
+
+def fit_step(shape, theta, m, v, step, pts, target_f, target_grad, near, *, lam_n=0.1, lam_e=0.05, lr=1e-4,
+             workspace=None, stream=None):
+    """One native fitting step: forward, objective, backward, Adam.  Returns (loss, workspace);
+    loss is the device float64 vector (l_val, l_dir, l_eik, L) before the update."""
+    f, g, workspace = train_forward(shape, theta, pts, workspace=workspace, stream=stream)
+    d_f, d_g, loss = fit_loss(f, g, target_f, target_grad, near, lam_n, lam_e, stream=stream)
+    d_theta = train_backward(shape, theta, pts, d_f, d_g, workspace, stream=stream)
+    adam_step(theta, d_theta, m, v, step, lr, stream=stream)
+    return loss, workspace

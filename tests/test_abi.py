@@ -81,3 +81,36 @@ def test_null_arguments_are_rejected(lib):
     assert lib.sdf_plan_info(None, None, 0, None) == -1
     lib.sdf_plan_free.argtypes = [C.c_void_p]
     lib.sdf_plan_free(None)
+
+
+def test_training_shapes_and_null_arguments(lib):
+    from paper_2201_09147_gb300 import sdfnn
+    for in_dim, w, k in ((3, 64, 1), (4, 128, 2), (3, 256, 3)):
+        count, ws = sdfnn.train_shape_info(in_dim, w, k, 1000)
+        assert count == inputs.param_count(in_dim, w, k)
+        # transposed weights, A_0, and two (k, n, 4, w) float blocks
+        assert ws >= 4 * (k * w * w + 1000 * w + 2 * k * 1000 * 4 * w)
+    with pytest.raises(sdfnn.SdfError) as e:
+        sdfnn.train_shape_info(3, 96, 1)
+    assert e.value.code == -7
+    lib.sdf_train_forward.argtypes = [C.c_int] * 3 + [C.c_void_p] * 3 + [C.c_int64] + [C.c_void_p] * 4
+    assert lib.sdf_train_forward(3, 64, 1, None, None, None, 0, None, None, None, None) == -1
+    lib.sdf_adam_step.argtypes = [C.c_void_p] * 4 + [C.c_int64] + [C.c_float] * 4 + [C.c_int, C.c_void_p]
+    assert lib.sdf_adam_step(None, None, None, None, 10, 1e-3, 0.9, 0.999, 1e-8, 0, None) == -1  # step from 1
+
+
+def test_theta_roundtrip_through_sdfn():
+    """The folded parameter vector and its SDFN image describe the same network."""
+    import numpy as np
+    import oracle
+    from paper_2201_09147_gb300 import sdfnn
+    net = inputs.siren_init(9, 64, 2)
+    b = inputs.net_to_bytes(net)
+    shape, theta = sdfnn.theta_from_sdfn(b)
+    assert shape == (3, 64, 2) and theta.size == inputs.param_count(3, 64, 2)
+    b2 = sdfnn.sdfn_from_theta(shape, theta)
+    assert sdfnn.theta_from_sdfn(b2)[1].tobytes() == theta.tobytes()
+    pts = inputs.random_points(2, 50).astype(np.float64)
+    g1, v1 = oracle.Net(b).grad_batch(pts, with_value=True)
+    g2, v2 = oracle.Net(b2).grad_batch(pts, with_value=True)
+    assert np.allclose(v1, v2, rtol=1e-5, atol=1e-5) and np.allclose(g1, g2, rtol=1e-4, atol=1e-3)

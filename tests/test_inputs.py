@@ -73,3 +73,18 @@ def test_workloads_resolve():
         assert len(w.level_bytes()) == len(w.delta) == len(w.caps)
         w.fine_bytes()
     assert workloads.get("normal_map_1080p").n_rays == 2073600
+
+
+def test_scene_gradient_and_fit_batch():
+    """The analytic scene gradient is the derivative of g (central differences); the fit
+    batch is half near-surface, half uniform, with targets equal to g there."""
+    sc = inputs.sphere_scene(1)
+    p, tf, tg, near = inputs.fit_batch(sc, 0, 2000)
+    assert p.shape == (3, 2000) and near.sum() == 1000 and p.dtype == np.float32
+    P = p.T.astype(np.float64)[::97]
+    v, g = sc.value_and_grad(P)
+    h = 1e-6
+    fd = np.stack([(sc.g(P + h * np.eye(3)[c]) - sc.g(P - h * np.eye(3)[c])) / (2 * h) for c in range(3)], axis=1)
+    assert np.abs(fd - g).max() < 1e-6
+    assert np.array_equal(v, sc.g(P))
+    assert np.abs(tf[:1000]).mean() < 0.05 < np.abs(tf[1000:]).mean()
