@@ -468,6 +468,34 @@ def main():
             del frames, oa, da, ta
         sdfnn.sync_status()
 
+        # native fitting step of a (256,3) network on 2^20 points (forward with tangents,
+        # objective, backward, Adam; FP32 SIMT kernels)
+        from paper_2201_09147_gb300 import inputs as _inputs
+        shape, theta_h = sdfnn.theta_from_sdfn(wl.fine_bytes())
+        th = torch.from_numpy(theta_h).cuda()
+        m_ = torch.zeros_like(th)
+        v_ = torch.zeros_like(th)
+        fp, ftf, ftg, fnear = (torch.from_numpy(x).cuda()
+                               for x in _inputs.fit_batch(_inputs.sphere_scene(1), 0, 1 << 20))
+        ws_ = None
+        loss_, ws_ = sdfnn.fit_step(shape, th, m_, v_, 1, fp, ftf, ftg, fnear, lr=1e-5, workspace=ws_)
+        torch.cuda.synchronize()
+        fit_ms = []
+        for k in range(2, 5):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            loss_, ws_ = sdfnn.fit_step(shape, th, m_, v_, k, fp, ftf, ftg, fnear, lr=1e-5, workspace=ws_)
+            b.record(stream)
+            torch.cuda.synchronize()
+            fit_ms.append(a.elapsed_time(b))
+        result["comparisons"]["fit_step_256x3_2^20"] = {
+            "ms_per_step": statistics.median(fit_ms), "points_per_s": (1 << 20) / (statistics.median(fit_ms) / 1e3),
+            "objective": float(loss_[3].item()), "workspace_GB": ws_.numel() / 1e9,
+            "kernels": "FP32 SIMT: forward+tangents, objective, backward, weight-gradient GEMMs, Adam"}
+        del ws_, fp, ftf, ftg, fnear
+        sdfnn.sync_status()
+
     if rank == 0 and not args.no_cpu_baseline:
         # FP64 oracle on a bounded sample of the same frame: speed, and the error of this run
         rows = np.arange(0, wl.height, ORACLE_ROW_STRIDE)
