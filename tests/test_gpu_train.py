@@ -150,19 +150,60 @@ def test_adam_matches_oracle(sdf):
     assert np.allclose(th.cpu().numpy(), rt, rtol=0, atol=2e-6)
 
 
-def test_native_fit_reduces_the_objective(sdf):
-    """200 native steps (forward, objective, backward, Adam) on a fresh SIREN (64,1)."""
+def _torch_objective(theta, pts, shape, tf, tg, near):
+    """The same network and objective written with torch autograd (FP32 reference)."""
+    in_dim, W, k = shape
+    o = 0
+    x = pts.T.clone().requires_grad_(True)
+    w0 = theta[o:o + W * in_dim].view(W, in_dim)
+    o += W * in_dim
+    b0 = theta[o:o + W]
+    o += W
+    h = torch.sin(x @ w0.T + b0)
+    for _ in range(k):
+        wl = theta[o:o + W * W].view(W, W)
+        o += W * W
+        bl = theta[o:o + W]
+        o += W
+        h = torch.sin(h @ wl.T + bl)
+    f = h @ theta[o:o + W] + theta[o + W]
+    (g,) = torch.autograd.grad(f.sum(), x, create_graph=True)
+    nrm = g.norm(dim=1)
+    nb = tg.T.norm(dim=1)
+    cos = (g * tg.T).sum(dim=1) / (nrm * nb)
+    nf = near.bool()
+    return ((f - tf).abs().mean() + LAM_N * (1.0 - cos[nf]).mean() + LAM_E * (nrm - 1.0).abs().mean())
+
+
+def test_native_fit_matches_torch_reference(sdf):
+    """Native steps (forward, objective, backward, Adam) against the same objective and
+    torch.optim.Adam through torch autograd, from one SIREN (64,1) initialisation."""
     shape, theta = sdf.theta_from_sdfn(inputs.net_to_bytes(inputs.siren_init(0, 64, 1)))
     th = _dev(theta)
     m, v = torch.zeros_like(th), torch.zeros_like(th)
-    pts, tf, tg, near = (_dev(x) for x in _loss_inputs(1 << 14, seed=9))
-    ws = None
-    first = None
-    for step in range(1, 201):
+    pts, tf, tg, near = (_dev(x) for x in _loss_inputs(1 << 13, seed=9))
+    ref = _dev(theta).requires_grad_(True)
+    opt = torch.optim.Adam([ref], lr=1e-4)
+    # the first gradient itself
+    f, g, ws = sdf.train_forward(shape, th, pts)
+    d_f, d_g, _ = sdf.fit_loss(f, g, tf, tg, near, LAM_N, LAM_E)
+    d0 = sdf.train_backward(shape, th, pts, d_f, d_g, ws)
+    _torch_objective(ref, pts, shape, tf, tg, near).backward()
+    rel = (d0 - ref.grad).norm() / ref.grad.norm()
+    print("first gradient rel diff", rel.item())
+    assert rel.item() <= 1e-4
+    opt.zero_grad()
+    objs = []
+    for step in range(1, 101):
         loss, ws = sdf.fit_step(shape, th, m, v, step, pts, tf, tg, near, lr=1e-4, workspace=ws)
-        if step == 1:
-            first = loss.cpu().numpy()[3]
-    last = loss.cpu().numpy()[3]
+        opt.zero_grad()
+        lt = _torch_objective(ref, pts, shape, tf, tg, near)
+        lt.backward()
+        opt.step()
+        objs.append((loss[3].item(), lt.item()))
     sdf.sync_status()
-    print("objective", first, "->", last)
-    assert np.isfinite(last) and last < 0.5 * first
+    objs = np.array(objs)
+    print("objective native / torch", objs[0], objs[-1])
+    assert np.all(np.abs(objs[:, 0] - objs[:, 1]) <= 2e-3 * objs[:, 1])
+    assert objs[-1, 0] < 0.8 * objs[0, 0]
+    assert (th - ref.detach()).abs().max().item() <= 1e-3 * ref.detach().abs().max().item()
