@@ -108,6 +108,19 @@ def dist_info():
     return ws, rank, local
 
 
+def job_throughput(local_total_ms: float, units_per_rank: int, steps: int, ws: int, device="cpu"):
+    """Whole-job throughput in millions of units per second: the units of all ranks over the
+    slowest rank's timed region (max over ranks); returns (value, max_ms)."""
+    t = float(local_total_ms)
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        x = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return ws * units_per_rank * steps / (t / 1e3) / 1e6, t
+
+
 def oracle_sample(wl, rows):
     """Runs the FP64 oracle on the given image rows: trace + normal map at its hits."""
     import oracle
@@ -238,12 +251,7 @@ def main():
     step_ms = [a.elapsed_time(c) for a, _, c in evs]
     trace_ms = [a.elapsed_time(b) for a, b, _ in evs]
     nmap_ms = [b.elapsed_time(c) for _, b, c in evs]
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * n * args.steps / (total_ms / 1e3) / 1e6
+    value, total_ms = job_throughput(sum(step_ms), n, args.steps, ws, "cuda")
     n_hit = int(hit.sum().item())
 
     # roofline of the dominant kernel (algorithmic work / event-timed duration)
