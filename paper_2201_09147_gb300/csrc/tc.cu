@@ -586,17 +586,26 @@ struct GradCfg {
     static constexpr int HPTS = 32;                 // points per half
     static constexpr int NROWS = 4 * NPTS;          // rows of X (point-streams)
     static constexpr int HROWS = 4 * HPTS;          // rows of X per half = MMA N
-    // weight ring stages (one K block of one TMEM tile each)
-    static constexpr int NS = (OP != kOpE4M3 && W == 256) ? 5 : 8;
+    // Weight ring.  A stage is SKB consecutive K blocks for all TMEM tiles: one
+    // contiguous 32 KB bulk copy where the layer allows it (bulk-copy throughput
+    // per SM grows with the copy size: ~20 B/clk with 16 KB copies, ~41 with
+    // 32 KB, measured with a copy ring on GB300).  NS fills what the activation
+    // tile leaves of the shared memory.
+    static constexpr int SKB = (MT * 16384 >= 32768 || KB == 1) ? 1 : 2;
+    static constexpr uint32_t STAGE_BYTES = static_cast<uint32_t>(SKB) * MT * 16384u;
+    static constexpr int STAGES_PER_LAYER = KB / SKB;
+    static constexpr uint32_t X_BYTES = 4u * 64u * 128u * KB;
+    static constexpr int NS_FIT = static_cast<int>((200u * 1024u - X_BYTES) / STAGE_BYTES);
+    static constexpr int NS = NS_FIT > 8 ? 8 : NS_FIT;
     static constexpr int GROUP_WARPS = 4 * MT;      // epilogue warps per half
     static constexpr int GROUP_THREADS = GROUP_WARPS * 32;
     static constexpr int EPI_WARPS = 2 * GROUP_WARPS;
     static constexpr int PRODUCER_WARP = EPI_WARPS;
     static constexpr int MMA_WARP = EPI_WARPS + 1;
     static constexpr int THREADS = (EPI_WARPS + 2) * 32;
-    static constexpr uint32_t STAGE_BYTES = 128u * 128u;  // 128 feature rows x one K block
     static constexpr int TMEM_COLS = MT * 256;      // per TMEM tile: half 0 at +0, half 1 at +128
     static_assert(KB >= 1, "E4M3 gradients need width >= 128");
+    static_assert(NS >= 2 && KB % SKB == 0, "weight ring");
 };
 
 struct GradLayout {
@@ -764,8 +773,9 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
 
     if (warp == C::PRODUCER_WARP) {
         if (lane == 0) {
-            // stages in MMA order: per pair, per layer, per half, K block, TMEM tile
-            const int per_layer = 2 * C::KB * C::MT;
+            // stages in MMA order: per pair, per layer, per half, stage of the layer
+            // (K blocks SKB * sg .. of every TMEM tile: contiguous in the weight image)
+            const int per_layer = 2 * C::STAGES_PER_LAYER;
             const long long total = my_pairs * KH * per_layer;
             uint32_t g = 0;
             for (long long st = 0; st < total && ok; ++st, ++g) {
@@ -773,12 +783,11 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
                 if (use > 0) ok = mbar_wait_bounded(bar_empty + 8u * stage, (use - 1) & 1u, a.status, abort_flag);
                 if (!ok) break;
                 const int sl = static_cast<int>(st % (KH * per_layer));
-                const int l = sl / per_layer, r = sl % (C::KB * C::MT);
-                const int kb = r / C::MT, mt = r % C::MT;
+                const int l = sl / per_layer, sg = sl % C::STAGES_PER_LAYER;
                 mbar_arrive_expect_tx(bar_full + 8u * stage, C::STAGE_BYTES);
                 bulk_g2s(ring_s + stage * C::STAGE_BYTES,
                          net.wbf + static_cast<size_t>(l) * net.wbf_layer_bytes +
-                             static_cast<size_t>(kb) * net.rows_pad * 128u + static_cast<size_t>(mt) * 128u * 128u,
+                             static_cast<size_t>(sg) * C::STAGE_BYTES,
                          C::STAGE_BYTES, bar_full + 8u * stage);
             }
         }
@@ -799,23 +808,28 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
                         const uint32_t xh = FP8 ? x_s + h * C::HROWS * 128u : x_s + h * (W * 256u);
                         if (l < KH) {
                             // D[mt][h] = W_l[mt rows] . X_h^T over all K blocks
-                            for (int kb = 0; kb < C::KB && ok; ++kb) {
-                                for (int mt = 0; mt < C::MT && ok; ++mt, ++g) {
-                                    const uint32_t stage = g % C::NS, use = g / C::NS;
-                                    ok = mbar_wait_bounded(bar_full + 8u * stage, use & 1u, a.status, abort_flag);
-                                    if (!ok) break;
-                                    tc_fence_after();
+                            for (int sg = 0; sg < C::STAGES_PER_LAYER && ok; ++sg, ++g) {
+                                const uint32_t stage = g % C::NS, use = g / C::NS;
+                                ok = mbar_wait_bounded(bar_full + 8u * stage, use & 1u, a.status, abort_flag);
+                                if (!ok) break;
+                                tc_fence_after();
 #pragma unroll
-                                    for (int kk = 0; kk < 4; ++kk) {
-                                        const uint64_t xd =
-                                            FP8 ? desc_kmajor_sw128(xh + kb * C::NROWS * 128u + kk * 32u)
-                                                : desc_mnmajor_sw128(xh + (kb * 8 + kk * 2) * 1024u, W * 128u);
-                                        mma_op<OP>(tmem + mt * 256u + h * 128u,
-                                                   desc_kmajor_sw128(ring_s + stage * C::STAGE_BYTES + kk * 32u), xd,
-                                                   idesc_h, (kb | kk) != 0);
-                                    }
-                                    mma_commit(bar_empty + 8u * stage);
+                                for (int kr = 0; kr < C::SKB; ++kr) {
+                                    const int kb = sg * C::SKB + kr;
+#pragma unroll
+                                    for (int mt = 0; mt < C::MT; ++mt)
+#pragma unroll
+                                        for (int kk = 0; kk < 4; ++kk) {
+                                            const uint64_t xd =
+                                                FP8 ? desc_kmajor_sw128(xh + kb * C::NROWS * 128u + kk * 32u)
+                                                    : desc_mnmajor_sw128(xh + (kb * 8 + kk * 2) * 1024u, W * 128u);
+                                            const uint32_t wa =
+                                                ring_s + stage * C::STAGE_BYTES + (kr * C::MT + mt) * 16384u + kk * 32u;
+                                            mma_op<OP>(tmem + mt * 256u + h * 128u, desc_kmajor_sw128(wa), xd, idesc_h,
+                                                       (kb | kk) != 0);
+                                        }
                                 }
+                                mma_commit(bar_empty + 8u * stage);
                             }
                         } else {
                             // output layer of this half: rows = its 128 point-streams, N = 16 (w_out head, remainder)
