@@ -220,19 +220,21 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
 
     while (ok) {
         refill_ray(a, ray, n_work);
-        if (!bar_or(bar_id, 128, ray.state == kSlotActive)) break;
         if (a.cap <= 0) {
+            if (!bar_or(bar_id, 128, ray.state == kSlotActive)) break;
             pass_ray(a, ray);
             continue;
         }
-        // layer 0 (FP32): row ttid of X = 16-bit sin(W_0 (p, t) + b_0)
+        // layer 0 (FP32): row ttid of X = 16-bit sin(W_0 (p, t) + b_0); an empty
+        // slot writes a row from its stale (finite) state, which nothing reads
         if (timed)
             trace_layer0<W, F16, SPLIT, true>(a, w0s, wts, ray, ttid, x_s, xlo_s);
         else
             trace_layer0<W, F16, SPLIT, false>(a, w0s, wts, ray, ttid, x_s, xlo_s);
         fence_proxy_async_smem();
         tc_fence_before();
-        bar_named(bar_id, 128);
+        // one barrier: X is complete, and the tile stops when no slot is active
+        if (!bar_or(bar_id, 128, ray.state == kSlotActive)) break;
 
         float f = 0.0f;
         for (int l = 0; l < KH; ++l) {
@@ -452,8 +454,8 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
         Ray ray;
         while (ok) {
             refill_ray(a, ray, n_work);
-            if (!bar_or(1, 128, ray.state == kSlotActive)) break;
             if (a.cap <= 0) {
+                if (!bar_or(1, 128, ray.state == kSlotActive)) break;
                 pass_ray(a, ray);
                 continue;
             }
@@ -463,7 +465,7 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
                 trace_layer0<W, F16, false, false>(a, w0s, wts, ray, tid, x_s, x_s);
             fence_proxy_async_smem();
             tc_fence_before();
-            bar_named(1, 128);
+            if (!bar_or(1, 128, ray.state == kSlotActive)) break;
 
             float f = 0.0f;
             for (int l = 0; l < KH; ++l) {
