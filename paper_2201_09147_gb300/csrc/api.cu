@@ -856,6 +856,40 @@ int plan_create(const sdf_trace_params* P, sdf_net_t fine, const sdf_frame_batch
 
 }  // namespace
 
+namespace {
+
+// Streams and events of sdf_render_host on one device (created on first use,
+// kept until exit); calls on one device take the mutex for their duration.
+constexpr int kHostChunks = 4;
+struct HostPipe {
+    std::mutex m;
+    bool ready = false;
+    cudaStream_t in = nullptr, cmp = nullptr, out = nullptr;
+    cudaEvent_t start = nullptr, done = nullptr, ev_in[kHostChunks] = {}, ev_cmp[kHostChunks] = {};
+};
+HostPipe g_host_pipes[64];
+
+int host_pipe_init(HostPipe* hp) {
+    if (hp->ready) return SDF_OK;
+    cudaError_t e = cudaSuccess;
+    for (cudaStream_t* st : {&hp->in, &hp->cmp, &hp->out})
+        if (e == cudaSuccess && !*st) e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
+    auto mk = [&](cudaEvent_t* ev) {
+        if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    };
+    mk(&hp->start);
+    mk(&hp->done);
+    for (int c = 0; c < kHostChunks; ++c) {
+        mk(&hp->ev_in[c]);
+        mk(&hp->ev_cmp[c]);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "creating the host-frame streams");
+    hp->ready = true;
+    return SDF_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int sdf_net_load_mem(const void* bytes, size_t n_bytes, int precision, int device, sdf_net_t* out) {
@@ -924,38 +958,75 @@ int sdf_render_host(const sdf_trace_params* params, sdf_net_t fine, const float*
     if (!fine) return fail(SDF_ERR_ARG, "fine is NULL");
     if (!orig || !dir || !out_pos || !out_hit || !out_normal) return fail(SDF_ERR_ARG, "NULL host buffer");
     if (n < 0 || n > 0x7fffffffLL) return fail(SDF_ERR_ARG, "n out of range");
+    if (params->ray_time) return fail(SDF_ERR_ARG, "sdf_render_host takes no per-ray times");
     if (n == 0) return SDF_OK;
     const int dev = params->nets[0]->device;
     if (fine->device != dev) return fail(SDF_ERR_ARG, "fine network on another device");
+    if (dev < 0 || dev >= 64) return fail(SDF_ERR_ARG, "device %d out of range", dev);
     DeviceGuard g(dev);
     if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", dev);
+    HostPipe& hp = g_host_pipes[dev];
+    std::lock_guard<std::mutex> lock(hp.m);
+    int rc = host_pipe_init(&hp);
+    if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    const size_t v3 = 3 * static_cast<size_t>(n) * sizeof(float), v1 = static_cast<size_t>(n) * sizeof(float);
-    // device buffers: orig, dir, pos, normal (3n floats each), t (n floats), hit (n bytes)
-    const size_t bytes = 4 * v3 + v1 + static_cast<size_t>(n) + 1024;
-    Scratch sc;
-    sc.s = s;
-    cudaError_t e = cudaMallocAsync(&sc.ptr, bytes, s);
+
+    // chunks of rays: the copies of one chunk overlap the kernels of another
+    const int nch = n >= (int64_t(1) << 20) ? kHostChunks : (n >= (int64_t(1) << 18) ? 2 : 1);
+    const int64_t m = (n + nch - 1) / nch;
+    const size_t cm = static_cast<size_t>(m);
+    // per chunk: orig, dir, pos, normal (3m floats each), t (m floats), hit (m bytes)
+    const size_t chunk_bytes = (13 * cm * sizeof(float) + cm + 255) & ~size_t(255);
+    void* block = nullptr;
+    cudaError_t e = cudaMallocAsync(&block, chunk_bytes * nch, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(frame)");
-    uint8_t* b = static_cast<uint8_t*>(sc.ptr);
-    float* d_orig = reinterpret_cast<float*>(b);
-    float* d_dir = reinterpret_cast<float*>(b + v3);
-    float* d_pos = reinterpret_cast<float*>(b + 2 * v3);
-    float* d_nrm = reinterpret_cast<float*>(b + 3 * v3);
-    float* d_t = reinterpret_cast<float*>(b + 4 * v3);
-    uint8_t* d_hit = b + 4 * v3 + v1;
-    if ((e = cudaMemcpyAsync(d_orig, orig, v3, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(d_dir, dir, v3, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return cuda_fail(e, "copying rays to the device");
-    int rc = trace_impl(params, d_orig, d_dir, n, d_pos, d_t, d_hit, nullptr, s);
+    e = cudaEventRecord(hp.start, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.in, hp.start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.cmp, hp.start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.out, hp.start, 0);
+    for (int c = 0; c < nch && e == cudaSuccess && rc == SDF_OK; ++c) {
+        const int64_t lo = c * m, mc = std::min<int64_t>(m, n - lo);
+        if (mc <= 0) break;
+        const size_t w = static_cast<size_t>(mc) * sizeof(float), hpitch = static_cast<size_t>(n) * sizeof(float);
+        uint8_t* b = static_cast<uint8_t*>(block) + c * chunk_bytes;
+        float* d_orig = reinterpret_cast<float*>(b);
+        float* d_dir = d_orig + 3 * mc;
+        float* d_pos = d_dir + 3 * mc;
+        float* d_nrm = d_pos + 3 * mc;
+        float* d_t = d_nrm + 3 * mc;
+        uint8_t* d_hit = reinterpret_cast<uint8_t*>(d_t + mc);
+        // rays in (3 rows of mc floats out of the host's (3, n) arrays)
+        if ((e = cudaMemcpy2DAsync(d_orig, w, orig + lo, hpitch, w, 3, cudaMemcpyHostToDevice, hp.in)) != cudaSuccess ||
+            (e = cudaMemcpy2DAsync(d_dir, w, dir + lo, hpitch, w, 3, cudaMemcpyHostToDevice, hp.in)) != cudaSuccess ||
+            (e = cudaEventRecord(hp.ev_in[c], hp.in)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(hp.cmp, hp.ev_in[c], 0)) != cudaSuccess)
+            break;
+        rc = trace_impl(params, d_orig, d_dir, mc, d_pos, d_t, d_hit, nullptr, hp.cmp);
+        if (rc == SDF_OK) rc = grad_impl(fine, d_pos, nullptr, d_hit, mc, d_nrm, 1, hp.cmp);
+        if (rc) break;
+        if ((e = cudaEventRecord(hp.ev_cmp[c], hp.cmp)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(hp.out, hp.ev_cmp[c], 0)) != cudaSuccess ||
+            (e = cudaMemcpy2DAsync(out_pos + lo, hpitch, d_pos, w, w, 3, cudaMemcpyDeviceToHost, hp.out)) != cudaSuccess ||
+            (e = cudaMemcpy2DAsync(out_normal + lo, hpitch, d_nrm, w, w, 3, cudaMemcpyDeviceToHost, hp.out)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(out_hit + lo, d_hit, static_cast<size_t>(mc), cudaMemcpyDeviceToHost, hp.out)) !=
+                cudaSuccess)
+            break;
+    }
+    // the caller's stream waits for everything, frees the frame and returns with the results on the host
+    cudaError_t e2 = cudaEventRecord(hp.done, hp.out);
+    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, hp.done, 0);
+    if (e2 != cudaSuccess) {
+        cudaStreamSynchronize(hp.in);
+        cudaStreamSynchronize(hp.cmp);
+        cudaStreamSynchronize(hp.out);
+    }
+    cudaFreeAsync(block, s);
+    const cudaError_t e3 = cudaStreamSynchronize(s);
     if (rc) return rc;
-    rc = grad_impl(fine, d_pos, nullptr, d_hit, n, d_nrm, 1, s);
-    if (rc) return rc;
-    if ((e = cudaMemcpyAsync(out_pos, d_pos, v3, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(out_normal, d_nrm, v3, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(out_hit, d_hit, static_cast<size_t>(n), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-        return cuda_fail(e, "copying results to the host");
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (e != cudaSuccess) return cuda_fail(e, "enqueueing the frame");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "ordering the frame's streams");
+    if (e3 != cudaSuccess) return cuda_fail(e3, "cudaStreamSynchronize");
     return SDF_OK;
 }
 

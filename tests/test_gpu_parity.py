@@ -357,15 +357,17 @@ def test_edge_cases(sdf):
     sdf.sync_status()
 
 
-def test_render_host_matches_device(sdf):
-    wl = workloads.get("normal_map_1080p", 160, 90)
+@pytest.mark.parametrize("size", [(160, 90), (640, 480), (1920, 1080)], ids=["1chunk", "2chunks", "4chunks"])
+def test_render_host_matches_device(sdf, size):
+    """The host-buffer frame (chunked, copies overlapping the kernels) equals the device calls bit for bit."""
+    wl = workloads.get("normal_map_1080p", *size)
     orig, dirs = wl.rays()
     nets = [sdf.Net(b, sdf.SDF_BF16) for b in wl.level_bytes()]
     fine = sdf.Net(wl.fine_bytes(), sdf.SDF_BF16)
     n = orig.shape[1]
-    hp = torch.empty((3, n)).pin_memory()
-    hh = torch.empty(n, dtype=torch.uint8).pin_memory()
-    hn = torch.empty((3, n)).pin_memory()
+    hp = torch.full((3, n), float("nan")).pin_memory()
+    hh = torch.full((n,), 7, dtype=torch.uint8).pin_memory()
+    hn = torch.full((3, n), float("nan")).pin_memory()
     sdf.render_host(nets, wl.delta, wl.caps, wl.eps, fine, torch.from_numpy(orig).pin_memory(),
                     torch.from_numpy(dirs).pin_memory(), hp, hh, hn, step_scale=wl.step_scale,
                     final_mode=wl.final_mode)
