@@ -21,6 +21,10 @@
  *     SDF_ERR_TIMEOUT) are latched in a per-device status word and returned
  *     by sdf_sync_status.
  *   - n == 0 is valid and launches nothing.
+ *   - Per-call scratch (work counters, ray queues, compaction lists, the
+ *     host-frame buffers of sdf_render_host) comes from a stream-ordered
+ *     memory pool of the library on each device, which keeps the memory it
+ *     has reserved for later calls (up to the largest call's need).
  *   - Every non-OK return sets a thread-local message (sdf_last_error).
  *
  * Network files ("SDFN", little-endian):
@@ -165,8 +169,8 @@ int sdf_normal_map_timed(sdf_net_t fine, const float *pts, const float *pt_time,
  * split into 2 or 4 chunks whose copies in, kernels and copies out run on
  * three streams of the library, so the transfers of one chunk overlap the
  * kernels of another (use pinned host memory for the copies to overlap).
- * Device buffers are taken from the stream-ordered allocator on
- * `cuda_stream`, which waits for the whole frame.  orig, dir: host (3, n);
+ * Device buffers come from the library's pool on `cuda_stream`, which waits
+ * for the whole frame.  orig, dir: host (3, n);
  * out_pos, out_normal: host (3, n); out_hit: host (n).  params->ray_time must
  * be NULL.  Calls on one device are serialised.  Returns after the results
  * are in host memory (the stream is synchronised).

@@ -66,6 +66,7 @@ struct DeviceGuard {
 struct DeviceInfo {
     int num_sms = 0;
     int* d_status = nullptr;
+    cudaMemPool_t pool = nullptr;  // the library's stream-ordered pool for per-call scratch
 };
 
 std::mutex g_dev_mutex;
@@ -84,6 +85,19 @@ int device_info(int dev, DeviceInfo* out) {
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(status)");
         e = cudaMemset(d.d_status, 0, sizeof(int));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(status)");
+        // Per-call scratch comes from a pool of the library that keeps what it
+        // has reserved (a release threshold of 0, the default pool's, would
+        // return freed memory at every synchronisation and make the next
+        // allocation map it again).
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        e = cudaMemPoolCreate(&d.pool, &props);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolCreate");
+        uint64_t keep = ~uint64_t(0);
+        e = cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolSetAttribute");
     }
     *out = d;
     return SDF_OK;
@@ -557,8 +571,8 @@ int trace_impl(const sdf_trace_params* P, const float* orig, const float* dir, i
     if ((rc = device_info(dev, &di))) return rc;
     Scratch sc;
     sc.s = s;
-    cudaError_t e = cudaMallocAsync(&sc.ptr, trace_scratch_bytes(P->n_levels, n) + 256, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch)");
+    cudaError_t e = cudaMallocFromPoolAsync(&sc.ptr, trace_scratch_bytes(P->n_levels, n) + 256, di.pool, s);
+    if (e != cudaSuccess) return cuda_fail(e, "allocating scratch");
     return launch_levels(P, orig, dir, n, out_pos, out_t, out_hit, out_iters, sc.ptr, di.d_status, di.num_sms,
                          nullptr, s);
 }
@@ -625,8 +639,8 @@ int grad_impl(sdf_net_t net, const float* pts, const float* pt_time, const uint8
     if ((rc = device_info(net->device, &di))) return rc;
     Scratch sc;
     sc.s = s;
-    cudaError_t e = cudaMallocAsync(&sc.ptr, grad_scratch_bytes(n, mask != nullptr) + 256, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch)");
+    cudaError_t e = cudaMallocFromPoolAsync(&sc.ptr, grad_scratch_bytes(n, mask != nullptr) + 256, di.pool, s);
+    if (e != cudaSuccess) return cuda_fail(e, "allocating scratch");
     return launch_gradients(net, pts, pt_time, mask, n, out, normalize, sc.ptr, di.d_status, di.num_sms, s);
 }
 
@@ -977,9 +991,11 @@ int sdf_render_host(const sdf_trace_params* params, sdf_net_t fine, const float*
     const size_t cm = static_cast<size_t>(m);
     // per chunk: orig, dir, pos, normal (3m floats each), t (m floats), hit (m bytes)
     const size_t chunk_bytes = (13 * cm * sizeof(float) + cm + 255) & ~size_t(255);
+    DeviceInfo di;
+    if ((rc = device_info(dev, &di))) return rc;
     void* block = nullptr;
-    cudaError_t e = cudaMallocAsync(&block, chunk_bytes * nch, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(frame)");
+    cudaError_t e = cudaMallocFromPoolAsync(&block, chunk_bytes * nch, di.pool, s);
+    if (e != cudaSuccess) return cuda_fail(e, "allocating the frame buffers");
     e = cudaEventRecord(hp.start, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.in, hp.start, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.cmp, hp.start, 0);
@@ -1219,8 +1235,8 @@ int sdf_fit_loss(const float* f, const float* grad, const float* target_f, const
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     Scratch sc;
     sc.s = s;
-    cudaError_t e = cudaMallocAsync(&sc.ptr, 64, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(loss scratch)");
+    cudaError_t e = cudaMallocFromPoolAsync(&sc.ptr, 64, di.pool, s);
+    if (e != cudaSuccess) return cuda_fail(e, "allocating scratch");
     double* sums = static_cast<double*>(sc.ptr);
     auto* cnt = reinterpret_cast<unsigned long long*>(sums + 4);
     e = launch_fit_loss(f, grad, target_f, target_grad, near, n, lam_n, lam_e, d_f, d_grad, sums, cnt, loss, di.num_sms,

@@ -18,6 +18,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "launch_cache.h"
 #include "rays.cuh"
 #include "simt.cuh"
 
@@ -265,14 +266,17 @@ __global__ void mask_compact_kernel(const uint8_t* __restrict__ mask, int64_t n,
 
 template <class Kernel>
 cudaError_t launch_persistent(Kernel k, size_t smem, int num_sms, cudaStream_t s, const void* arg) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    // ask for the largest shared-memory carveout, so that the occupancy query
-    // (and the launch) can place as many CTAs per SM as shared memory allows
-    e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
+    // the attributes are set and the occupancy counted once per kernel and device
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kSimtThreads, smem);
+    cudaError_t e = launch_cached(reinterpret_cast<const void*>(k), smem, kSimtThreads, &per_sm, [&](int* v) {
+        cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        // the largest shared-memory carveout lets the occupancy query (and the launch)
+        // place as many CTAs per SM as shared memory allows
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(v, k, kSimtThreads, smem);
+        return r;
+    });
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     void* args[] = {const_cast<void*>(arg)};

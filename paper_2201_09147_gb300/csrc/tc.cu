@@ -29,6 +29,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "launch_cache.h"
 #include "rays.cuh"
 
 namespace sdfnn {
@@ -1049,12 +1050,19 @@ cudaError_t resident_ctas(Kernel k, int threads, size_t smem, int tmem_cols, int
 template <class Kernel>
 cudaError_t launch_tc(Kernel k, int threads, size_t smem, int tmem_cols, int num_sms, cudaStream_t s,
                       const void* arg) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    if ((e = resident_ctas(k, threads, smem, tmem_cols, &per_sm)) != cudaSuccess) return e;
+    cudaError_t e = launch_cached(reinterpret_cast<const void*>(k), smem,
+                                  (static_cast<uint64_t>(threads) << 32) | static_cast<uint32_t>(tmem_cols), &per_sm,
+                                  [&](int* v) {
+                                      cudaError_t r = cudaFuncSetAttribute(
+                                          k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+                                      if (r == cudaSuccess)
+                                          r = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                                   cudaSharedmemCarveoutMaxShared);
+                                      if (r == cudaSuccess) r = resident_ctas(k, threads, smem, tmem_cols, v);
+                                      return r;
+                                  });
+    if (e != cudaSuccess) return e;
     void* args[] = {const_cast<void*>(arg)};
     return cudaLaunchKernel(reinterpret_cast<const void*>(k), dim3(num_sms * per_sm), dim3(threads), args, smem, s);
 }
@@ -1072,7 +1080,7 @@ bool tc_grad_supported(int width, int n_hidden) {
 // Ray tiles per CTA for the resident trace kernel: as many as shared memory,
 // registers, TMEM and the thread limit allow (all tiles share the weights).
 template <class Kernel>
-static int trace_tiles(Kernel k, int W, int KH, bool split) {
+static int trace_tiles_uncached(Kernel k, int W, int KH, bool split) {
     int dev = 0, smem_optin = 0, regs_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -1084,6 +1092,18 @@ static int trace_tiles(Kernel k, int W, int KH, bool split) {
     while (T > 1 && (trace_layout(W, KH, split, T).total + 1024 > static_cast<uint32_t>(smem_optin) ||
                      regs_warp * 4 * T > regs_sm || static_cast<int>(tmem_cols_for(T * W)) > 512))
         --T;
+    return T;
+}
+
+template <class Kernel>
+static int trace_tiles(Kernel k, int W, int KH, bool split) {
+    int T = 1;
+    if (launch_cached(reinterpret_cast<const void*>(k), static_cast<uint64_t>(W) * 16 + KH, split ? 1 : 0, &T,
+                      [&](int* v) {
+                          *v = trace_tiles_uncached(k, W, KH, split);
+                          return cudaSuccess;
+                      }) != cudaSuccess)
+        return 1;
     return T;
 }
 
