@@ -878,7 +878,9 @@ constexpr int kHostChunks = 4;
 struct HostPipe {
     std::mutex m;
     bool ready = false;
-    cudaStream_t in = nullptr, cmp = nullptr, out = nullptr;
+    // copies in, two compute streams (consecutive chunks alternate, so one
+    // chunk's kernels fill the SMs its predecessor's tail leaves idle), copies out
+    cudaStream_t in = nullptr, cmp[2] = {}, out = nullptr;
     cudaEvent_t start = nullptr, done = nullptr, ev_in[kHostChunks] = {}, ev_cmp[kHostChunks] = {};
 };
 HostPipe g_host_pipes[64];
@@ -886,7 +888,7 @@ HostPipe g_host_pipes[64];
 int host_pipe_init(HostPipe* hp) {
     if (hp->ready) return SDF_OK;
     cudaError_t e = cudaSuccess;
-    for (cudaStream_t* st : {&hp->in, &hp->cmp, &hp->out})
+    for (cudaStream_t* st : {&hp->in, &hp->cmp[0], &hp->cmp[1], &hp->out})
         if (e == cudaSuccess && !*st) e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
     auto mk = [&](cudaEvent_t* ev) {
         if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
@@ -998,7 +1000,8 @@ int sdf_render_host(const sdf_trace_params* params, sdf_net_t fine, const float*
     if (e != cudaSuccess) return cuda_fail(e, "allocating the frame buffers");
     e = cudaEventRecord(hp.start, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.in, hp.start, 0);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.cmp, hp.start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.cmp[0], hp.start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.cmp[1], hp.start, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.out, hp.start, 0);
     for (int c = 0; c < nch && e == cudaSuccess && rc == SDF_OK; ++c) {
         const int64_t lo = c * m, mc = std::min<int64_t>(m, n - lo);
@@ -1015,12 +1018,12 @@ int sdf_render_host(const sdf_trace_params* params, sdf_net_t fine, const float*
         if ((e = cudaMemcpy2DAsync(d_orig, w, orig + lo, hpitch, w, 3, cudaMemcpyHostToDevice, hp.in)) != cudaSuccess ||
             (e = cudaMemcpy2DAsync(d_dir, w, dir + lo, hpitch, w, 3, cudaMemcpyHostToDevice, hp.in)) != cudaSuccess ||
             (e = cudaEventRecord(hp.ev_in[c], hp.in)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(hp.cmp, hp.ev_in[c], 0)) != cudaSuccess)
+            (e = cudaStreamWaitEvent(hp.cmp[c & 1], hp.ev_in[c], 0)) != cudaSuccess)
             break;
-        rc = trace_impl(params, d_orig, d_dir, mc, d_pos, d_t, d_hit, nullptr, hp.cmp);
-        if (rc == SDF_OK) rc = grad_impl(fine, d_pos, nullptr, d_hit, mc, d_nrm, 1, hp.cmp);
+        rc = trace_impl(params, d_orig, d_dir, mc, d_pos, d_t, d_hit, nullptr, hp.cmp[c & 1]);
+        if (rc == SDF_OK) rc = grad_impl(fine, d_pos, nullptr, d_hit, mc, d_nrm, 1, hp.cmp[c & 1]);
         if (rc) break;
-        if ((e = cudaEventRecord(hp.ev_cmp[c], hp.cmp)) != cudaSuccess ||
+        if ((e = cudaEventRecord(hp.ev_cmp[c], hp.cmp[c & 1])) != cudaSuccess ||
             (e = cudaStreamWaitEvent(hp.out, hp.ev_cmp[c], 0)) != cudaSuccess ||
             (e = cudaMemcpy2DAsync(out_pos + lo, hpitch, d_pos, w, w, 3, cudaMemcpyDeviceToHost, hp.out)) != cudaSuccess ||
             (e = cudaMemcpy2DAsync(out_normal + lo, hpitch, d_nrm, w, w, 3, cudaMemcpyDeviceToHost, hp.out)) !=
@@ -1034,7 +1037,8 @@ int sdf_render_host(const sdf_trace_params* params, sdf_net_t fine, const float*
     if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, hp.done, 0);
     if (e2 != cudaSuccess) {
         cudaStreamSynchronize(hp.in);
-        cudaStreamSynchronize(hp.cmp);
+        cudaStreamSynchronize(hp.cmp[0]);
+        cudaStreamSynchronize(hp.cmp[1]);
         cudaStreamSynchronize(hp.out);
     }
     cudaFreeAsync(block, s);
