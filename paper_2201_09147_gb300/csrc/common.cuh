@@ -116,6 +116,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// try_wait that may suspend the thread for up to `hint_ns` while the phase
+// is incomplete (the thread resumes when the phase completes): waiting
+// threads then stop competing for issue slots with working ones.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+constexpr uint32_t kWaitSleepNs = 20000;  // one suspension; the overall bound is kWaitBudgetNs
+
 // Wait for phase `parity` of the barrier to complete, for at most
 // kWaitBudgetNs.  On expiry the device status word receives
 // kStatusTimeout, the block-wide abort flag is set and false is returned.
@@ -125,7 +142,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_sleep(bar, parity, kWaitSleepNs)) return true;
         if (*abort_flag) return false;
         if (globaltimer_ns() - t0 > kWaitBudgetNs) {
             raise_status(status, kStatusTimeout);
