@@ -53,4 +53,23 @@ cudaError_t launch_cached(const void* fn, uint64_t a, uint64_t b, int* out, Make
     return cudaSuccess;
 }
 
+// Sets the kernel's shared-memory attributes once per device: the dynamic
+// limit to the device's opt-in maximum (the attribute belongs to the function,
+// not to one launch, so launches with different sizes must not lower it) and
+// the largest carveout.
+template <class Kernel>
+cudaError_t ensure_smem_attributes(Kernel k) {
+    int done = 0;
+    return launch_cached(reinterpret_cast<const void*>(k), ~uint64_t(0), 0, &done, [&](int* v) {
+        int dev = 0, optin = 0;
+        cudaError_t r = cudaGetDevice(&dev);
+        if (r == cudaSuccess) r = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (r == cudaSuccess) r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        *v = 1;
+        return r;
+    });
+}
+
 }  // namespace sdfnn

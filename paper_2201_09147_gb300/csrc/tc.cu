@@ -1050,18 +1050,12 @@ cudaError_t resident_ctas(Kernel k, int threads, size_t smem, int tmem_cols, int
 template <class Kernel>
 cudaError_t launch_tc(Kernel k, int threads, size_t smem, int tmem_cols, int num_sms, cudaStream_t s,
                       const void* arg) {
+    cudaError_t e = ensure_smem_attributes(k);
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    cudaError_t e = launch_cached(reinterpret_cast<const void*>(k), smem,
-                                  (static_cast<uint64_t>(threads) << 32) | static_cast<uint32_t>(tmem_cols), &per_sm,
-                                  [&](int* v) {
-                                      cudaError_t r = cudaFuncSetAttribute(
-                                          k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-                                      if (r == cudaSuccess)
-                                          r = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                                                   cudaSharedmemCarveoutMaxShared);
-                                      if (r == cudaSuccess) r = resident_ctas(k, threads, smem, tmem_cols, v);
-                                      return r;
-                                  });
+    e = launch_cached(reinterpret_cast<const void*>(k), smem,
+                      (static_cast<uint64_t>(threads) << 32) | static_cast<uint32_t>(tmem_cols), &per_sm,
+                      [&](int* v) { return resident_ctas(k, threads, smem, tmem_cols, v); });
     if (e != cudaSuccess) return e;
     void* args[] = {const_cast<void*>(arg)};
     return cudaLaunchKernel(reinterpret_cast<const void*>(k), dim3(num_sms * per_sm), dim3(threads), args, smem, s);

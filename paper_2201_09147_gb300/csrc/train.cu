@@ -635,16 +635,14 @@ __global__ void adam_kernel(float* __restrict__ theta, const float* __restrict__
 
 template <class Kernel>
 cudaError_t launch_simt_persistent(Kernel k, size_t smem, int num_sms, cudaStream_t s, const void* arg) {
-    // the attributes are set and the occupancy counted once per kernel and device
+    // the attributes are set and the occupancy counted once per kernel and device; the
+    // largest shared-memory carveout lets the occupancy query (and the launch) place as
+    // many CTAs per SM as shared memory allows
+    cudaError_t e = ensure_smem_attributes(k);
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    cudaError_t e = launch_cached(reinterpret_cast<const void*>(k), smem, kSimtThreads, &per_sm, [&](int* v) {
-        cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        // the largest shared-memory carveout lets the occupancy query (and the launch)
-        // place as many CTAs per SM as shared memory allows
-        if (r == cudaSuccess)
-            r = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-        if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(v, k, kSimtThreads, smem);
-        return r;
+    e = launch_cached(reinterpret_cast<const void*>(k), smem, kSimtThreads, &per_sm, [&](int* v) {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(v, k, kSimtThreads, smem);
     });
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
