@@ -69,17 +69,17 @@ __host__ __device__ inline TraceLayout trace_layout(int W, int KH, bool split, i
     L.wout = o;
     o += W * 4u;
     L.bars = o;
-    o += 8u * (1 + 2 * 8);  // weights, then per tile: MMA done, X ready
+    o += 8u * (1 + 8);
     o = (o + 15u) & ~15u;
     L.misc = o;
-    o += 128u;  // TMEM base, abort flag, per tile: active-ray count, exit flag
+    o += 64u;
     L.total = o;
     return L;
 }
 
 constexpr uint32_t kSplitSmemLimit = 200u * 1024u;
 constexpr int kMaxTraceTiles = 6;
-constexpr int kTraceMaxThreads = 128 * kMaxTraceTiles + 32;  // tiles + the MMA warp
+constexpr int kTraceMaxThreads = 128 * kMaxTraceTiles;
 
 // The trace kernel's tensor pipe is mostly idle (its time goes to the sines),
 // so whenever the doubled operands fit it computes each hidden layer as
@@ -151,15 +151,10 @@ __device__ __forceinline__ void trace_layer0(const LevelArgs& a, const float* w0
     }
 }
 
-// T = (blockDim.x - 32) / 128 independent ray tiles per CTA and one MMA
-// warp.  Tile t owns warps 4t..4t+3 (so its threads read TMEM lanes 0..127),
-// TMEM columns [t*W, (t+1)*W), its own activation buffers and two mbarriers:
-// X-ready (its 128 threads arrive after writing their rows) and MMA-done.  The
-// MMA warp (warp 4T, one elected thread) polls the tiles' X-ready barriers,
-// issues each ready tile's MMAs against the weights shared by all tiles and
-// commits them to the tile's MMA-done barrier; at the start of an evaluation
-// it also reads the tile's count of active rays and, when it is zero, ends
-// the tile instead of issuing.  The tiles' warps never wait for each other.
+// T = blockDim.x / 128 independent ray tiles per CTA.  Tile t owns warps
+// 4t..4t+3 (so its threads read TMEM lanes 0..127), TMEM columns
+// [t*W, (t+1)*W), its own activation buffers, MMA mbarrier and named barrier
+// 1 + t; the weights and layer parameters are shared.
 template <int W, bool F16, bool SPLIT>
 __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(const LevelArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -168,31 +163,26 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
     uint8_t* base = smem_raw + (base_s - raw_s);
     const NetView& net = a.net;
     const int KH = net.n_hidden;
-    const int T = (blockDim.x - 32) >> 7;
+    const int T = blockDim.x >> 7;
     const TraceLayout L = trace_layout(W, KH, SPLIT, T);
     float* w0s = reinterpret_cast<float*>(base + L.w0);
     float* wts = reinterpret_cast<float*>(base + L.wt);
     float* bhs = reinterpret_cast<float*>(base + L.bh);
     float* wos = reinterpret_cast<float*>(base + L.wout);
     const uint32_t bar_w = base_s + L.bars;
-    const uint32_t bars_mma = bar_w + 8u, bars_x = bar_w + 8u * (1 + 8);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.misc);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(base + L.misc + 8);
-    int* active = reinterpret_cast<int*>(base + L.misc + 16);              // [8]
-    volatile int* exitf = reinterpret_cast<volatile int*>(base + L.misc + 48);  // [8]
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tile = tid >> 7, ttid = tid & 127, twarp = ttid >> 5;
     constexpr uint32_t xbytes = 128u * W * 2u;
+    const uint32_t bar_mma = base_s + L.bars + 8u * (1 + tile);
+    const uint32_t x_s = base_s + L.x + tile * xbytes, xlo_s = base_s + L.xlo + tile * xbytes;
     const uint32_t w_s = base_s + L.w, wlo_s = base_s + L.wlo;
     const uint32_t tcols = tmem_cols_for(T * W);
 
     if (tid == 0) {
         mbar_init(bar_w, 1);
-        for (int t = 0; t < T; ++t) {
-            mbar_init(bars_mma + 8u * t, 1);
-            mbar_init(bars_x + 8u * t, 128);
-            active[t] = 0;
-            exitf[t] = 0;
-        }
+        for (int t = 0; t < T; ++t) mbar_init(base_s + L.bars + 8u * (1 + t), 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -209,168 +199,120 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    const uint32_t tmem = *tmem_slot + static_cast<uint32_t>(tile * W);
+
+    if (tid == 0) {
+        mbar_arrive_expect_tx(bar_w, static_cast<uint32_t>(KH) * W * W * 2u * (SPLIT ? 2u : 1u));
+        for (int l = 0; l < KH; ++l)
+            for (int kb = 0; kb < W / 64; ++kb) {
+                const size_t src = static_cast<size_t>(l) * net.wbf_layer_bytes + static_cast<size_t>(kb) * net.rows_pad * 128u;
+                bulk_g2s(w_s + l * W * W * 2u + kb * W * 128u, net.wbf + src, W * 128u, bar_w);
+                if (SPLIT) bulk_g2s(wlo_s + l * W * W * 2u + kb * W * 128u, net.wbf_lo + src, W * 128u, bar_w);
+            }
+    }
+    bool ok = mbar_wait_bounded(bar_w, 0, a.status, abort_flag);
+
     const long long n_work = a.in_list ? static_cast<long long>(*a.in_count) : a.n;
+    const uint32_t lane_base = static_cast<uint32_t>(twarp * 32) << 16;
+    constexpr uint32_t idesc = idesc_f32acc(128, W, F16);
+    uint32_t mma_phase = 0;
+    const int bar_id = 1 + tile;
+    Ray ray;
 
-    if (warp == 4 * T) {
-        // ------------------------------------------------------------- MMA warp
-        if (lane == 0 && a.cap > 0) {
-            mbar_arrive_expect_tx(bar_w, static_cast<uint32_t>(KH) * W * W * 2u * (SPLIT ? 2u : 1u));
-            for (int l = 0; l < KH; ++l)
-                for (int kb = 0; kb < W / 64; ++kb) {
-                    const size_t src =
-                        static_cast<size_t>(l) * net.wbf_layer_bytes + static_cast<size_t>(kb) * net.rows_pad * 128u;
-                    bulk_g2s(w_s + l * W * W * 2u + kb * W * 128u, net.wbf + src, W * 128u, bar_w);
-                    if (SPLIT) bulk_g2s(wlo_s + l * W * W * 2u + kb * W * 128u, net.wbf_lo + src, W * 128u, bar_w);
-                }
-            bool ok = mbar_wait_bounded(bar_w, 0, a.status, abort_flag);
-            constexpr uint32_t idesc = idesc_f32acc(128, W, F16);
-            const uint32_t tmem0 = *tmem_slot;
-            uint32_t px = 0u, done = 0u, lyrs = 0u;  // lyrs: next hidden layer of tile t in bits 2t, 2t + 1
-            int alive = T;
-            uint64_t t_last = globaltimer_ns();
-            while (ok && alive > 0) {
-                bool progressed = false;
-                for (int t = 0; t < T; ++t) {
-                    if ((done >> t) & 1u) continue;
-                    if (!mbar_test_wait(bars_x + 8u * t, (px >> t) & 1u)) continue;
-                    px ^= 1u << t;
-                    progressed = true;
-                    tc_fence_after();
-                    const uint32_t lyr = (lyrs >> (2 * t)) & 3u;
-                    if (lyr == 0 && atomicExch(&active[t], 0) == 0) {
-                        // no active ray left in the tile: end it
-                        exitf[t] = 1;
-                        done |= 1u << t;
-                        --alive;
-                        mbar_arrive(bars_mma + 8u * t);
-                        continue;
-                    }
-                    // hidden layer lyr of tile t: D = X W^T (+ the remainder products)
-                    const uint32_t x_s = base_s + L.x + t * xbytes, xlo_s = base_s + L.xlo + t * xbytes;
-                    const uint32_t wl = w_s + lyr * W * W * 2u, wll = wlo_s + lyr * W * W * 2u;
-                    const uint32_t d = tmem0 + static_cast<uint32_t>(t * W);
-                    const uint64_t dx = desc_kmajor_sw128(x_s), dxl = desc_kmajor_sw128(xlo_s);
-                    const uint64_t dw = desc_kmajor_sw128(wl), dwl = desc_kmajor_sw128(wll);
-#pragma unroll
-                    for (int kb = 0; kb < W / 64; ++kb)
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            // descriptors advance by the byte offset / 16 in their address field
-                            const uint64_t xo = (kb * 128u * 128u + kk * 32u) >> 4, wo = (kb * W * 128u + kk * 32u) >> 4;
-                            mma_f16kind(d, dx + xo, dw + wo, idesc, (kb | kk) != 0);
-                            if (SPLIT) {
-                                mma_f16kind(d, dx + xo, dwl + wo, idesc, 1u);
-                                mma_f16kind(d, dxl + xo, dw + wo, idesc, 1u);
-                            }
-                        }
-                    mma_commit(bars_mma + 8u * t);
-                    const uint32_t nxt = lyr + 1 == static_cast<uint32_t>(KH) ? 0u : lyr + 1;
-                    lyrs = (lyrs & ~(3u << (2 * t))) | (nxt << (2 * t));
-                }
-                if (progressed) {
-                    t_last = globaltimer_ns();
-                } else {
-                    if (*abort_flag) break;
-                    if (globaltimer_ns() - t_last > kWaitBudgetNs) {
-                        raise_status(a.status, kStatusTimeout);
-                        *abort_flag = 1;
-                        break;
-                    }
-                }
-            }
-        }
-    } else if (a.cap <= 0) {
-        // ------------------------------------------- pass-through level (no step)
-        Ray ray;
-        while (true) {
-            refill_ray(a, ray, n_work);
-            if (!__any_sync(0xffffffffu, ray.state == kSlotActive)) break;
+    while (ok) {
+        refill_ray(a, ray, n_work);
+        if (a.cap <= 0) {
+            if (!bar_or(bar_id, 128, ray.state == kSlotActive)) break;
             pass_ray(a, ray);
+            continue;
         }
-    } else {
-        // ------------------------------------------------------------ ray tiles
-        const int tile = tid >> 7, ttid = tid & 127, twarp = ttid >> 5;
-        const uint32_t bar_mma = bars_mma + 8u * tile, bar_x = bars_x + 8u * tile;
-        const uint32_t x_s = base_s + L.x + tile * xbytes, xlo_s = base_s + L.xlo + tile * xbytes;
-        const uint32_t tmem = *tmem_slot + static_cast<uint32_t>(tile * W);
-        const uint32_t lane_base = static_cast<uint32_t>(twarp * 32) << 16;
-        uint32_t mma_phase = 0;
-        bool ok = true;
-        Ray ray;
-        while (ok) {
-            refill_ray(a, ray, n_work);
-            // layer 0 (FP32): row ttid of X = 16-bit sin(W_0 (p, t) + b_0); an empty
-            // slot writes a row from its stale (finite) state, which nothing reads
-            if (timed)
-                trace_layer0<W, F16, SPLIT, true>(a, w0s, wts, ray, ttid, x_s, xlo_s);
-            else
-                trace_layer0<W, F16, SPLIT, false>(a, w0s, wts, ray, ttid, x_s, xlo_s);
-            const unsigned act = __popc(__ballot_sync(0xffffffffu, ray.state == kSlotActive));
-            if (lane == 0 && act) atomicAdd(&active[tile], static_cast<int>(act));
-            fence_proxy_async_smem();
-            tc_fence_before();
-            mbar_arrive(bar_x);
+        // layer 0 (FP32): row ttid of X = 16-bit sin(W_0 (p, t) + b_0); an empty
+        // slot writes a row from its stale (finite) state, which nothing reads
+        if (timed)
+            trace_layer0<W, F16, SPLIT, true>(a, w0s, wts, ray, ttid, x_s, xlo_s);
+        else
+            trace_layer0<W, F16, SPLIT, false>(a, w0s, wts, ray, ttid, x_s, xlo_s);
+        fence_proxy_async_smem();
+        tc_fence_before();
+        // one barrier: X is complete, and the tile stops when no slot is active
+        if (!bar_or(bar_id, 128, ray.state == kSlotActive)) break;
 
-            float f = 0.0f;
-            for (int l = 0; l < KH; ++l) {
-                ok = mbar_wait_bounded(bar_mma, mma_phase, a.status, abort_flag);
-                mma_phase ^= 1u;
-                if (!ok || exitf[tile]) break;
+        float f = 0.0f;
+        for (int l = 0; l < KH; ++l) {
+            if (ttid == 0) {
                 tc_fence_after();
-                const float* bl = bhs + l * W;
-                if (l + 1 < KH) {
-                    // hidden epilogue: X row = 16-bit sin(D + b)
-                    for (int c0 = 0; c0 < W; c0 += 32) {
-                        float v[32];
-                        tmem_ld32(tmem + lane_base + c0, v);
-                        tmem_wait_ld();
+                const uint32_t wl = w_s + l * W * W * 2u, wll = wlo_s + l * W * W * 2u;
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            uint32_t pk[4], pl[4];
-                            const float4 ba = reinterpret_cast<const float4*>(bl + c0)[2 * q];
-                            const float4 bb = reinterpret_cast<const float4*>(bl + c0)[2 * q + 1];
-                            const float b8[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+                for (int kb = 0; kb < W / 64; ++kb)
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const int j = q * 8 + 2 * e;
-                                const float s0 = sin_fast(v[j] + b8[2 * e]), s1 = sin_fast(v[j + 1] + b8[2 * e + 1]);
-                                if (SPLIT)
-                                    pack_split<F16>(s0, s1, pk[e], pl[e]);
-                                else
-                                    pk[e] = pack16x2<F16>(s0, s1);
-                            }
-                            const uint32_t off = sw128_chunk_offset(ttid, (c0 >> 3) + q, 128);
-                            st_shared_v4(x_s + off, pk[0], pk[1], pk[2], pk[3]);
-                            if (SPLIT) st_shared_v4(xlo_s + off, pl[0], pl[1], pl[2], pl[3]);
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint32_t xo = kb * 128u * 128u + kk * 32u, wo = kb * W * 128u + kk * 32u;
+                        mma_f16kind(tmem, desc_kmajor_sw128(x_s + xo), desc_kmajor_sw128(wl + wo), idesc,
+                                    (kb | kk) != 0);
+                        if (SPLIT) {
+                            mma_f16kind(tmem, desc_kmajor_sw128(x_s + xo), desc_kmajor_sw128(wll + wo), idesc, 1u);
+                            mma_f16kind(tmem, desc_kmajor_sw128(xlo_s + xo), desc_kmajor_sw128(wl + wo), idesc, 1u);
                         }
                     }
-                    fence_proxy_async_smem();
-                    tc_fence_before();
-                    mbar_arrive(bar_x);
-                } else {
-                    // output layer in FP32: f = w_out . sin(D + b) + b_out
-                    float dot = 0.0f;
-                    for (int c0 = 0; c0 < W; c0 += 32) {
-                        float v[32];
-                        tmem_ld32(tmem + lane_base + c0, v);
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int j4 = 0; j4 < 8; ++j4) {
-                            const float4 b4 = reinterpret_cast<const float4*>(bl + c0)[j4];
-                            const float4 w4 = reinterpret_cast<const float4*>(wos + c0)[j4];
-                            dot = fmaf(w4.x, sin_fast(v[4 * j4 + 0] + b4.x), dot);
-                            dot = fmaf(w4.y, sin_fast(v[4 * j4 + 1] + b4.y), dot);
-                            dot = fmaf(w4.z, sin_fast(v[4 * j4 + 2] + b4.z), dot);
-                            dot = fmaf(w4.w, sin_fast(v[4 * j4 + 3] + b4.w), dot);
-                        }
-                    }
-                    f = dot + net.bout;
-                }
+                mma_commit(bar_mma);
             }
-            if (!ok || exitf[tile]) break;
-            tc_fence_before();
-            step_ray(a, ray, f);
+            ok = mbar_wait_bounded(bar_mma, mma_phase, a.status, abort_flag);
+            mma_phase ^= 1u;
+            if (!ok) break;
+            tc_fence_after();
+            const float* bl = bhs + l * W;
+            if (l + 1 < KH) {
+                // hidden epilogue: X row = 16-bit sin(D + b)
+                for (int c0 = 0; c0 < W; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(tmem + lane_base + c0, v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        uint32_t pk[4], pl[4];
+                        const float4 ba = reinterpret_cast<const float4*>(bl + c0)[2 * q];
+                        const float4 bb = reinterpret_cast<const float4*>(bl + c0)[2 * q + 1];
+                        const float b8[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int j = q * 8 + 2 * e;
+                            const float s0 = sin_fast(v[j] + b8[2 * e]), s1 = sin_fast(v[j + 1] + b8[2 * e + 1]);
+                            if (SPLIT)
+                                pack_split<F16>(s0, s1, pk[e], pl[e]);
+                            else
+                                pk[e] = pack16x2<F16>(s0, s1);
+                        }
+                        const uint32_t off = sw128_chunk_offset(ttid, (c0 >> 3) + q, 128);
+                        st_shared_v4(x_s + off, pk[0], pk[1], pk[2], pk[3]);
+                        if (SPLIT) st_shared_v4(xlo_s + off, pl[0], pl[1], pl[2], pl[3]);
+                    }
+                }
+                fence_proxy_async_smem();
+                tc_fence_before();
+                bar_named(bar_id, 128);
+            } else {
+                // output layer in FP32: f = w_out . sin(D + b) + b_out
+                float dot = 0.0f;
+                for (int c0 = 0; c0 < W; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(tmem + lane_base + c0, v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j4 = 0; j4 < 8; ++j4) {
+                        const float4 b4 = reinterpret_cast<const float4*>(bl + c0)[j4];
+                        const float4 w4 = reinterpret_cast<const float4*>(wos + c0)[j4];
+                        dot = fmaf(w4.x, sin_fast(v[4 * j4 + 0] + b4.x), dot);
+                        dot = fmaf(w4.y, sin_fast(v[4 * j4 + 1] + b4.y), dot);
+                        dot = fmaf(w4.z, sin_fast(v[4 * j4 + 2] + b4.z), dot);
+                        dot = fmaf(w4.w, sin_fast(v[4 * j4 + 3] + b4.w), dot);
+                    }
+                }
+                f = dot + net.bout;
+            }
         }
+        if (!ok) break;
+        tc_fence_before();
+        step_ray(a, ray, f);
     }
 
     tc_fence_before();
@@ -1142,7 +1084,7 @@ static int trace_tiles_uncached(Kernel k, int W, int KH, bool split) {
     const int regs_warp = ((at.numRegs * 32 + 255) / 256) * 256;
     int T = kMaxTraceTiles;
     while (T > 1 && (trace_layout(W, KH, split, T).total + 1024 > static_cast<uint32_t>(smem_optin) ||
-                     regs_warp * (4 * T + 1) > regs_sm || static_cast<int>(tmem_cols_for(T * W)) > 512))
+                     regs_warp * 4 * T > regs_sm || static_cast<int>(tmem_cols_for(T * W)) > 512))
         --T;
     return T;
 }
@@ -1168,14 +1110,12 @@ static cudaError_t launch_trace_resident(const LevelArgs& a, int num_sms, cudaSt
         auto k = trace_level_tc_kernel<W, F16, true>;
         int T = trace_tiles(k, W, KH, true);
         if (a.tiles > 0) T = std::min(T, a.tiles);
-        return launch_tc(k, 128 * T + 32, trace_layout(W, KH, true, T).total + 1024, tmem_cols_for(T * W), num_sms, s,
-                         &a);
+        return launch_tc(k, 128 * T, trace_layout(W, KH, true, T).total + 1024, tmem_cols_for(T * W), num_sms, s, &a);
     }
     auto k = trace_level_tc_kernel<W, F16, false>;
     int T = trace_tiles(k, W, KH, false);
     if (a.tiles > 0) T = std::min(T, a.tiles);
-    return launch_tc(k, 128 * T + 32, trace_layout(W, KH, false, T).total + 1024, tmem_cols_for(T * W), num_sms, s,
-                     &a);
+    return launch_tc(k, 128 * T, trace_layout(W, KH, false, T).total + 1024, tmem_cols_for(T * W), num_sms, s, &a);
 }
 
 template <int W, bool F16>
