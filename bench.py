@@ -121,7 +121,7 @@ def job_throughput(local_total_ms: float, units_per_rank: int, steps: int, ws: i
     return ws * units_per_rank * steps / (t / 1e3) / 1e6, t
 
 
-def oracle_sample(wl, rows):
+def oracle_sample(wl, rows, threads=None):
     """Runs the FP64 oracle on the given image rows: trace + normal map at its hits."""
     import oracle
     orig, dirs = wl.rays(rows=rows)
@@ -129,9 +129,9 @@ def oracle_sample(wl, rows):
     onets = [oracle.Net(b) for b in wl.level_bytes()]
     tp = oracle.TraceParams([oracle.SDF.of_net(n) for n in onets], wl.delta, wl.caps, wl.step_scale, wl.eps,
                             final_mode=wl.final_mode)
-    res = tp.trace_batch(orig, dirs)
+    res = tp.trace_batch(orig, dirs, threads=threads)
     fine = oracle.Net(wl.fine_bytes())
-    nrm = fine.normal_map(res["pos"], res["hit"])
+    nrm = fine.normal_map(res["pos"], res["hit"], threads=threads)
     dt = time.perf_counter() - t0
     return res, nrm, dt, orig.shape[1]
 
@@ -353,6 +353,22 @@ def main():
             torch.cuda.synchronize()
             pt.append(a.elapsed_time(b))
         plain_value = n / (statistics.mean(pt) / 1e3) / 1e6
+        # the same plain (256,3) tracer with BF16 hidden layers: the precision alone
+        pb = [sdfnn.Net(b, sdfnn.SDF_BF16, local) for b in plain.level_bytes()]
+        pbf = sdfnn.Net(plain.fine_bytes(), sdfnn.SDF_BF16, local)
+        bt = []
+        for _ in range(4):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sdfnn.trace_multiscale(pb, plain.delta, plain.caps, plain.eps, orig, dirs, step_scale=plain.step_scale,
+                                   final_mode=plain.final_mode, out_pos=pos, out_t=tt, out_hit=hit, want_iters=False)
+            sdfnn.normal_map(pbf, pos, hit, out=nrm)
+            b.record(stream)
+            torch.cuda.synchronize()
+            bt.append(a.elapsed_time(b))
+        plain_bf16_value = n / (statistics.mean(bt[1:]) / 1e3) / 1e6
         # multiscale with FP32 hidden layers: isolates the algorithm from the precision
         c32 = [sdfnn.Net(b, sdfnn.SDF_FP32, local) for b in wl.level_bytes()]
         f32 = sdfnn.Net(wl.fine_bytes(), sdfnn.SDF_FP32, local)
@@ -407,6 +423,8 @@ def main():
                                  "fp8_normal_map_Mrays_s": fp8_value,
                                  "fp8_normal_map_ms": fp8_nm_ms,
                                  "plain_fp32_256x3_Mrays_s": plain_value,
+                                 "plain_bf16_256x3_Mrays_s": plain_bf16_value,
+                                 "speedup_precision_only_plain": plain_bf16_value / plain_value,
                                  "speedup_vs_plain_fp32": value / ws / plain_value,
                                  "multiscale_fp32_Mrays_s": ms_fp32_value,
                                  "speedup_algorithm_only": ms_fp32_value / plain_value,
@@ -509,10 +527,14 @@ def main():
         rows = np.arange(0, wl.height, ORACLE_ROW_STRIDE)
         res, onrm, dt, ns = oracle_sample(wl, rows)
         import oracle
+        # one core, on a 16x smaller sample
+        _, _, dt1, ns1 = oracle_sample(wl, rows[::16], threads=1)
         result["cpu_baseline"] = {"value": ns / dt / 1e6, "unit": UNIT, "cores": oracle.default_threads(),
                                   "kind": "oracle",
                                   "sample": f"{ns} rays: every {ORACLE_ROW_STRIDE}th row of the 1080p frame, "
-                                            f"trace + normal map in FP64"}
+                                            f"trace + normal map in FP64",
+                                  "one_core": {"value": ns1 / dt1 / 1e6, "unit": UNIT, "cores": 1,
+                                               "sample": f"{ns1} rays: every {16 * ORACLE_ROW_STRIDE}th row"}}
         idx = (rows[:, None] * wl.width + np.arange(wl.width)[None, :]).ravel()
         fine_oracle = oracle.Net(wl.fine_bytes())
 
