@@ -266,6 +266,28 @@ def test_normal_map_1080p_sampled(sdf, precision):
     assert np.all(nrm.cpu().numpy()[:, ~allhit] == 0.0)
 
 
+@pytest.mark.parametrize("name", ["nested_3level_512", "three_level_512", "silhouette_512"])
+@pytest.mark.parametrize("precision", [1, 3], ids=["bf16", "fp16"])
+def test_512_workloads_full_size_sampled(sdf, precision, name):
+    """The 512 x 512 workloads at full size as the benchmark runs them; oracle on 2,000 sampled rays."""
+    wl = workloads.get(name)
+    orig, dirs = wl.rays()
+    lb = wl.level_bytes()
+    g = gpu_trace(sdf, lb, precision, wl, orig, dirs)
+    fine = sdf.Net(wl.fine_bytes(), precision)
+    nrm = sdf.normal_map(fine, g["pos_dev"], g["hit_dev"])
+    sdf.sync_status()
+    idx = np.sort(np.unique((inputs.uniform01(123, 2000) * wl.n_rays).astype(np.int64)))
+    o = oracle_trace(lb, wl, orig, dirs, idx=idx)
+    gs = {"pos": g["pos"][:, idx], "hit": g["hit"][idx]}
+    rep = check_trace(gs, o, precision, f"{name} full p={precision}")
+    assert rep["n_both"] > 150
+    ref = oracle.Net(wl.fine_bytes()).normal_map(gs["pos"].astype(np.float64), gs["hit"])
+    ar = angle_report(nrm.cpu().numpy()[:, idx], ref, gs["hit"].astype(bool))
+    print(ar)
+    assert ar["angle_p999"] <= TOL[precision][2]
+
+
 @pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
 def test_mesh_normal_map(sdf, precision):
     """Neural normal mapping onto mesh vertices (Sec. 5): displaced icosphere, subdivision 5."""

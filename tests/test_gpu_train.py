@@ -207,3 +207,35 @@ def test_native_fit_matches_torch_reference(sdf):
     assert np.all(np.abs(objs[:, 0] - objs[:, 1]) <= 2e-3 * objs[:, 1])
     assert objs[-1, 0] < 0.8 * objs[0, 0]
     assert (th - ref.detach()).abs().max().item() <= 1e-3 * ref.detach().abs().max().item()
+
+
+def test_full_batch_objective_and_chunking(sdf):
+    """2^20 points (the benchmark's batch) of a (64,2): the objective matches the FP64 oracle,
+    and the gradient of the whole batch equals the sum over four chunks."""
+    b = (workloads.SCENES / "s8_64x2.sdfn").read_bytes()
+    shape, theta = sdf.theta_from_sdfn(b)
+    n = 1 << 20
+    pts, tf, tg, near = _loss_inputs(n, seed=11)
+    th = _dev(theta)
+    dp, dtf, dtg, dnear = _dev(pts), _dev(tf), _dev(tg), _dev(near)
+    f, g, ws = sdf.train_forward(shape, th, dp)
+    d_f, d_g, loss = sdf.fit_loss(f, g, dtf, dtg, dnear, LAM_N, LAM_E)
+    whole = sdf.train_backward(shape, th, dp, d_f, d_g, ws)
+    torch.cuda.synchronize()
+    L, parts = oracle.fit_loss(b, pts, tf, tg, near, LAM_N, LAM_E)
+    got = loss.cpu().numpy()
+    print(got, L)
+    assert np.allclose(got[:3], parts, rtol=2e-4) and abs(got[3] - L) <= 2e-4 * abs(L)
+    del ws
+    acc = torch.zeros_like(whole)
+    q = n // 4
+    for c in range(4):
+        sl = slice(c * q, (c + 1) * q)
+        p = dp[:, sl].contiguous()
+        _, _, w = sdf.train_forward(shape, th, p)
+        sdf.train_backward(shape, th, p, d_f[sl].contiguous(), d_g[:, sl].contiguous(), w, acc)
+        del w
+    sdf.sync_status()
+    rel = (acc - whole).norm() / whole.norm()
+    print("chunked vs whole rel", rel.item())
+    assert rel.item() <= 1e-4
