@@ -13,8 +13,8 @@ import torch
 
 import oracle
 from paper_2201_09147_gb300 import inputs, workloads
-from parity import (FP8_ANGLE_MEDIAN_DEG, FP8_ANGLE_P999_DEG, FP8_MAGNITUDE_REL, HIT_AGREEMENT, PRECISION_IDS,
-                    PRECISIONS, RANDOM_NET_ANGLE_FACTOR, TOL, angle_report, trace_report)
+from parity import (DECISION_MARGIN, FP8_ANGLE_MEDIAN_DEG, FP8_ANGLE_P999_DEG, FP8_MAGNITUDE_REL, HIT_AGREEMENT,
+                    PRECISION_IDS, PRECISIONS, RANDOM_NET_ANGLE_FACTOR, TOL, angle_report, trace_report)
 
 pytestmark = pytest.mark.gpu
 
@@ -280,7 +280,15 @@ def test_512_workloads_full_size_sampled(sdf, precision, name):
     idx = np.sort(np.unique((inputs.uniform01(123, 2000) * wl.n_rays).astype(np.int64)))
     o = oracle_trace(lb, wl, orig, dirs, idx=idx)
     gs = {"pos": g["pos"][:, idx], "hit": g["hit"][idx]}
-    rep = check_trace(gs, o, precision, f"{name} full p={precision}")
+    # the hit test of the last level compares its FP64 end residual with eps
+    d_last = wl.delta[-1] if wl.final_mode == 1 else 0.0
+    _, v_last = oracle.Net(lb[-1]).grad_batch(o["pos"], with_value=True)
+    amb = np.abs((v_last - d_last) - wl.eps) <= DECISION_MARGIN[precision]
+    agree_tol, pos_tol, _ = TOL[precision]
+    rep = trace_report(gs["pos"], gs["hit"], o["pos"], o["hit"], ambiguous=amb)
+    print(name, precision, {k: v for k, v in rep.items() if k != "both"})
+    assert rep["agree"] >= agree_tol and rep["pos_p999"] <= pos_tol
+    assert rep["n_ambiguous"] <= 0.02 * idx.size
     assert rep["n_both"] > 150
     ref = oracle.Net(wl.fine_bytes()).normal_map(gs["pos"].astype(np.float64), gs["hit"])
     ar = angle_report(nrm.cpu().numpy()[:, idx], ref, gs["hit"].astype(bool))
