@@ -318,6 +318,16 @@ int sdf_adam_step(float *theta, const float *grad, float *m, float *v, int64_t c
  * current device (SDF_OK, or the first device-side error since the last call). */
 int sdf_sync_status(void *cuda_stream);
 
+/* Self-test of the device-side failure detection: launches a kernel whose
+ * bounded wait (the same loop the library's kernels use around every
+ * mbarrier) waits on a barrier that nothing signals, with a limit of
+ * budget_us microseconds (1 .. 10^7).  Returns SDF_OK when the wait expired,
+ * the kernel returned and sdf_sync_status reported (and cleared)
+ * SDF_ERR_TIMEOUT; the device stays usable.  The paper has no counterpart.
+ * Errors: SDF_ERR_ARG, SDF_ERR_CUDA (also when the expiry was not reported),
+ * or a status already pending on the device before the call. */
+int sdf_selftest_wait_timeout(int device, int64_t budget_us, void *cuda_stream);
+
 /* Thread-local message describing the last non-OK return of this thread. */
 const char *sdf_last_error(void);
 

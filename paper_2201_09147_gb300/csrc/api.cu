@@ -1271,6 +1271,29 @@ int sdf_adam_step(float* theta, const float* grad, float* m, float* v, int64_t c
     return SDF_OK;
 }
 
+int sdf_selftest_wait_timeout(int device, int64_t budget_us, void* cuda_stream) {
+    if (budget_us < 1 || budget_us > 10000000) return fail(SDF_ERR_ARG, "budget_us out of range 1..1e7");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return fail(SDF_ERR_ARG, "device %d not available", device);
+    }
+    DeviceGuard g(device);
+    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", device);
+    DeviceInfo di;
+    int rc = device_info(device, &di);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // the status word must be clear before, and must read the timeout after
+    rc = sdf_sync_status(cuda_stream);
+    if (rc) return rc;
+    cudaError_t e = launch_wait_timeout_selftest(di.d_status, static_cast<unsigned long long>(budget_us) * 1000ull, s);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the timeout self-test");
+    rc = sdf_sync_status(cuda_stream);
+    if (rc == SDF_ERR_TIMEOUT) return SDF_OK;
+    return rc ? rc : fail(SDF_ERR_CUDA, "the bounded wait did not report its expiry");
+}
+
 const char* sdf_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"

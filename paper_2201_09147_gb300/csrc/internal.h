@@ -131,6 +131,10 @@ cudaError_t launch_fit_loss(const float* f, const float* grad, const float* tf, 
 cudaError_t launch_adam(float* theta, const float* grad, float* m, float* v, int64_t count, float lr, float beta1,
                         float beta2, float eps, int step, int num_sms, cudaStream_t s);
 
+// A bounded wait on a barrier nothing signals, with the given budget: must
+// latch kStatusTimeout in *status and return.
+cudaError_t launch_wait_timeout_selftest(int* status, unsigned long long budget_ns, cudaStream_t s);
+
 // Builds list[] of the indices with mask[i] != 0 (order unspecified), zeroes
 // out[.][i] where mask[i] == 0, and counts into *count (zero at launch).
 cudaError_t launch_mask_compact(const uint8_t* mask, int64_t n, int32_t* list, unsigned long long* count,

@@ -264,6 +264,24 @@ __global__ void mask_compact_kernel(const uint8_t* __restrict__ mask, int64_t n,
     }
 }
 
+// One thread waits, with the library's bounded-wait loop but a budget of
+// `budget_ns`, on an mbarrier that nothing ever arrives on; on expiry it
+// latches kStatusTimeout in *status and the kernel returns normally.
+__global__ void wait_timeout_selftest_kernel(int* status, unsigned long long budget_ns) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = smem_u32(&bar);
+    mbar_init(b, 1);
+    fence_mbar_init();
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(b, 0u)) {
+        if (globaltimer_ns() - t0 > budget_ns) {
+            raise_status(status, kStatusTimeout);
+            return;
+        }
+    }
+}
+
 template <class Kernel>
 cudaError_t launch_persistent(Kernel k, size_t smem, int num_sms, cudaStream_t s, const void* arg) {
     // the attributes are set and the occupancy counted once per kernel and device; the
@@ -306,6 +324,11 @@ cudaError_t launch_grad_simt(const GradArgs& a, int num_sms, cudaStream_t s) {
         return launch_persistent(grad_simt_kernel<256>, sizeof(SimtSmem<256>), num_sms, s, &a);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_wait_timeout_selftest(int* status, unsigned long long budget_ns, cudaStream_t s) {
+    wait_timeout_selftest_kernel<<<1, 32, 0, s>>>(status, budget_ns);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_mask_compact(const uint8_t* mask, int64_t n, int32_t* list, unsigned long long* count, float* out,

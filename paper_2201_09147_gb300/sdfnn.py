@@ -24,7 +24,7 @@ EXPORTS = ["sdf_net_load", "sdf_net_load_mem", "sdf_net_info", "sdf_net_set_time
            "sdf_trace_multiscale", "sdf_normals", "sdf_normal_map", "sdf_render_host", "sdf_sync_status",
            "sdf_last_error", "sdf_trace_multiscale_noalloc", "sdf_normal_map_timed", "sdf_plan_create",
            "sdf_plan_launch", "sdf_plan_info", "sdf_plan_free", "sdf_train_shape_info", "sdf_train_forward",
-           "sdf_train_backward", "sdf_fit_loss", "sdf_adam_step"]
+           "sdf_train_backward", "sdf_fit_loss", "sdf_adam_step", "sdf_selftest_wait_timeout"]
 
 
 class SdfError(RuntimeError):
@@ -83,6 +83,7 @@ def lib():
         L.sdf_fit_loss.argtypes = [vp, vp, vp, vp, vp, C.c_int64, C.c_float, C.c_float, vp, vp, vp, vp]
         L.sdf_adam_step.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int,
                                     vp]
+        L.sdf_selftest_wait_timeout.argtypes = [C.c_int, C.c_int64, vp]
         L.sdf_sync_status.argtypes = [vp]
         L.sdf_last_error.restype = C.c_char_p
         _lib = L
@@ -276,6 +277,11 @@ def render_host(nets, delta, max_iters, eps, fine: Net, orig, dirs, out_pos, out
     _check(lib().sdf_render_host(C.byref(p), fine.handle, _ptr(orig), _ptr(dirs), n, _ptr(out_pos), _ptr(out_hit),
                                  _ptr(out_normal), C.c_void_p(_stream(stream))))
     del keep
+
+
+def selftest_wait_timeout(budget_us: int = 20000, device: int = 0, stream=None):
+    """Runs the device-side timeout self-test (raises if the expiry is not reported)."""
+    _check(lib().sdf_selftest_wait_timeout(device, int(budget_us), C.c_void_p(_stream(stream))))
 
 
 def sync_status(stream=None):

@@ -114,3 +114,9 @@ def test_theta_roundtrip_through_sdfn():
     g1, v1 = oracle.Net(b).grad_batch(pts, with_value=True)
     g2, v2 = oracle.Net(b2).grad_batch(pts, with_value=True)
     assert np.allclose(v1, v2, rtol=1e-5, atol=1e-5) and np.allclose(g1, g2, rtol=1e-4, atol=1e-3)
+
+
+def test_selftest_argument_check_without_a_gpu(lib):
+    lib.sdf_selftest_wait_timeout.argtypes = [C.c_int, C.c_int64, C.c_void_p]
+    assert lib.sdf_selftest_wait_timeout(0, 0, None) == -1
+    assert lib.sdf_selftest_wait_timeout(0, 10 ** 8, None) == -1
