@@ -18,9 +18,10 @@ infinity norm estimated as the maximum over sampled points, as the paper
 prescribes; that estimate lives in the tests (it needs the oracle).
 
 This module is not on the rendering path: nothing in the CUDA library or its
-binding imports it.  Usage:
+binding imports it.  With ``--native`` the same objective and Adam run on the
+GPU through the library's training kernels instead of torch autograd.  Usage:
 
-    python -m paper_2201_09147_gb300.fit --out paper_2201_09147_gb300/scenes
+    python -m paper_2201_09147_gb300.fit --out paper_2201_09147_gb300/scenes [--native]
 """
 from __future__ import annotations
 
@@ -159,6 +160,34 @@ def fit_net(scene, width, n_hidden, steps, seed=0, batch=1 << 14, lr=1e-4, lam_n
     return model.cpu().to_sinenet(template)
 
 
+def fit_net_native(scene, width, n_hidden, steps, seed=0, batch=1 << 14, lr=1e-4, lam_n=0.1, lam_e=0.05,
+                   log_every=500, scene_seed=1):
+    """The same objective and Adam, run natively on the GPU through the library's
+    training kernels (sdf_train_forward / sdf_fit_loss / sdf_train_backward /
+    sdf_adam_step) with parameters in folded form; 3-D networks.  A fresh batch
+    of inputs.fit_batch points per step, seeded by (seed, step)."""
+    from . import sdfnn
+    template = inputs.siren_init(seed, width, n_hidden)
+    shape, theta = sdfnn.theta_from_sdfn(inputs.net_to_bytes(template))
+    th = torch.from_numpy(theta).cuda()
+    m, v = torch.zeros_like(th), torch.zeros_like(th)
+    ws = None
+    t0 = time.time()
+    for it in range(steps):
+        pts, tf, tg, near = (torch.from_numpy(x).cuda() for x in inputs.fit_batch(scene, seed * 1_000_003 + it, batch))
+        # cosine schedule to lr / 20, as the torch fitter
+        lr_t = lr * (0.05 + 0.95 * 0.5 * (1.0 + math.cos(math.pi * it / steps)))
+        loss, ws = sdfnn.fit_step(shape, th, m, v, it + 1, pts, tf, tg, near, lam_n=lam_n, lam_e=lam_e, lr=lr_t,
+                                  workspace=ws if ws is not None and ws.numel() >= sdfnn.train_shape_info(
+                                      *shape, batch)[1] else None)
+        if log_every and (it % log_every == 0 or it == steps - 1):
+            lv = loss.cpu().numpy()
+            print(f"  ({width},{n_hidden}) native it {it:5d} loss {lv[3]:.5f} val {lv[0]:.5f} n {lv[1]:.4f} "
+                  f"eik {lv[2]:.4f}  {time.time() - t0:.0f}s", flush=True)
+    sdfnn.sync_status()
+    return inputs.net_from_bytes(sdfnn.sdfn_from_theta(shape, th.cpu().numpy()))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=str(SCENES_DIR))
@@ -166,6 +195,8 @@ def main():
     ap.add_argument("--steps", type=int, default=0, help="override the step count")
     ap.add_argument("--device", default="cpu")
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--native", action="store_true",
+                    help="fit on the GPU with the library's training kernels (3-D networks)")
     args = ap.parse_args()
     if args.threads:
         torch.set_num_threads(args.threads)
@@ -179,9 +210,13 @@ def main():
         in_dim = rest[0] if rest else 3
         steps = args.steps or steps
         print(f"fitting {name}: ({w},{k}) in_dim {in_dim}, {steps} steps", flush=True)
-        net = fit_net(scene, w, k, steps, device=args.device, in_dim=in_dim)
+        if args.native and in_dim == 3:
+            net = fit_net_native(scene, w, k, steps)
+        else:
+            net = fit_net(scene, w, k, steps, device=args.device, in_dim=in_dim)
         inputs.write_net(out / f"{name}.sdfn", net)
-        meta[name] = {"width": w, "n_hidden": k, "in_dim": in_dim, "steps": steps, "seed": 0, "scene_seed": 1}
+        meta[name] = {"width": w, "n_hidden": k, "in_dim": in_dim, "steps": steps, "seed": 0, "scene_seed": 1,
+                      "fitter": "native" if args.native and in_dim == 3 else "torch"}
     meta_path.write_text(json.dumps(meta, indent=1, sort_keys=True) + "\n")
 
 

@@ -196,3 +196,19 @@ def test_animation_32_frames_sampled(sdf, precision):
     ar = angle_report(nrm[:, flat], o_nrm, hit[flat].astype(bool))
     print(ar)
     assert ar["angle_p999"] <= ang_tol
+
+
+def test_fp8_normal_map_with_per_point_times(sdf):
+    """E4M3 normal mapping of the 4-D (256,3) at points of two times, against FP64 (E4M3 bounds)."""
+    from parity import FP8_ANGLE_MEDIAN_DEG
+    b = (workloads.SCENES / "a8_256x3_t.sdfn").read_bytes()
+    net = sdf.Net(b, sdf.SDF_FP8)
+    pts = inputs.random_points(31, 4000)
+    times = np.repeat(np.array([0.2, 0.7], np.float32), 2000)
+    nm = sdf.normal_map_timed(net, _dev(pts), _dev(times)).cpu().numpy()
+    on = oracle.Net(b)
+    ref = np.concatenate([on.normal_map(pts[:, :2000].astype(np.float64), time=float(np.float32(0.2))),
+                          on.normal_map(pts[:, 2000:].astype(np.float64), time=float(np.float32(0.7)))], axis=1)
+    ar = angle_report(nm, ref)
+    print(ar)
+    assert ar["angle_median"] <= FP8_ANGLE_MEDIAN_DEG

@@ -239,3 +239,13 @@ def test_full_batch_objective_and_chunking(sdf):
     rel = (acc - whole).norm() / whole.norm()
     print("chunked vs whole rel", rel.item())
     assert rel.item() <= 1e-4
+
+
+def test_native_fitter_produces_a_loadable_network(sdf, tmp_path):
+    """fit.py --native path: a few steps give an SDFN network the renderer and the oracle load."""
+    from paper_2201_09147_gb300 import fit
+    net = fit.fit_net_native(inputs.sphere_scene(1), 64, 1, 30, batch=1 << 12, log_every=0)
+    b = inputs.net_to_bytes(net)
+    assert oracle.Net(b).width == 64
+    n = sdf.Net(b, sdf.SDF_BF16)
+    assert n.lipschitz > 0
