@@ -178,8 +178,7 @@ def fit_net_native(scene, width, n_hidden, steps, seed=0, batch=1 << 14, lr=1e-4
         # cosine schedule to lr / 20, as the torch fitter
         lr_t = lr * (0.05 + 0.95 * 0.5 * (1.0 + math.cos(math.pi * it / steps)))
         loss, ws = sdfnn.fit_step(shape, th, m, v, it + 1, pts, tf, tg, near, lam_n=lam_n, lam_e=lam_e, lr=lr_t,
-                                  workspace=ws if ws is not None and ws.numel() >= sdfnn.train_shape_info(
-                                      *shape, batch)[1] else None)
+                                  workspace=ws)  # same batch size every step: the workspace is reused
         if log_every and (it % log_every == 0 or it == steps - 1):
             lv = loss.cpu().numpy()
             print(f"  ({width},{n_hidden}) native it {it:5d} loss {lv[3]:.5f} val {lv[0]:.5f} n {lv[1]:.4f} "
