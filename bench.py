@@ -281,14 +281,17 @@ def main():
                     "traffic": traffic_tbl.get("grad_tc_kernel<256, 0>"), "peak_source": f"{pk['source']} bf16 sustained",
                     "work": f"{n_hit} points x {normal_flops_per_point} hidden-layer MMA flops"}
     else:
-        # sine-bound: one MUFU sine per hidden unit per evaluation
+        # sine-bound: one hardware sine per unit per evaluation; the roof is the measured
+        # rate of the same sine (independent chains on all SMs)
         sm_mhz = clk.get("sm_mhz") or 1900.0
-        peak_gsin = 152 * 16 * sm_mhz * 1e6 / 1e9
+        nominal_gsin = 152 * 16 * sm_mhz * 1e6 / 1e9
+        peak_gsin = sdfnn.measure_sine_rate(local) / 1e9
         achieved = total_evals * sines_per_eval / (tr_ms / 1e3) / 1e9
         roofline = {"kernel": "trace_level_tc_kernel<64> (coarse (64,1) trace)", "bound": "alu", "achieved": achieved,
                     "peak": peak_gsin, "unit": "Gsin/s", "frac": achieved / peak_gsin,
                     "traffic": traffic_tbl.get("trace_level_tc_kernel<64, 0, 1>"),
-                    "peak_source": "152 SMs x 16 MUFU/clk x median SM clock",
+                    "peak_source": "measured: sine microbenchmark (sdf_measure_sine_rate), "
+                                   f"nominal 152 SMs x 16 per clock = {nominal_gsin:.0f} Gsin/s",
                     "work": f"{total_evals} evaluations x {sines_per_eval} sines"}
 
     # end to end from pinned host buffers through sdf_render_host

@@ -328,6 +328,13 @@ int sdf_sync_status(void *cuda_stream);
  * or a status already pending on the device before the call. */
 int sdf_selftest_wait_timeout(int device, int64_t budget_us, void *cuda_stream);
 
+/* Measurement helper: the throughput, in sines per second on all SMs, of the
+ * hardware sine the tensor-core kernels use (independent chains of
+ * sin(x) * c + d, timed with CUDA events on `cuda_stream`, which is
+ * synchronised).  It is the ALU roof of the sine-bound trace kernel.
+ * Errors: SDF_ERR_ARG, SDF_ERR_CUDA. */
+int sdf_measure_sine_rate(int device, double *sines_per_s, void *cuda_stream);
+
 /* Thread-local message describing the last non-OK return of this thread. */
 const char *sdf_last_error(void);
 

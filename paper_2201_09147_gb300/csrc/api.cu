@@ -1294,6 +1294,23 @@ int sdf_selftest_wait_timeout(int device, int64_t budget_us, void* cuda_stream) 
     return rc ? rc : fail(SDF_ERR_CUDA, "the bounded wait did not report its expiry");
 }
 
+int sdf_measure_sine_rate(int device, double* sines_per_s, void* cuda_stream) {
+    if (!sines_per_s) return fail(SDF_ERR_ARG, "sines_per_s is NULL");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return fail(SDF_ERR_ARG, "device %d not available", device);
+    }
+    DeviceGuard g(device);
+    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", device);
+    DeviceInfo di;
+    int rc = device_info(device, &di);
+    if (rc) return rc;
+    cudaError_t e = measure_sine_rate(di.num_sms, static_cast<cudaStream_t>(cuda_stream), sines_per_s);
+    if (e != cudaSuccess) return cuda_fail(e, "measuring the sine rate");
+    return SDF_OK;
+}
+
 const char* sdf_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"

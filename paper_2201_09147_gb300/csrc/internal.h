@@ -84,6 +84,8 @@ cudaError_t launch_trace_level_tc(const LevelArgs& a, int num_sms, cudaStream_t 
 cudaError_t launch_grad_tc(const GradArgs& a, int num_sms, cudaStream_t s);
 int trace_tiles_max(const NetView& net);  // largest `tiles` the tensor-core trace kernel accepts for net
 bool tc_trace_supported(int width, int n_hidden);
+// Measured throughput of the tensor-core kernels' sine on all SMs (sines per second).
+cudaError_t measure_sine_rate(int num_sms, cudaStream_t s, double* sines_per_s);
 bool tc_trace_split(int width, int n_hidden);  // head+remainder operands in the trace kernel
 bool tc_grad_supported(int width, int n_hidden);
 

@@ -1175,6 +1175,47 @@ static cudaError_t launch_grad_w(const GradArgs& a, int num_sms, cudaStream_t s)
     return launch_grad_op<W, kOpBF16>(a, num_sms, s);
 }
 
+// Sine throughput of the tensor-core kernels' sine (sin_fast): every thread
+// runs 8 independent chains x <- sin_fast(x) * c + d for `iters` steps (the
+// multiply-add keeps the chains from settling and costs an FMA-pipe slot, as
+// the kernels' own uses do).
+__global__ void __launch_bounds__(256) sine_rate_kernel(float* out, int iters) {
+    float x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = 0.1f * static_cast<float>(threadIdx.x + i);
+    for (int it = 0; it < iters; ++it)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = fmaf(sin_fast(x[i]), 1.7f, 0.3f);
+    float acc = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc += x[i];
+    if (acc == 12345.678f) out[0] = acc;  // keeps the chains live
+}
+
+cudaError_t measure_sine_rate(int num_sms, cudaStream_t s, double* sines_per_s) {
+    float* out = nullptr;
+    cudaError_t e = cudaMallocAsync(&out, 16, s);
+    if (e != cudaSuccess) return e;
+    const int blocks = num_sms * 8, iters = 4096;
+    cudaEvent_t a = nullptr, b = nullptr;
+    e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e == cudaSuccess) {
+        sine_rate_kernel<<<blocks, 256, 0, s>>>(out, iters);  // warm-up
+        cudaEventRecord(a, s);
+        sine_rate_kernel<<<blocks, 256, 0, s>>>(out, iters);
+        cudaEventRecord(b, s);
+        e = cudaEventSynchronize(b);
+    }
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess) *sines_per_s = static_cast<double>(blocks) * 256.0 * 8.0 * iters / (ms * 1e-3);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFreeAsync(out, s);
+    return e;
+}
+
 cudaError_t launch_grad_tc(const GradArgs& a, int num_sms, cudaStream_t s) {
     if (a.net.op_fp8) {
         if (a.net.width == 128) return launch_grad_op<128, kOpE4M3>(a, num_sms, s);

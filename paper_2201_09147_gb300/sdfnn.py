@@ -24,7 +24,8 @@ EXPORTS = ["sdf_net_load", "sdf_net_load_mem", "sdf_net_info", "sdf_net_set_time
            "sdf_trace_multiscale", "sdf_normals", "sdf_normal_map", "sdf_render_host", "sdf_sync_status",
            "sdf_last_error", "sdf_trace_multiscale_noalloc", "sdf_normal_map_timed", "sdf_plan_create",
            "sdf_plan_launch", "sdf_plan_info", "sdf_plan_free", "sdf_train_shape_info", "sdf_train_forward",
-           "sdf_train_backward", "sdf_fit_loss", "sdf_adam_step", "sdf_selftest_wait_timeout"]
+           "sdf_train_backward", "sdf_fit_loss", "sdf_adam_step", "sdf_selftest_wait_timeout",
+           "sdf_measure_sine_rate"]
 
 
 class SdfError(RuntimeError):
@@ -84,6 +85,7 @@ def lib():
         L.sdf_adam_step.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int,
                                     vp]
         L.sdf_selftest_wait_timeout.argtypes = [C.c_int, C.c_int64, vp]
+        L.sdf_measure_sine_rate.argtypes = [C.c_int, C.POINTER(C.c_double), vp]
         L.sdf_sync_status.argtypes = [vp]
         L.sdf_last_error.restype = C.c_char_p
         _lib = L
@@ -282,6 +284,13 @@ def render_host(nets, delta, max_iters, eps, fine: Net, orig, dirs, out_pos, out
 def selftest_wait_timeout(budget_us: int = 20000, device: int = 0, stream=None):
     """Runs the device-side timeout self-test (raises if the expiry is not reported)."""
     _check(lib().sdf_selftest_wait_timeout(device, int(budget_us), C.c_void_p(_stream(stream))))
+
+
+def measure_sine_rate(device: int = 0, stream=None) -> float:
+    """Sines per second of the kernels' hardware sine on all SMs."""
+    r = C.c_double()
+    _check(lib().sdf_measure_sine_rate(device, C.byref(r), C.c_void_p(_stream(stream))))
+    return r.value
 
 
 def sync_status(stream=None):
