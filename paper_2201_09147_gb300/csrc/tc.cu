@@ -1,29 +1,31 @@
-// Tensor-core (tcgen05) kernels of the 16-bit paths (SDF_BF16, SDF_FP16).
-// Both run tcgen05.mma.kind::f16 with FP32 accumulation in TMEM; the operand
-// type (bfloat16 or IEEE half) is a template parameter.
+// Tensor-core (tcgen05) kernels of the 16-bit and 8-bit paths (SDF_BF16,
+// SDF_FP16, SDF_FP8), FP32 accumulation in TMEM; the operand type is a
+// template parameter (tcgen05.mma.kind::f16 for bfloat16 / half,
+// kind::f8f6f4 for E4M3).
 //
 // trace_level_tc : one level of multiscale sphere tracing (Alg. 1).  A CTA
-//   holds 128 persistent ray slots, one per thread and per TMEM lane.  Each
+//   holds up to six independent tiles of 128 persistent ray slots, one per
+//   thread and per TMEM lane, sharing one copy of the weights.  Each
 //   evaluation of f (Eq. 2) runs layer 0 in FP32 on the CUDA cores, writes
-//   sin(A_0) in 16 bits into the A operand (128 rays x width, K-major,
-//   128-byte swizzle), then for every hidden layer one thread issues
-//   tcgen05.mma (M = 128 rays, N = width, K = width) against the resident
-//   16-bit weights; each thread reads its own row back with tcgen05.ld, adds
-//   the bias and applies the sine in registers.  The output layer is an FP32
-//   dot product of the last sine layer straight from TMEM, so the step
-//   t = f - d is never rounded to 16 bits.
+//   sin(A_0) in 16 bits (head and remainder) into the A operand (128 rays x
+//   width, K-major, 128-byte swizzle), then for every hidden layer one thread
+//   of the tile issues tcgen05.mma (M = 128 rays, N = width, K = width)
+//   against the resident 16-bit weights; each thread reads its own row back
+//   with tcgen05.ld, adds the bias and applies the sine in registers.  The
+//   output layer is an FP32 dot product of the last sine layer straight from
+//   TMEM, so the step t = f - d is never rounded to 16 bits.
 //
 // grad_tc : analytic gradients (Alg. 2).  Tiles of 64 points in two halves;
 //   the MMA runs with the features as rows (M = 128 per TMEM tile,
 //   width/128 tiles) and N = 128 columns = 32 points x {forward, G^x, G^y,
 //   G^z} per half, so one weight tile feeds the forward pass and the three
-//   tangents at once and the
-//   thread that owns feature m finds A_i[m] and the three G_i[m] of a point
-//   in its own TMEM lane: the epilogue P_i = sin(A_i), G_i = cos(A_i) (.)
-//   (W_i G_{i-1}) needs no data exchange.  Hidden weights stream from L2
-//   through a ring of shared-memory stages filled by bulk copies (TMA); the
-//   output layer W_n G_{n-1} is one more small MMA (rows = the 256
-//   point-streams, N = 16, w_out as a head row plus a remainder row).
+//   tangents at once and the thread that owns feature m finds A_i[m] and the
+//   three G_i[m] of a point in its own TMEM lane: the epilogue
+//   P_i = sin(A_i), G_i = cos(A_i) (.) (W_i G_{i-1}) needs no data exchange.
+//   Hidden weights stream from L2 through a ring of shared-memory stages
+//   filled by bulk copies (TMA); the output layer W_n G_{n-1} is one more
+//   small MMA (rows = the 128 point-streams of a half, N = 16, w_out as a
+//   head row plus a remainder row).
 #include <algorithm>
 #include <cstdint>
 
@@ -38,7 +40,6 @@ namespace {
 // ---------------------------------------------------------------------------
 // trace kernel
 // ---------------------------------------------------------------------------
-constexpr int kTraceThreads = 128;
 
 struct TraceLayout {
     uint32_t x, xlo, w, wlo, w0, wt, bh, wout, bars, misc, total;
@@ -658,7 +659,7 @@ __device__ __forceinline__ uint32_t sel4(uint32_t i, uint32_t a0, uint32_t a1, u
     return (i & 2u) ? hi : lo;
 }
 
-// 8-bit counterpart of store_pair for four points p0 .. p0+3 (v[q][s]: point
+// Stores into the 8-bit K-major X the four stream values of four points p0 .. p0+3 (v[q][s]: point
 // p0 + q, stream s, already scaled), exchanged within the lane quad of
 // features m0 .. m0+3 (m0 = m & ~3): lane j = m & 3 gathers point p0 + j of
 // all four features and writes its four rows as 32-bit words of features
