@@ -326,7 +326,13 @@ def main():
                          "parallelism": f"replicas x{ws}"},
               "clocks": clk, "gpu_launches": 3 * args.steps,
               "e2e": ({"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 3 * 4 * n,
-                       "d2h_bytes_per_step": (3 + 3) * 4 * n + n} if e2e_value is not None else None),
+                       "d2h_bytes_per_step": (3 + 3) * 4 * n + n,
+                       "transfer": "pinned host buffers: the trace kernel reads the rays and the normal-mapping "
+                                   "kernel writes the hits' normals in host memory over NVLink-C2C; the copy "
+                                   "engine clears the host normals during the trace and copies the end points "
+                                   "and hit flags back during the normal mapping",
+                       "timer": "host wall clock around each sdf_render_host call (returns synchronised)"}
+                      if e2e_value is not None else None),
               "roofline": roofline,
               "breakdown_ms": {"trace_coarse": tr_ms, "normal_map_fine": nm_ms, "hits": n_hit,
                                "mean_coarse_iters": total_evals / n},

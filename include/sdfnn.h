@@ -163,17 +163,23 @@ int sdf_normal_map(sdf_net_t fine, const float *pts, const uint8_t *mask, int64_
 int sdf_normal_map_timed(sdf_net_t fine, const float *pts, const float *pt_time, const uint8_t *mask, int64_t n,
                          float *out_normal, void *cuda_stream);
 
-/* One frame end to end from HOST memory: copies orig/dir to the device,
- * runs sdf_trace_multiscale and then sdf_normal_map(fine) on the hits, and
- * copies hit, end point and normal back.  Frames of 2^18 rays and more are
- * split into 2 or 4 chunks whose copies in, kernels and copies out run on
- * three streams of the library, so the transfers of one chunk overlap the
- * kernels of another (use pinned host memory for the copies to overlap).
- * Device buffers come from the library's pool on `cuda_stream`, which waits
- * for the whole frame.  orig, dir: host (3, n);
- * out_pos, out_normal: host (3, n); out_hit: host (n).  params->ray_time must
- * be NULL.  Calls on one device are serialised.  Returns after the results
- * are in host memory (the stream is synchronised).
+/* One frame end to end from HOST memory: sdf_trace_multiscale of the rays
+ * orig/dir, then sdf_normal_map(fine) on the hits; hit, end point and normal
+ * come back to host memory.  Two ways, chosen per call:
+ *   - every buffer page-locked and mapped into the device's address space
+ *     (cudaHostAlloc, cudaHostRegister, pinned torch tensors; the whole
+ *     range is checked with cudaPointerGetAttributes): the kernels read the
+ *     rays and write the normals in host memory themselves (over NVLink-C2C on
+ *     Grace systems), one trace covers all rays, and the copy engine brings
+ *     back the end points and hit flags while the normals are computed;
+ *   - otherwise: frames of 2^18 rays and more are split into 2 or 4 chunks
+ *     whose copies in, kernels and copies out run on three streams of the
+ *     library, so the transfers of one chunk overlap the kernels of another.
+ * Both give the same bytes as the device calls.  Device buffers come from
+ * the library's pool on `cuda_stream`, which waits for the whole frame.
+ * orig, dir: host (3, n); out_pos, out_normal: host (3, n); out_hit: host
+ * (n).  params->ray_time must be NULL.  Calls on one device are serialised.
+ * Returns after the results are in host memory (the stream is synchronised).
  * Errors: as sdf_trace_multiscale and sdf_normal_map. */
 int sdf_render_host(const sdf_trace_params *params, sdf_net_t fine, const float *orig, const float *dir,
                     int64_t n, float *out_pos, uint8_t *out_hit, float *out_normal, void *cuda_stream);

@@ -451,10 +451,8 @@ struct Scratch {
 
 // Checks the parameters and buffers of a trace; *dev receives the device of
 // the networks.  Device pointers are checked only when n > 0.
-int validate_trace(const sdf_trace_params* P, const float* orig, const float* dir, int64_t n, const float* out_pos,
-                   const float* out_t, const uint8_t* out_hit, const uint16_t* out_iters, int* dev_out) {
+int validate_trace_params(const sdf_trace_params* P, int* dev_out) {
     if (!P) return fail(SDF_ERR_ARG, "params is NULL");
-    if (n < 0 || n > 0x7fffffffLL) return fail(SDF_ERR_ARG, "n = %lld out of range", static_cast<long long>(n));
     const int m = P->n_levels;
     if (m < 1 || m > kMaxLevels) return fail(SDF_ERR_ARG, "n_levels = %d out of range 1..%d", m, kMaxLevels);
     if (!P->nets || !P->delta || !P->max_iters) return fail(SDF_ERR_ARG, "nets, delta and max_iters are required");
@@ -484,10 +482,19 @@ int validate_trace(const sdf_trace_params* P, const float* orig, const float* di
     }
     if (P->ray_time && P->nets[0]->in_dim != 4) return fail(SDF_ERR_ARG, "ray_time given for 3-input networks");
     *dev_out = dev;
+    return SDF_OK;
+}
+
+int validate_trace(const sdf_trace_params* P, const float* orig, const float* dir, int64_t n, const float* out_pos,
+                   const float* out_t, const uint8_t* out_hit, const uint16_t* out_iters, int* dev_out) {
+    if (!P) return fail(SDF_ERR_ARG, "params is NULL");
+    if (n < 0 || n > 0x7fffffffLL) return fail(SDF_ERR_ARG, "n = %lld out of range", static_cast<long long>(n));
+    int rc = validate_trace_params(P, dev_out);
+    if (rc) return rc;
+    const int dev = *dev_out;
     if (n == 0) return SDF_OK;
     DeviceGuard g(dev);
     if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", dev);
-    int rc;
     if ((rc = check_device_ptr(orig, dev, "orig")) || (rc = check_device_ptr(dir, dev, "dir")) ||
         (rc = check_device_ptr(out_pos, dev, "out_pos")) || (rc = check_device_ptr(out_t, dev, "out_t")) ||
         (rc = check_device_ptr(out_hit, dev, "out_hit")))
@@ -600,15 +607,18 @@ size_t grad_scratch_bytes(int64_t n, bool mask) {
     return 4 * sizeof(unsigned long long) + (mask ? static_cast<size_t>(n) * sizeof(int32_t) : 0);
 }
 
+// With a mask, the entries it excludes are zeroed in `out` by the compaction
+// kernel unless zero_unmasked is false (the caller zeroes them itself).
 int launch_gradients(sdf_net_t net, const float* pts, const float* pt_time, const uint8_t* mask, int64_t n, float* out,
-                     int normalize, void* scratch, int* status, int num_sms, cudaStream_t s) {
+                     int normalize, void* scratch, int* status, int num_sms, cudaStream_t s,
+                     bool zero_unmasked = true) {
     const size_t counter_bytes = 4 * sizeof(unsigned long long);
     cudaError_t e = cudaMemsetAsync(scratch, 0, counter_bytes, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");
     auto* counters = static_cast<unsigned long long*>(scratch);
     int32_t* list = mask ? reinterpret_cast<int32_t*>(static_cast<uint8_t*>(scratch) + counter_bytes) : nullptr;
     if (mask) {
-        e = launch_mask_compact(mask, n, list, &counters[1], out, num_sms, s);
+        e = launch_mask_compact(mask, n, list, &counters[1], zero_unmasked ? out : nullptr, num_sms, s);
         if (e != cudaSuccess) return cuda_fail(e, "launching mask compaction");
     }
     GradArgs ga{};
@@ -904,6 +914,92 @@ int host_pipe_init(HostPipe* hp) {
     return SDF_OK;
 }
 
+// Device address of [p, p + bytes) when the whole range is page-locked host
+// memory mapped into the device's address space (cudaHostAlloc,
+// cudaHostRegister, pinned torch tensors), else nullptr.
+const void* mapped_host(const void* p, size_t bytes) {
+    cudaPointerAttributes a0, a1;
+    const void* last = static_cast<const uint8_t*>(p) + (bytes - 1);
+    if (cudaPointerGetAttributes(&a0, p) != cudaSuccess || cudaPointerGetAttributes(&a1, last) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer || !a1.devicePointer)
+        return nullptr;
+    if (static_cast<const uint8_t*>(a1.devicePointer) - static_cast<const uint8_t*>(a0.devicePointer) !=
+        static_cast<ptrdiff_t>(bytes - 1))
+        return nullptr;
+    return a0.devicePointer;
+}
+
+// sdf_render_host with mapped host buffers: one trace over all rays (level 0
+// reads orig / dir from host memory), then on one stream the normal mapping
+// (writing the hits' normals to host memory) and on another the copy of the
+// end points and hit flags.  orig, dir and nrm are device addresses of host
+// memory (nrm that of out_normal_host).
+int render_mapped(const sdf_trace_params* params, sdf_net_t fine, const float* orig, const float* dir, int64_t n,
+                  float* out_pos, uint8_t* out_hit, float* out_normal_host, float* nrm, HostPipe& hp, cudaStream_t s) {
+    int dev = -1;
+    int rc = validate_trace_params(params, &dev);
+    if (rc) return rc;
+    if (fine->precision != SDF_FP32 && !tc_grad_supported(fine->width, fine->n_hidden))
+        return fail(SDF_ERR_UNSUPPORTED, "tensor-core gradients of a (%d,%d) network are not built", fine->width,
+                    fine->n_hidden);
+    DeviceInfo di;
+    if ((rc = device_info(dev, &di))) return rc;
+    const size_t un = static_cast<size_t>(n);
+    const size_t ts = (trace_scratch_bytes(params->n_levels, n) + 255) & ~size_t(255);
+    const size_t gs = (grad_scratch_bytes(n, true) + 255) & ~size_t(255);
+    const size_t fb = (4 * un * sizeof(float) + un + 255) & ~size_t(255);  // pos (3n), t (n), hit (n)
+    const size_t zb = 3 * un * sizeof(float);                               // zeros for the normals
+    void* block = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&block, ts + gs + fb + zb, di.pool, s);
+    if (e != cudaSuccess) return cuda_fail(e, "allocating the frame buffers");
+    uint8_t* b = static_cast<uint8_t*>(block);
+    float* d_pos = reinterpret_cast<float*>(b + ts + gs);
+    float* d_t = d_pos + 3 * un;
+    uint8_t* d_hit = reinterpret_cast<uint8_t*>(d_t + un);
+    void* d_zero = b + ts + gs + fb;
+    cudaStream_t c = hp.cmp[0];
+    if ((e = cudaEventRecord(hp.start, s)) == cudaSuccess && (e = cudaStreamWaitEvent(c, hp.start, 0)) == cudaSuccess &&
+        (e = cudaStreamWaitEvent(hp.in, hp.start, 0)) == cudaSuccess &&
+        (e = cudaStreamWaitEvent(hp.out, hp.start, 0)) == cudaSuccess &&
+        // while the rays are traced, the copy engine clears the host normals
+        // (the normal mapping then writes the hits' entries only)
+        (e = cudaMemsetAsync(d_zero, 0, zb, hp.in)) == cudaSuccess &&
+        (e = cudaMemcpyAsync(out_normal_host, d_zero, zb, cudaMemcpyDeviceToHost, hp.in)) == cudaSuccess &&
+        (e = cudaEventRecord(hp.ev_cmp[1], hp.in)) == cudaSuccess) {
+        rc = launch_levels(params, orig, dir, n, d_pos, d_t, d_hit, nullptr, b, di.d_status, di.num_sms, nullptr, c);
+        // then the normals of the hits on c, and the end points and hit flags
+        // copied back on `out` meanwhile
+        if (rc == SDF_OK && (e = cudaEventRecord(hp.ev_in[0], c)) == cudaSuccess &&
+            (e = cudaStreamWaitEvent(hp.out, hp.ev_in[0], 0)) == cudaSuccess &&
+            (e = cudaMemcpyAsync(out_pos, d_pos, 3 * un * sizeof(float), cudaMemcpyDeviceToHost, hp.out)) ==
+                cudaSuccess &&
+            (e = cudaMemcpyAsync(out_hit, d_hit, un, cudaMemcpyDeviceToHost, hp.out)) == cudaSuccess &&
+            (e = cudaStreamWaitEvent(c, hp.ev_cmp[1], 0)) == cudaSuccess)
+            rc = launch_gradients(fine, d_pos, nullptr, d_hit, n, nrm, 1, b + ts, di.d_status, di.num_sms, c, false);
+    }
+    cudaError_t e2 = cudaEventRecord(hp.ev_cmp[0], c);
+    if (e2 == cudaSuccess) e2 = cudaEventRecord(hp.ev_cmp[1], hp.in);
+    if (e2 == cudaSuccess) e2 = cudaEventRecord(hp.done, hp.out);
+    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, hp.ev_cmp[0], 0);
+    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, hp.ev_cmp[1], 0);
+    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, hp.done, 0);
+    if (e2 != cudaSuccess) {
+        cudaStreamSynchronize(c);
+        cudaStreamSynchronize(hp.in);
+        cudaStreamSynchronize(hp.out);
+    }
+    cudaFreeAsync(block, s);
+    const cudaError_t e3 = cudaStreamSynchronize(s);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "enqueueing the frame");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "ordering the frame's streams");
+    if (e3 != cudaSuccess) return cuda_fail(e3, "cudaStreamSynchronize");
+    return SDF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -986,6 +1082,16 @@ int sdf_render_host(const sdf_trace_params* params, sdf_net_t fine, const float*
     int rc = host_pipe_init(&hp);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+
+    // Page-locked host buffers that the device maps: the kernels read the rays
+    // and write the normals over the host link themselves, the copy engine
+    // brings back the end points and hit flags while the normals are computed.
+    const size_t b3 = 3 * static_cast<size_t>(n) * sizeof(float), b1 = static_cast<size_t>(n);
+    const float* m_orig = static_cast<const float*>(mapped_host(orig, b3));
+    const float* m_dir = static_cast<const float*>(mapped_host(dir, b3));
+    float* m_nrm = static_cast<float*>(const_cast<void*>(mapped_host(out_normal, b3)));
+    if (m_orig && m_dir && m_nrm && mapped_host(out_pos, b3) && mapped_host(out_hit, b1))
+        return render_mapped(params, fine, m_orig, m_dir, n, out_pos, out_hit, out_normal, m_nrm, hp, s);
 
     // chunks of rays: the copies of one chunk overlap the kernels of another
     const int nch = n >= (int64_t(1) << 20) ? kHostChunks : (n >= (int64_t(1) << 18) ? 2 : 1);

@@ -138,7 +138,8 @@ cudaError_t launch_adam(float* theta, const float* grad, float* m, float* v, int
 cudaError_t launch_wait_timeout_selftest(int* status, unsigned long long budget_ns, cudaStream_t s);
 
 // Builds list[] of the indices with mask[i] != 0 (order unspecified), zeroes
-// out[.][i] where mask[i] == 0, and counts into *count (zero at launch).
+// out[.][i] where mask[i] == 0 (out may be NULL: nothing is zeroed), and
+// counts into *count (zero at launch).
 cudaError_t launch_mask_compact(const uint8_t* mask, int64_t n, int32_t* list, unsigned long long* count,
                                 float* out, int num_sms, cudaStream_t s);
 

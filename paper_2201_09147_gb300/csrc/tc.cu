@@ -227,12 +227,17 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
             pass_ray(a, ray);
             continue;
         }
-        // layer 0 (FP32): row ttid of X = 16-bit sin(W_0 (p, t) + b_0); an empty
-        // slot writes a row from its stale (finite) state, which nothing reads
-        if (timed)
-            trace_layer0<W, F16, SPLIT, true>(a, w0s, wts, ray, ttid, x_s, xlo_s);
-        else
-            trace_layer0<W, F16, SPLIT, false>(a, w0s, wts, ray, ttid, x_s, xlo_s);
+        // layer 0 (FP32): row ttid of X = 16-bit sin(W_0 (p, t) + b_0).  A warp
+        // with no active slot skips its rows and their epilogues: its 32 rows of
+        // X keep stale values, and an MMA row depends on its own A row only
+        // (what matters at the end of the work list, when tiles thin out).
+        const bool wact = __any_sync(0xffffffffu, ray.state == kSlotActive);
+        if (wact) {
+            if (timed)
+                trace_layer0<W, F16, SPLIT, true>(a, w0s, wts, ray, ttid, x_s, xlo_s);
+            else
+                trace_layer0<W, F16, SPLIT, false>(a, w0s, wts, ray, ttid, x_s, xlo_s);
+        }
         fence_proxy_async_smem();
         tc_fence_before();
         // one barrier: X is complete, and the tile stops when no slot is active
@@ -264,7 +269,7 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
             const float* bl = bhs + l * W;
             if (l + 1 < KH) {
                 // hidden epilogue: X row = 16-bit sin(D + b)
-                for (int c0 = 0; c0 < W; c0 += 32) {
+                for (int c0 = 0; c0 < W && wact; c0 += 32) {
                     float v[32];
                     tmem_ld32(tmem + lane_base + c0, v);
                     tmem_wait_ld();
@@ -294,7 +299,7 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
             } else {
                 // output layer in FP32: f = w_out . sin(D + b) + b_out
                 float dot = 0.0f;
-                for (int c0 = 0; c0 < W; c0 += 32) {
+                for (int c0 = 0; c0 < W && wact; c0 += 32) {
                     float v[32];
                     tmem_ld32(tmem + lane_base + c0, v);
                     tmem_wait_ld();
@@ -461,10 +466,14 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
                 pass_ray(a, ray);
                 continue;
             }
-            if (timed)
-                trace_layer0<W, F16, false, true>(a, w0s, wts, ray, tid, x_s, x_s);
-            else
-                trace_layer0<W, F16, false, false>(a, w0s, wts, ray, tid, x_s, x_s);
+            // a warp with no active slot skips its rows (as in trace_level_tc_kernel)
+            const bool wact = __any_sync(0xffffffffu, ray.state == kSlotActive);
+            if (wact) {
+                if (timed)
+                    trace_layer0<W, F16, false, true>(a, w0s, wts, ray, tid, x_s, x_s);
+                else
+                    trace_layer0<W, F16, false, false>(a, w0s, wts, ray, tid, x_s, x_s);
+            }
             fence_proxy_async_smem();
             tc_fence_before();
             if (!bar_or(1, 128, ray.state == kSlotActive)) break;
@@ -493,7 +502,7 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
                 tc_fence_after();
                 const float* bl = bhs + l * W;
                 if (l + 1 < KH) {
-                    for (int c0 = 0; c0 < W; c0 += 32) {
+                    for (int c0 = 0; c0 < W && wact; c0 += 32) {
                         float v[32];
                         tmem_ld32(tmem + lane_base + c0, v);
                         tmem_wait_ld();
@@ -517,7 +526,7 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
                     bar_named(1, 128);
                 } else {
                     float dot = 0.0f;
-                    for (int c0 = 0; c0 < W; c0 += 32) {
+                    for (int c0 = 0; c0 < W && wact; c0 += 32) {
                         float v[32];
                         tmem_ld32(tmem + lane_base + c0, v);
                         tmem_wait_ld();

@@ -389,20 +389,36 @@ def test_edge_cases(sdf):
     sdf.sync_status()
 
 
+@pytest.mark.parametrize("memory", ["pinned", "pageable", "mixed"])
 @pytest.mark.parametrize("size", [(160, 90), (640, 480), (1920, 1080)], ids=["1chunk", "2chunks", "4chunks"])
-def test_render_host_matches_device(sdf, size):
-    """The host-buffer frame (chunked, copies overlapping the kernels) equals the device calls bit for bit."""
+def test_render_host_matches_device(sdf, size, memory):
+    """The host-buffer frame equals the device calls bit for bit: with page-locked buffers the kernels
+    read the rays and write the normals in host memory directly; otherwise (pageable, or any one buffer
+    pageable) the frame goes through the chunked copy pipeline."""
     wl = workloads.get("normal_map_1080p", *size)
+    _render_host_vs_device(sdf, wl, memory)
+
+
+@pytest.mark.parametrize("memory", ["pinned", "pageable"])
+def test_render_host_three_levels(sdf, memory):
+    """Three levels through sdf_render_host: later levels re-read the directions through the ray queues."""
+    _render_host_vs_device(sdf, workloads.get("three_level_512"), memory)
+
+
+def _render_host_vs_device(sdf, wl, memory):
     orig, dirs = wl.rays()
     nets = [sdf.Net(b, sdf.SDF_BF16) for b in wl.level_bytes()]
     fine = sdf.Net(wl.fine_bytes(), sdf.SDF_BF16)
     n = orig.shape[1]
-    hp = torch.full((3, n), float("nan")).pin_memory()
-    hh = torch.full((n,), 7, dtype=torch.uint8).pin_memory()
-    hn = torch.full((3, n), float("nan")).pin_memory()
-    sdf.render_host(nets, wl.delta, wl.caps, wl.eps, fine, torch.from_numpy(orig).pin_memory(),
-                    torch.from_numpy(dirs).pin_memory(), hp, hh, hn, step_scale=wl.step_scale,
-                    final_mode=wl.final_mode)
+    pin = (lambda t: t.pin_memory()) if memory == "pinned" else (lambda t: t)
+    hp = pin(torch.full((3, n), float("nan")))
+    hh = pin(torch.full((n,), 7, dtype=torch.uint8))
+    hn = torch.full((3, n), float("nan"))
+    hn = hn if memory == "mixed" else pin(hn)
+    ho = torch.from_numpy(orig)
+    ho = ho.pin_memory() if memory in ("pinned", "mixed") else ho
+    sdf.render_host(nets, wl.delta, wl.caps, wl.eps, fine, ho, pin(torch.from_numpy(dirs)), hp, hh, hn,
+                    step_scale=wl.step_scale, final_mode=wl.final_mode)
     o = torch.from_numpy(orig).cuda()
     d = torch.from_numpy(dirs).cuda()
     pos, _, hit, _ = sdf.trace_multiscale(nets, wl.delta, wl.caps, wl.eps, o, d, step_scale=wl.step_scale,
