@@ -212,6 +212,12 @@ __device__ __forceinline__ uint64_t desc_mnmajor_sw128(uint32_t smem_addr, uint3
     d |= static_cast<uint64_t>(2u) << 61;
     return d;
 }
+// The descriptor of an operand `bytes` further on (a multiple of 16): the
+// start address field holds address >> 4 in 14 bits and shared memory ends
+// below 256 KB, so the field never carries into the next one.
+__device__ __forceinline__ uint64_t desc_add(uint64_t desc, uint32_t bytes) {
+    return desc + static_cast<uint64_t>(bytes >> 4);
+}
 constexpr uint32_t kIdescMajorMnA = 1u << 15;
 constexpr uint32_t kIdescMajorMnB = 1u << 16;
 
@@ -312,6 +318,13 @@ __host__ __device__ __forceinline__ uint32_t sw128_chunk_offset(uint32_t row, ui
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
     asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
+
+// 4-byte asynchronous copy global -> shared (no register staging), and the
+// wait for all of this thread's outstanding ones.
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ void st_shared_u32(uint32_t addr, uint32_t v) {
     asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");

@@ -247,17 +247,17 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
         for (int l = 0; l < KH; ++l) {
             if (ttid == 0) {
                 tc_fence_after();
-                const uint32_t wl = w_s + l * W * W * 2u, wll = wlo_s + l * W * W * 2u;
+                const uint64_t xd0 = desc_kmajor_sw128(x_s), xld0 = desc_kmajor_sw128(xlo_s);
+                const uint64_t wd0 = desc_kmajor_sw128(w_s + l * W * W * 2u), wld0 = desc_kmajor_sw128(wlo_s + l * W * W * 2u);
 #pragma unroll
                 for (int kb = 0; kb < W / 64; ++kb)
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
                         const uint32_t xo = kb * 128u * 128u + kk * 32u, wo = kb * W * 128u + kk * 32u;
-                        mma_f16kind(tmem, desc_kmajor_sw128(x_s + xo), desc_kmajor_sw128(wl + wo), idesc,
-                                    (kb | kk) != 0);
+                        mma_f16kind(tmem, desc_add(xd0, xo), desc_add(wd0, wo), idesc, (kb | kk) != 0);
                         if (SPLIT) {
-                            mma_f16kind(tmem, desc_kmajor_sw128(x_s + xo), desc_kmajor_sw128(wll + wo), idesc, 1u);
-                            mma_f16kind(tmem, desc_kmajor_sw128(xlo_s + xo), desc_kmajor_sw128(wl + wo), idesc, 1u);
+                            mma_f16kind(tmem, desc_add(xd0, xo), desc_add(wld0, wo), idesc, 1u);
+                            mma_f16kind(tmem, desc_add(xld0, xo), desc_add(wd0, wo), idesc, 1u);
                         }
                     }
                 mma_commit(bar_mma);
@@ -456,6 +456,7 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
         const long long n_work = a.in_list ? static_cast<long long>(*a.in_count) : a.n;
         const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
         constexpr uint32_t idesc = idesc_f32acc(128, W, F16);
+        const uint64_t xd0 = desc_kmajor_sw128(x_s), rd0 = desc_kmajor_sw128(ring_s);
         uint32_t mma_phase = 0, g = 0;
         bool ok = true;
         Ray ray;
@@ -489,9 +490,8 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
                         tc_fence_after();
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)
-                            mma_f16kind(tmem, desc_kmajor_sw128(x_s + kb * 128u * 128u + kk * 32u),
-                                        desc_kmajor_sw128(ring_s + stage * kStreamStageBytes + kk * 32u), idesc,
-                                        (kb | kk) != 0);
+                            mma_f16kind(tmem, desc_add(xd0, kb * 128u * 128u + kk * 32u),
+                                        desc_add(rd0, stage * kStreamStageBytes + kk * 32u), idesc, (kb | kk) != 0);
                         mma_commit(bar_empty + 8u * stage);
                     }
                     if (ok) mma_commit(bar_mma);
@@ -622,7 +622,7 @@ struct GradCfg {
 };
 
 struct GradLayout {
-    uint32_t x, ring, woutb, w0, wt, pts, idx, bars, misc, total;
+    uint32_t x, ring, woutb, w0, wt, pts, idx, nidx, bars, misc, total;
 };
 
 template <int W, int OP>
@@ -643,6 +643,8 @@ __host__ __device__ inline GradLayout grad_layout(int KH) {
     L.pts = o;
     o += C::NPTS * 4u * 4u;
     L.idx = o;
+    o += C::NPTS * 4u;
+    L.nidx = o;
     o += C::NPTS * 4u;
     L.bars = o;
     o += (2 * C::NS + 4) * 8u;
@@ -708,6 +710,47 @@ __device__ __forceinline__ void mma_op(uint32_t d, uint64_t a, uint64_t b, uint3
         mma_f16kind(d, a, b, idesc, acc);
 }
 
+// Index of point j (j < 0: none) of half h of pair i of this CTA (-1 past the
+// work), and its coordinates (zero for -1).
+template <int HPTS>
+__device__ __forceinline__ int grad_point_index(const GradArgs& a, long long n_work, int cta, int h, int j,
+                                                long long i) {
+    const long long k = ((i * gridDim.x + cta) * 2 + h) * HPTS + j;
+    if (j < 0 || k >= n_work) return -1;
+    return a.list ? a.list[k] : static_cast<int>(k);
+}
+// The same index written to the int at shared address dst: copied there
+// asynchronously when it comes from the list (complete after
+// cp_async_wait_all in the same thread).
+template <int HPTS>
+__device__ __forceinline__ void grad_point_index_async(uint32_t dst, const GradArgs& a, long long n_work, int cta,
+                                                       int h, int j, long long i) {
+    const long long k = ((i * gridDim.x + cta) * 2 + h) * HPTS + j;
+    if (j < 0 || k >= n_work)
+        st_shared_u32(dst, 0xFFFFFFFFu);
+    else if (a.list)
+        cp_async4(dst, a.list + k);
+    else
+        st_shared_u32(dst, static_cast<uint32_t>(k));
+}
+
+// Copies (x, y, z, t) of point idx into the float4 at shared address dst
+// with asynchronous 4-byte copies (zeros for idx < 0); complete after
+// cp_async_wait_all in the same thread.
+__device__ __forceinline__ void grad_point_async(uint32_t dst, const GradArgs& a, bool timed, int idx) {
+    if (idx < 0) {
+        st_shared_v4(dst, 0u, 0u, 0u, 0u);
+        return;
+    }
+    cp_async4(dst, a.pts + idx);
+    cp_async4(dst + 4u, a.pts + a.n + idx);
+    cp_async4(dst + 8u, a.pts + 2 * a.n + idx);
+    if (timed)
+        cp_async4(dst + 12u, a.pt_time + idx);
+    else
+        st_shared_u32(dst + 12u, 0u);
+}
+
 template <int W, int OP>
 __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const GradArgs a) {
     using C = GradCfg<W, OP>;
@@ -724,6 +767,7 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
     float* wts = reinterpret_cast<float*>(base + L.wt);
     float4* pts = reinterpret_cast<float4*>(base + L.pts);  // (x, y, z, t) per point
     int* idxs = reinterpret_cast<int*>(base + L.idx);
+    int* nidxs = reinterpret_cast<int*>(base + L.nidx);  // indices of the next pair's points
     const uint32_t bar_full = base_s + L.bars;             // NS barriers
     const uint32_t bar_empty = bar_full + 8u * C::NS;      // NS barriers
     const uint32_t bar_xready = bar_empty + 8u * C::NS;    // 2 barriers (one per half)
@@ -874,16 +918,24 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
         const float sf = FP8 ? kFp8ActScale : 1.0f;
         const float g0s = FP8 ? net.q_g[0] : 1.0f;
         uint32_t df_phase = 0;
+        // Point gt of this half in pair i (threads gt < HPTS): its index is
+        // loaded a pair ahead and its coordinates during the pair before, so
+        // neither global load sits between two pairs.
+        // Point gt < HPTS of this half: its index is copied into shared memory
+        // at the start of the pair before, its coordinates once that pair's
+        // input layer has read the current ones, so no global load sits
+        // between two pairs.
+        if (gt < C::HPTS) {
+            const int idx = grad_point_index<C::HPTS>(a, n_work, blockIdx.x, h, my_pairs > 0 ? gt : -1, 0);
+            nidxs[p0 + gt] = idx;
+            grad_point_async(base_s + L.pts + static_cast<uint32_t>(p0 + gt) * 16u, a, timed, idx);
+        }
         for (long long i = 0; i < my_pairs; ++i) {
-            const long long base_pt = ((i * G + blockIdx.x) * 2 + h) * C::HPTS;
             if (gt < C::HPTS) {
-                const long long k = base_pt + gt;
-                int idx = -1;
-                if (k < n_work) idx = a.list ? a.list[k] : static_cast<int>(k);
-                idxs[p0 + gt] = idx;
-                pts[p0 + gt] = idx >= 0 ? make_float4(a.pts[idx], a.pts[a.n + idx], a.pts[2 * a.n + idx],
-                                                      timed ? a.pt_time[idx] : 0.0f)
-                                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                cp_async_wait_all();
+                idxs[p0 + gt] = nidxs[p0 + gt];
+                grad_point_index_async<C::HPTS>(base_s + L.nidx + static_cast<uint32_t>(p0 + gt) * 4u, a, n_work,
+                                                blockIdx.x, h, i + 1 < my_pairs ? gt : -1, i + 1);
             }
             bar_named(1 + h, C::GROUP_THREADS);
             // input layer: P_0 = sin(A_0), G_0^c = W_0[:, c] (.) cos(A_0); the time
@@ -930,6 +982,12 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
                 ok = mbar_wait_bounded(bar_dfull + 8u * h, df_phase, a.status, abort_flag);
                 df_phase ^= 1u;
                 if (!ok) break;
+                // every thread of the group has read this pair's points by now (the
+                // MMA that produced D waited for all of them)
+                if (l == 0 && gt < C::HPTS) {
+                    cp_async_wait_all();  // the index copied at the top of the pair
+                    grad_point_async(base_s + L.pts + static_cast<uint32_t>(p0 + gt) * 16u, a, timed, nidxs[p0 + gt]);
+                }
                 tc_fence_after();
                 const float bb = live ? __ldg(net.bh[l] + m) : 0.0f;  // one load per layer and half-tile
                 // accumulator -> value multipliers of the sine and tangent streams, and the
@@ -1020,6 +1078,7 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
             // the OR-barrier also makes the stop decision uniform over the group
             if (bar_or(1 + h, C::GROUP_THREADS, !ok || *abort_flag != 0)) break;
         }
+        if (gt < C::HPTS) cp_async_wait_all();
     }
 
     tc_fence_before();
