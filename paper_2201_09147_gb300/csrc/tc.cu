@@ -820,33 +820,47 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
     // Static schedule: half-tiles of 32 points; CTA b takes the pairs b, b + G,
     // b + 2G, ... (G = grid size) and half h of each pair is half-tile
     // 2 * pair + h.  Both halves run the same number of pairs, so the MMA warp
-    // and the producer can follow a fixed alternation h0, h1 per layer; a
-    // half-tile beyond the work is computed with no valid points.
+    // and the producer can follow the fixed schedule of grad_slot; a half-tile
+    // beyond the work is computed with no valid points.
     const long long n_work = a.list ? static_cast<long long>(*a.count) : a.n;
     const long long n_pairs = (n_work + 2 * C::HPTS - 1) / (2 * C::HPTS);
     const long long G = gridDim.x;
     const long long my_pairs = n_pairs > blockIdx.x ? (n_pairs - blockIdx.x + G - 1) / G : 0;
+    // MMA schedule: each half runs n_groups groups in order (per pair: the KH
+    // hidden layers, then the output layer).  With 16-bit operands half 1 runs
+    // one group behind half 0 (LAG = 1):
+    //   h0.G0 | h0.G1 h1.G0 | h0.G2 h1.G1 | ... | h1.G(n-1),
+    // so the short output-layer group of one half sits between hidden-layer
+    // groups of the other, which cover that half's last epilogue and its next
+    // input layer.  E4M3 MMAs take half as long as the epilogues they
+    // alternate with, and there the halves run in step (LAG = 0: h0.Gk h1.Gk),
+    // which measured faster.  The producer streams the weights in the same order.
+    constexpr int LAG = FP8 ? 0 : 1;
+    const int n_groups = static_cast<int>(my_pairs) * (KH + 1);
     bool ok = true;
 
     if (warp == C::PRODUCER_WARP) {
         if (lane == 0) {
-            // stages in MMA order: per pair, per layer, per half, stage of the layer
+            // stages in MMA order: per slot of the schedule, the stages of its layer
             // (K blocks SKB * sg .. of every TMEM tile: contiguous in the weight image)
-            const int per_layer = 2 * C::STAGES_PER_LAYER;
-            const long long total = my_pairs * KH * per_layer;
             uint32_t g = 0;
-            for (long long st = 0; st < total && ok; ++st, ++g) {
-                const uint32_t stage = g % C::NS, use = g / C::NS;
-                if (use > 0) ok = mbar_wait_bounded(bar_empty + 8u * stage, (use - 1) & 1u, a.status, abort_flag);
-                if (!ok) break;
-                const int sl = static_cast<int>(st % (KH * per_layer));
-                const int l = sl / per_layer, sg = sl % C::STAGES_PER_LAYER;
-                mbar_arrive_expect_tx(bar_full + 8u * stage, C::STAGE_BYTES);
-                bulk_g2s(ring_s + stage * C::STAGE_BYTES,
-                         net.wbf + static_cast<size_t>(l) * net.wbf_layer_bytes +
-                             static_cast<size_t>(sg) * C::STAGE_BYTES,
-                         C::STAGE_BYTES, bar_full + 8u * stage);
-            }
+            for (int k = 0; k < n_groups + LAG && ok; ++k)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int grp = k - h * LAG;
+                    if (grp < 0 || grp >= n_groups) continue;
+                    const int l = grp % (KH + 1);
+                    for (int sg = 0; sg < C::STAGES_PER_LAYER && l < KH && ok; ++sg, ++g) {
+                        const uint32_t stage = g % C::NS, use = g / C::NS;
+                        if (use > 0) ok = mbar_wait_bounded(bar_empty + 8u * stage, (use - 1) & 1u, a.status, abort_flag);
+                        if (!ok) break;
+                        mbar_arrive_expect_tx(bar_full + 8u * stage, C::STAGE_BYTES);
+                        bulk_g2s(ring_s + stage * C::STAGE_BYTES,
+                                 net.wbf + static_cast<size_t>(l) * net.wbf_layer_bytes +
+                                     static_cast<size_t>(sg) * C::STAGE_BYTES,
+                                 C::STAGE_BYTES, bar_full + 8u * stage);
+                    }
+                }
         }
     } else if (warp == C::MMA_WARP) {
         if (lane == 0) {
@@ -854,56 +868,57 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
             constexpr uint32_t idesc_h = idesc_f32acc(128, C::HROWS, F16 || FP8) | (FP8 ? 0u : kIdescMajorMnB);
             constexpr uint32_t idesc_o = idesc_f32acc(128, 16, F16 || FP8) | (FP8 ? 0u : kIdescMajorMnA);
             uint32_t g = 0, xr_phase[2] = {0u, 0u};
-            for (long long i = 0; i < my_pairs && ok; ++i) {
-                for (int l = 0; l <= KH && ok; ++l) {
-                    for (int h = 0; h < 2 && ok; ++h) {
-                        ok = mbar_wait_bounded(bar_xready + 8u * h, xr_phase[h], a.status, abort_flag);
-                        xr_phase[h] ^= 1u;
-                        if (!ok) break;
-                        tc_fence_after();
-                        // X of this half: K-major rows (E4M3), or the MN-major half block (16-bit)
-                        const uint32_t xh = FP8 ? x_s + h * C::HROWS * 128u : x_s + h * (W * 256u);
-                        if (l < KH) {
-                            // D[mt][h] = W_l[mt rows] . X_h^T over all K blocks
-                            for (int sg = 0; sg < C::STAGES_PER_LAYER && ok; ++sg, ++g) {
-                                const uint32_t stage = g % C::NS, use = g / C::NS;
-                                ok = mbar_wait_bounded(bar_full + 8u * stage, use & 1u, a.status, abort_flag);
-                                if (!ok) break;
-                                tc_fence_after();
+            for (int k = 0; k < n_groups + LAG && ok; ++k)
 #pragma unroll
-                                for (int kr = 0; kr < C::SKB; ++kr) {
-                                    const int kb = sg * C::SKB + kr;
+                for (int h = 0; h < 2 && ok; ++h) {
+                    const int grp = k - h * LAG;
+                    if (grp < 0 || grp >= n_groups) continue;
+                    const int l = grp % (KH + 1);
+                    ok = mbar_wait_bounded(bar_xready + 8u * h, xr_phase[h], a.status, abort_flag);
+                    xr_phase[h] ^= 1u;
+                    if (!ok) break;
+                    tc_fence_after();
+                    // X of this half: K-major rows (E4M3), or the MN-major half block (16-bit)
+                    const uint32_t xh = FP8 ? x_s + h * C::HROWS * 128u : x_s + h * (W * 256u);
+                    if (l < KH) {
+                        // D[mt][h] = W_l[mt rows] . X_h^T over all K blocks
+                        for (int sg = 0; sg < C::STAGES_PER_LAYER && ok; ++sg, ++g) {
+                            const uint32_t stage = g % C::NS, use = g / C::NS;
+                            ok = mbar_wait_bounded(bar_full + 8u * stage, use & 1u, a.status, abort_flag);
+                            if (!ok) break;
+                            tc_fence_after();
 #pragma unroll
-                                    for (int mt = 0; mt < C::MT; ++mt)
+                            for (int kr = 0; kr < C::SKB; ++kr) {
+                                const int kb = sg * C::SKB + kr;
 #pragma unroll
-                                        for (int kk = 0; kk < 4; ++kk) {
-                                            const uint64_t xd =
-                                                FP8 ? desc_kmajor_sw128(xh + kb * C::NROWS * 128u + kk * 32u)
-                                                    : desc_mnmajor_sw128(xh + (kb * 8 + kk * 2) * 1024u, W * 128u);
-                                            const uint32_t wa =
-                                                ring_s + stage * C::STAGE_BYTES + (kr * C::MT + mt) * 16384u + kk * 32u;
-                                            mma_op<OP>(tmem + mt * 256u + h * 128u, desc_kmajor_sw128(wa), xd, idesc_h,
-                                                       (kb | kk) != 0);
-                                        }
-                                }
-                                mma_commit(bar_empty + 8u * stage);
+                                for (int mt = 0; mt < C::MT; ++mt)
+#pragma unroll
+                                    for (int kk = 0; kk < 4; ++kk) {
+                                        const uint64_t xd =
+                                            FP8 ? desc_kmajor_sw128(xh + kb * C::NROWS * 128u + kk * 32u)
+                                                : desc_mnmajor_sw128(xh + (kb * 8 + kk * 2) * 1024u, W * 128u);
+                                        const uint32_t wa =
+                                            ring_s + stage * C::STAGE_BYTES + (kr * C::MT + mt) * 16384u + kk * 32u;
+                                        mma_op<OP>(tmem + mt * 256u + h * 128u, desc_kmajor_sw128(wa), xd, idesc_h,
+                                                   (kb | kk) != 0);
+                                    }
                             }
-                        } else {
-                            // output layer of this half: rows = its 128 point-streams, N = 16 (w_out head, remainder)
-                            for (int kb = 0; kb < C::KB; ++kb)
-#pragma unroll
-                                for (int kk = 0; kk < 4; ++kk) {
-                                    const uint64_t xd =
-                                        FP8 ? desc_kmajor_sw128(xh + kb * C::NROWS * 128u + kk * 32u)
-                                            : desc_mnmajor_sw128(xh + (kb * 8 + kk * 2) * 1024u, W * 128u);
-                                    mma_op<OP>(tmem + h * 128u, xd, desc_kmajor_sw128(wo_s + kb * 16u * 128u + kk * 32u),
-                                               idesc_o, (kb | kk) != 0);
-                                }
+                            mma_commit(bar_empty + 8u * stage);
                         }
-                        if (ok) mma_commit(bar_dfull + 8u * h);
+                    } else {
+                        // output layer of this half: rows = its 128 point-streams, N = 16 (w_out head, remainder)
+                        for (int kb = 0; kb < C::KB; ++kb)
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint64_t xd =
+                                    FP8 ? desc_kmajor_sw128(xh + kb * C::NROWS * 128u + kk * 32u)
+                                        : desc_mnmajor_sw128(xh + (kb * 8 + kk * 2) * 1024u, W * 128u);
+                                mma_op<OP>(tmem + h * 128u, xd, desc_kmajor_sw128(wo_s + kb * 16u * 128u + kk * 32u),
+                                           idesc_o, (kb | kk) != 0);
+                            }
                     }
+                    if (ok) mma_commit(bar_dfull + 8u * h);
                 }
-            }
         }
     } else {
         // epilogue group h: thread <-> feature row m of TMEM tile mt, points 32h .. 32h+31 of X
