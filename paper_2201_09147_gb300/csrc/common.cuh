@@ -152,6 +152,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     }
 }
 
+// Wait for a bulk copy issued by this block to land before the block exits,
+// whatever the abort flag says (a copy from valid global memory always
+// completes); bounded by kWaitBudgetNs like every other wait.
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return;
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait_sleep(bar, parity, kWaitSleepNs))
+        if (globaltimer_ns() - t0 > kWaitBudgetNs) return;
+}
+
 // ---------------------------------------------------------------------------
 // bulk copy (TMA, non-tensor): global -> shared, completes on an mbarrier
 // ---------------------------------------------------------------------------

@@ -79,6 +79,7 @@ __host__ __device__ inline TraceLayout trace_layout(int W, int KH, bool split, i
 }
 
 constexpr uint32_t kSplitSmemLimit = 200u * 1024u;
+constexpr int kTailRound = 4;  // trace iterations between two regroupings of the tail's rays
 constexpr int kMaxTraceTiles = 6;
 constexpr int kTraceMaxThreads = 128 * kMaxTraceTiles;
 
@@ -185,6 +186,7 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
         mbar_init(bar_w, 1);
         for (int t = 0; t < T; ++t) mbar_init(base_s + L.bars + 8u * (1 + t), 1);
         *abort_flag = 0;
+        *reinterpret_cast<uint32_t*>(base + L.misc + 16) = 0u;  // tail round counter
         fence_mbar_init();
     }
     if (warp == 0) {
@@ -211,7 +213,8 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
                 if (SPLIT) bulk_g2s(wlo_s + l * W * W * 2u + kb * W * 128u, net.wbf_lo + src, W * 128u, bar_w);
             }
     }
-    bool ok = mbar_wait_bounded(bar_w, 0, a.status, abort_flag);
+    // the weights are in, or the whole block gives up (one decision for all threads)
+    const bool ok = __syncthreads_and(mbar_wait_bounded(bar_w, 0, a.status, abort_flag) ? 1 : 0) != 0;
 
     const long long n_work = a.in_list ? static_cast<long long>(*a.in_count) : a.n;
     const uint32_t lane_base = static_cast<uint32_t>(twarp * 32) << 16;
@@ -220,105 +223,176 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
     const int bar_id = 1 + tile;
     Ray ray;
 
-    while (ok) {
-        refill_ray(a, ray, n_work);
-        if (a.cap <= 0) {
+    if (ok && a.cap <= 0) {
+        // a level with no iterations passes its rays on unchanged
+        while (true) {
+            refill_ray(a, ray, n_work);
             if (!bar_or(bar_id, 128, ray.state == kSlotActive)) break;
             pass_ray(a, ray);
-            continue;
         }
-        // layer 0 (FP32): row ttid of X = 16-bit sin(W_0 (p, t) + b_0).  A warp
-        // with no active slot skips its rows and their epilogues: its 32 rows of
-        // X keep stale values, and an MMA row depends on its own A row only
-        // (what matters at the end of the work list, when tiles thin out).
-        const bool wact = __any_sync(0xffffffffu, ray.state == kSlotActive);
-        if (wact) {
-            if (timed)
-                trace_layer0<W, F16, SPLIT, true>(a, w0s, wts, ray, ttid, x_s, xlo_s);
-            else
-                trace_layer0<W, F16, SPLIT, false>(a, w0s, wts, ray, ttid, x_s, xlo_s);
-        }
-        fence_proxy_async_smem();
-        tc_fence_before();
-        // one barrier: X is complete, and the tile stops when no slot is active
-        if (!bar_or(bar_id, 128, ray.state == kSlotActive)) break;
+    } else if (ok) {
+        // Two phases.  While the work list lasts, each tile refills its slots
+        // and runs on its own; the first time a refill comes back empty the
+        // tile enters the tail.  In the tail the block works in rounds of
+        // kTailRound iterations: at each round boundary (all tiles at a block
+        // barrier) the active rays of all tiles are gathered and dealt out
+        // again to the first tiles, so the long rays that remain run in as few
+        // tiles as possible instead of keeping every tile alive for a few rays.
+        // A thread that sees a timeout drops its ray; every stop decision goes
+        // through a barrier that all threads of the tile (or block) reach.
+        uint32_t* tail_count = reinterpret_cast<uint32_t*>(base + L.misc + 16);
+        uint32_t* rec = reinterpret_cast<uint32_t*>(base + L.x);  // round records, 12 words per ray
+        bool tail = false, live = true;
+        int it = 0;
+        while (true) {
+            if (!tail) {
+                refill_ray(a, ray, n_work);
+            } else if (it >= kTailRound || !live) {
+                __syncthreads();  // every tile is at the boundary: X, TMEM and the records are free
+                if (ray.state == kSlotActive) {
+                    const uint32_t r = atomicAdd(tail_count, 1u) * 12u;
+                    st_shared_v4(smem_u32(rec + r), static_cast<uint32_t>(ray.idx), static_cast<uint32_t>(ray.nlev),
+                                 static_cast<uint32_t>(ray.ntot), __float_as_uint(ray.tau));
+                    st_shared_v4(smem_u32(rec + r + 4), __float_as_uint(ray.px), __float_as_uint(ray.py),
+                                 __float_as_uint(ray.pz), __float_as_uint(ray.vx));
+                    st_shared_v4(smem_u32(rec + r + 8), __float_as_uint(ray.vy), __float_as_uint(ray.vz), 0u, 0u);
+                }
+                __syncthreads();
+                const int count = static_cast<int>(*tail_count);
+                const bool stop = count == 0 || *abort_flag != 0;
+                if (!stop && tid < count) {
+                    const uint32_t* q = rec + tid * 12;
+                    ray.idx = static_cast<int>(q[0]);
+                    ray.nlev = static_cast<int>(q[1]);
+                    ray.ntot = static_cast<int>(q[2]);
+                    ray.tau = __uint_as_float(q[3]);
+                    ray.px = __uint_as_float(q[4]);
+                    ray.py = __uint_as_float(q[5]);
+                    ray.pz = __uint_as_float(q[6]);
+                    ray.vx = __uint_as_float(q[7]);
+                    ray.vy = __uint_as_float(q[8]);
+                    ray.vz = __uint_as_float(q[9]);
+                    ray.state = kSlotActive;
+                } else {
+                    ray.state = kSlotDone;
+                }
+                __syncthreads();  // records read before layer 0 overwrites X
+                if (stop) break;
+                if (tid == 0) *tail_count = 0u;  // next written after the next boundary's first barrier
+                live = count > tile * 128;       // the same for all threads of a tile
+                it = 0;
+                if (!live) continue;
+            }
+            // layer 0 (FP32): row ttid of X = 16-bit sin(W_0 (p, t) + b_0).  A warp
+            // with no active slot skips its rows and their epilogues: its 32 rows of
+            // X keep stale values, and an MMA row depends on its own A row only.
+            const bool wact = __any_sync(0xffffffffu, ray.state == kSlotActive);
+            if (wact) {
+                if (timed)
+                    trace_layer0<W, F16, SPLIT, true>(a, w0s, wts, ray, ttid, x_s, xlo_s);
+                else
+                    trace_layer0<W, F16, SPLIT, false>(a, w0s, wts, ray, ttid, x_s, xlo_s);
+            }
+            fence_proxy_async_smem();
+            tc_fence_before();
+            // one barrier: X is complete, and the tile's decision.  Before the tail:
+            // an empty refill anywhere in the tile starts the tail (this layer 0 is
+            // dropped; the rays keep their state).  In the tail: no active ray left
+            // ends the tile's round.
+            if (!tail) {
+                if (bar_or(bar_id, 128, ray.state == kSlotDone)) {
+                    tail = true;
+                    it = kTailRound;
+                    continue;
+                }
+            } else if (!bar_or(bar_id, 128, ray.state == kSlotActive)) {
+                it = kTailRound;
+                continue;
+            }
 
-        float f = 0.0f;
-        for (int l = 0; l < KH; ++l) {
-            if (ttid == 0) {
+            float f = 0.0f;
+            bool good = true;
+            for (int l = 0; l < KH; ++l) {
+                if (ttid == 0) {
+                    tc_fence_after();
+                    const uint64_t xd0 = desc_kmajor_sw128(x_s), xld0 = desc_kmajor_sw128(xlo_s);
+                    const uint64_t wd0 = desc_kmajor_sw128(w_s + l * W * W * 2u);
+                    const uint64_t wld0 = desc_kmajor_sw128(wlo_s + l * W * W * 2u);
+#pragma unroll
+                    for (int kb = 0; kb < W / 64; ++kb)
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint32_t xo = kb * 128u * 128u + kk * 32u, wo = kb * W * 128u + kk * 32u;
+                            mma_f16kind(tmem, desc_add(xd0, xo), desc_add(wd0, wo), idesc, (kb | kk) != 0);
+                            if (SPLIT) {
+                                mma_f16kind(tmem, desc_add(xd0, xo), desc_add(wld0, wo), idesc, 1u);
+                                mma_f16kind(tmem, desc_add(xld0, xo), desc_add(wd0, wo), idesc, 1u);
+                            }
+                        }
+                    mma_commit(bar_mma);
+                }
+                // a warp either reads the accumulator whole or not at all
+                good = __all_sync(0xffffffffu, mbar_wait_bounded(bar_mma, mma_phase, a.status, abort_flag) && good);
+                mma_phase ^= 1u;
                 tc_fence_after();
-                const uint64_t xd0 = desc_kmajor_sw128(x_s), xld0 = desc_kmajor_sw128(xlo_s);
-                const uint64_t wd0 = desc_kmajor_sw128(w_s + l * W * W * 2u), wld0 = desc_kmajor_sw128(wlo_s + l * W * W * 2u);
+                const float* bl = bhs + l * W;
+                const bool rd = good && wact;
+                if (l + 1 < KH) {
+                    // hidden epilogue: X row = 16-bit sin(D + b)
+                    for (int c0 = 0; c0 < W && rd; c0 += 32) {
+                        float v[32];
+                        tmem_ld32(tmem + lane_base + c0, v);
+                        tmem_wait_ld();
 #pragma unroll
-                for (int kb = 0; kb < W / 64; ++kb)
+                        for (int q = 0; q < 4; ++q) {
+                            uint32_t pk[4], pl[4];
+                            const float4 ba = reinterpret_cast<const float4*>(bl + c0)[2 * q];
+                            const float4 bb = reinterpret_cast<const float4*>(bl + c0)[2 * q + 1];
+                            const float b8[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint32_t xo = kb * 128u * 128u + kk * 32u, wo = kb * W * 128u + kk * 32u;
-                        mma_f16kind(tmem, desc_add(xd0, xo), desc_add(wd0, wo), idesc, (kb | kk) != 0);
-                        if (SPLIT) {
-                            mma_f16kind(tmem, desc_add(xd0, xo), desc_add(wld0, wo), idesc, 1u);
-                            mma_f16kind(tmem, desc_add(xld0, xo), desc_add(wd0, wo), idesc, 1u);
+                            for (int e = 0; e < 4; ++e) {
+                                const int j = q * 8 + 2 * e;
+                                const float s0 = sin_fast(v[j] + b8[2 * e]), s1 = sin_fast(v[j + 1] + b8[2 * e + 1]);
+                                if (SPLIT)
+                                    pack_split<F16>(s0, s1, pk[e], pl[e]);
+                                else
+                                    pk[e] = pack16x2<F16>(s0, s1);
+                            }
+                            const uint32_t off = sw128_chunk_offset(ttid, (c0 >> 3) + q, 128);
+                            st_shared_v4(x_s + off, pk[0], pk[1], pk[2], pk[3]);
+                            if (SPLIT) st_shared_v4(xlo_s + off, pl[0], pl[1], pl[2], pl[3]);
                         }
                     }
-                mma_commit(bar_mma);
-            }
-            ok = mbar_wait_bounded(bar_mma, mma_phase, a.status, abort_flag);
-            mma_phase ^= 1u;
-            if (!ok) break;
-            tc_fence_after();
-            const float* bl = bhs + l * W;
-            if (l + 1 < KH) {
-                // hidden epilogue: X row = 16-bit sin(D + b)
-                for (int c0 = 0; c0 < W && wact; c0 += 32) {
-                    float v[32];
-                    tmem_ld32(tmem + lane_base + c0, v);
-                    tmem_wait_ld();
+                    fence_proxy_async_smem();
+                    tc_fence_before();
+                    bar_named(bar_id, 128);
+                } else {
+                    // output layer in FP32: f = w_out . sin(D + b) + b_out
+                    float dot = 0.0f;
+                    for (int c0 = 0; c0 < W && rd; c0 += 32) {
+                        float v[32];
+                        tmem_ld32(tmem + lane_base + c0, v);
+                        tmem_wait_ld();
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        uint32_t pk[4], pl[4];
-                        const float4 ba = reinterpret_cast<const float4*>(bl + c0)[2 * q];
-                        const float4 bb = reinterpret_cast<const float4*>(bl + c0)[2 * q + 1];
-                        const float b8[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int j = q * 8 + 2 * e;
-                            const float s0 = sin_fast(v[j] + b8[2 * e]), s1 = sin_fast(v[j + 1] + b8[2 * e + 1]);
-                            if (SPLIT)
-                                pack_split<F16>(s0, s1, pk[e], pl[e]);
-                            else
-                                pk[e] = pack16x2<F16>(s0, s1);
+                        for (int j4 = 0; j4 < 8; ++j4) {
+                            const float4 b4 = reinterpret_cast<const float4*>(bl + c0)[j4];
+                            const float4 w4 = reinterpret_cast<const float4*>(wos + c0)[j4];
+                            dot = fmaf(w4.x, sin_fast(v[4 * j4 + 0] + b4.x), dot);
+                            dot = fmaf(w4.y, sin_fast(v[4 * j4 + 1] + b4.y), dot);
+                            dot = fmaf(w4.z, sin_fast(v[4 * j4 + 2] + b4.z), dot);
+                            dot = fmaf(w4.w, sin_fast(v[4 * j4 + 3] + b4.w), dot);
                         }
-                        const uint32_t off = sw128_chunk_offset(ttid, (c0 >> 3) + q, 128);
-                        st_shared_v4(x_s + off, pk[0], pk[1], pk[2], pk[3]);
-                        if (SPLIT) st_shared_v4(xlo_s + off, pl[0], pl[1], pl[2], pl[3]);
                     }
+                    f = dot + net.bout;
                 }
-                fence_proxy_async_smem();
-                tc_fence_before();
-                bar_named(bar_id, 128);
-            } else {
-                // output layer in FP32: f = w_out . sin(D + b) + b_out
-                float dot = 0.0f;
-                for (int c0 = 0; c0 < W && wact; c0 += 32) {
-                    float v[32];
-                    tmem_ld32(tmem + lane_base + c0, v);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int j4 = 0; j4 < 8; ++j4) {
-                        const float4 b4 = reinterpret_cast<const float4*>(bl + c0)[j4];
-                        const float4 w4 = reinterpret_cast<const float4*>(wos + c0)[j4];
-                        dot = fmaf(w4.x, sin_fast(v[4 * j4 + 0] + b4.x), dot);
-                        dot = fmaf(w4.y, sin_fast(v[4 * j4 + 1] + b4.y), dot);
-                        dot = fmaf(w4.z, sin_fast(v[4 * j4 + 2] + b4.z), dot);
-                        dot = fmaf(w4.w, sin_fast(v[4 * j4 + 3] + b4.w), dot);
-                    }
-                }
-                f = dot + net.bout;
             }
+            tc_fence_before();
+            if (good)
+                step_ray(a, ray, f);
+            else
+                ray.state = kSlotDone;  // timed out (the status word says so): the ray is dropped
+            ++it;
         }
-        if (!ok) break;
-        tc_fence_before();
-        step_ray(a, ray, f);
     }
 
     tc_fence_before();
@@ -449,8 +523,7 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
                 ++g;
             }
             // every copy issued must land before the block exits
-            for (uint32_t gg = *consumed; gg < g; ++gg)
-                mbar_wait_bounded(bar_full + 8u * (gg % NS), (gg / NS) & 1u, a.status, abort_flag);
+            for (uint32_t gg = *consumed; gg < g; ++gg) mbar_drain(bar_full + 8u * (gg % NS), (gg / NS) & 1u);
         }
     } else {
         const long long n_work = a.in_list ? static_cast<long long>(*a.in_count) : a.n;
@@ -861,6 +934,10 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
                                  C::STAGE_BYTES, bar_full + 8u * stage);
                     }
                 }
+            // every copy issued must land before the block exits (the last use of
+            // each stage; earlier uses were waited on before their stage was refilled)
+            for (uint32_t gg = g > C::NS ? g - C::NS : 0; gg < g; ++gg)
+                mbar_drain(bar_full + 8u * (gg % C::NS), (gg / C::NS) & 1u);
         }
     } else if (warp == C::MMA_WARP) {
         if (lane == 0) {
