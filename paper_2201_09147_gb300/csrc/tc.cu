@@ -531,9 +531,11 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
         constexpr uint32_t idesc = idesc_f32acc(128, W, F16);
         const uint64_t xd0 = desc_kmajor_sw128(x_s), rd0 = desc_kmajor_sw128(ring_s);
         uint32_t mma_phase = 0, g = 0;
-        bool ok = true;
+        bool issue_ok = true;  // thread 0: every weight stage so far arrived in time
         Ray ray;
-        while (ok) {
+        // Stop decisions go through the ray threads' barrier: a timed-out wait
+        // drops the ray (the status word reports it) instead of leaving the loop.
+        while (true) {
             refill_ray(a, ray, n_work);
             if (a.cap <= 0) {
                 if (!bar_or(1, 128, ray.state == kSlotActive)) break;
@@ -553,13 +555,14 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
             if (!bar_or(1, 128, ray.state == kSlotActive)) break;
 
             float f = 0.0f;
+            bool good = true;
             for (int l = 0; l < KH; ++l) {
                 if (tid == 0) {
                     tc_fence_after();
-                    for (int kb = 0; kb < KB && ok; ++kb, ++g) {
+                    for (int kb = 0; kb < KB && issue_ok; ++kb, ++g) {
                         const uint32_t stage = g % NS;
-                        ok = mbar_wait_bounded(bar_full + 8u * stage, (g / NS) & 1u, a.status, abort_flag);
-                        if (!ok) break;
+                        issue_ok = mbar_wait_bounded(bar_full + 8u * stage, (g / NS) & 1u, a.status, abort_flag);
+                        if (!issue_ok) break;
                         tc_fence_after();
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)
@@ -567,15 +570,16 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
                                         desc_add(rd0, stage * kStreamStageBytes + kk * 32u), idesc, (kb | kk) != 0);
                         mma_commit(bar_empty + 8u * stage);
                     }
-                    if (ok) mma_commit(bar_mma);
+                    if (issue_ok) mma_commit(bar_mma);
                 }
-                ok = mbar_wait_bounded(bar_mma, mma_phase, a.status, abort_flag);
+                // a warp either reads the accumulator whole or not at all
+                good = __all_sync(0xffffffffu, mbar_wait_bounded(bar_mma, mma_phase, a.status, abort_flag) && good);
                 mma_phase ^= 1u;
-                if (!ok) break;
                 tc_fence_after();
                 const float* bl = bhs + l * W;
+                const bool rd = good && wact;
                 if (l + 1 < KH) {
-                    for (int c0 = 0; c0 < W && wact; c0 += 32) {
+                    for (int c0 = 0; c0 < W && rd; c0 += 32) {
                         float v[32];
                         tmem_ld32(tmem + lane_base + c0, v);
                         tmem_wait_ld();
@@ -599,7 +603,7 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
                     bar_named(1, 128);
                 } else {
                     float dot = 0.0f;
-                    for (int c0 = 0; c0 < W && wact; c0 += 32) {
+                    for (int c0 = 0; c0 < W && rd; c0 += 32) {
                         float v[32];
                         tmem_ld32(tmem + lane_base + c0, v);
                         tmem_wait_ld();
@@ -616,9 +620,11 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
                     f = dot + net.bout;
                 }
             }
-            if (!ok) break;
             tc_fence_before();
-            step_ray(a, ray, f);
+            if (good)
+                step_ray(a, ray, f);
+            else
+                ray.state = kSlotDone;
         }
         if (tid == 0) *consumed = g;
         bar_named(1, 128);
@@ -1071,7 +1077,8 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
             mbar_arrive(bar_xready + 8u * h);
 
             for (int l = 0; l < KH && ok; ++l) {
-                ok = mbar_wait_bounded(bar_dfull + 8u * h, df_phase, a.status, abort_flag);
+                // warp-uniform, so that a warp's TMEM loads run whole or not at all
+                ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar_dfull + 8u * h, df_phase, a.status, abort_flag));
                 df_phase ^= 1u;
                 if (!ok) break;
                 // every thread of the group has read this pair's points by now (the
@@ -1134,7 +1141,8 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
                 tc_fence_before();
                 mbar_arrive(bar_xready + 8u * h);
             }
-            if (ok) ok = mbar_wait_bounded(bar_dfull + 8u * h, df_phase, a.status, abort_flag);
+            if (ok)
+                ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar_dfull + 8u * h, df_phase, a.status, abort_flag));
             df_phase ^= 1u;
             if (ok && mt == 0) {
                 tc_fence_after();
