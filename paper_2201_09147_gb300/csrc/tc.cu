@@ -96,19 +96,22 @@ __host__ __device__ inline uint32_t tmem_cols_for(int cols) {
     return n;
 }
 
-// 16-bit head and remainder of two floats, packed as pairs.
+// 16-bit head and remainder of two floats, packed as pairs (the two
+// remainders in one packed FP32 operation: a - head(a) by an FMA with -1,
+// which is exact in the product, so each lane is the rounded difference).
 template <bool F16>
 __device__ __forceinline__ void pack_split(float a, float b, uint32_t& hi, uint32_t& lo) {
     hi = pack16x2<F16>(a, b);
-    const float ah = from16<F16>(static_cast<uint16_t>(hi & 0xFFFFu));
-    const float bh = from16<F16>(static_cast<uint16_t>(hi >> 16));
-    lo = pack16x2<F16>(a - ah, b - bh);
+    const float2 h = make_float2(from16<F16>(static_cast<uint16_t>(hi & 0xFFFFu)),
+                                 from16<F16>(static_cast<uint16_t>(hi >> 16)));
+    const float2 r = __ffma2_rn(h, make_float2(-1.0f, -1.0f), make_float2(a, b));
+    lo = pack16x2<F16>(r.x, r.y);
 }
 
 // Layer-0 parameters in shared memory: (w_x, w_y, w_z, b) per unit as a
 // float4, and the time column w_t apart.  With per-ray times (TIMED) b is
 // the plain bias and each ray adds w_t * t_ray; otherwise the launch's
-// constant time is folded into b.
+// constant time is folded into b.  (Gradient kernels.)
 __device__ __forceinline__ void stage_layer0(const NetView& net, float time, bool timed, int i, float* w0s,
                                              float* wts) {
 #pragma unroll
@@ -120,34 +123,96 @@ __device__ __forceinline__ void stage_layer0(const NetView& net, float time, boo
     wts[i] = timed ? wt : 0.0f;
 }
 
+// The same parameters laid out for packed FP32 arithmetic on unit pairs
+// (trace kernels): pair p = units 2p, 2p+1 as two float4s,
+// (w_x0, w_x1, w_y0, w_y1) and (w_z0, w_z1, b0, b1); w_t per unit as before.
+__device__ __forceinline__ void stage_layer0_pairs(const NetView& net, float time, bool timed, int i, float* w0s,
+                                                   float* wts) {
+    const int p = i >> 1, e = i & 1;
+    float bb = net.b0[i];
+    const float wt = net.in_dim == 4 ? net.w0[i * 4 + 3] : 0.0f;
+    if (!timed) bb = fmaf(wt, time, bb);
+    w0s[p * 8 + e] = net.w0[i * net.in_dim + 0];
+    w0s[p * 8 + 2 + e] = net.w0[i * net.in_dim + 1];
+    w0s[p * 8 + 4 + e] = net.w0[i * net.in_dim + 2];
+    w0s[p * 8 + 6 + e] = bb;
+    wts[i] = timed ? wt : 0.0f;
+}
+
 // Layer 0 (FP32) of one ray row: X[row] = 16-bit sin(W_0 (p, t) + b_0),
-// as a head and (SPLIT) the rounding of the remainder.  With TIMED the
-// ray's time is read here (it is not kept in a register between steps).
+// as a head and (SPLIT) the rounding of the remainder.  Two units per packed
+// FP32 FMA chain, in the same order as the scalar form
+// w_x p_x + (w_y p_y + (w_z p_z + b)), so each lane rounds as a scalar FMA
+// would.  With TIMED the ray's time is read here (it is not kept in a
+// register between steps).
 template <int W, bool F16, bool SPLIT, bool TIMED>
 __device__ __forceinline__ void trace_layer0(const LevelArgs& a, const float* w0s, const float* wts, const Ray& ray,
                                              int row, uint32_t x_s, uint32_t xlo_s) {
     const float tm = (TIMED && ray.state == kSlotActive) ? __ldg(a.ray_time + ray.idx) : 0.0f;
+    const float2 px = make_float2(ray.px, ray.px), py = make_float2(ray.py, ray.py), pz = make_float2(ray.pz, ray.pz);
+    const float2 t2 = make_float2(tm, tm);
     for (int k8 = 0; k8 < W / 8; ++k8) {
         uint32_t pk[4], pl[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int e0 = k8 * 8 + 2 * q, e1 = e0 + 1;
-            const float4 u0 = reinterpret_cast<const float4*>(w0s)[e0];
-            const float4 u1 = reinterpret_cast<const float4*>(w0s)[e1];
-            float c0 = u0.w, c1 = u1.w;
-            if (TIMED) {
-                const float2 t2 = reinterpret_cast<const float2*>(wts)[k8 * 4 + q];
-                c0 = fmaf(t2.x, tm, c0);
-                c1 = fmaf(t2.y, tm, c1);
-            }
-            const float z0 = fmaf(u0.x, ray.px, fmaf(u0.y, ray.py, fmaf(u0.z, ray.pz, c0)));
-            const float z1 = fmaf(u1.x, ray.px, fmaf(u1.y, ray.py, fmaf(u1.z, ray.pz, c1)));
+            const int pr = k8 * 4 + q;
+            const float4 A = reinterpret_cast<const float4*>(w0s)[2 * pr];
+            const float4 B = reinterpret_cast<const float4*>(w0s)[2 * pr + 1];
+            float2 c = make_float2(B.z, B.w);
+            if (TIMED) c = __ffma2_rn(reinterpret_cast<const float2*>(wts)[pr], t2, c);
+            const float2 z = __ffma2_rn(make_float2(A.x, A.y), px,
+                                        __ffma2_rn(make_float2(A.z, A.w), py, __ffma2_rn(make_float2(B.x, B.y), pz, c)));
             if (SPLIT)
-                pack_split<F16>(sin_fast(z0), sin_fast(z1), pk[q], pl[q]);
+                pack_split<F16>(sin_fast(z.x), sin_fast(z.y), pk[q], pl[q]);
             else
-                pk[q] = pack16x2<F16>(sin_fast(z0), sin_fast(z1));
+                pk[q] = pack16x2<F16>(sin_fast(z.x), sin_fast(z.y));
         }
         const uint32_t off = sw128_chunk_offset(row, k8, 128);
+        st_shared_v4(x_s + off, pk[0], pk[1], pk[2], pk[3]);
+        if (SPLIT) st_shared_v4(xlo_s + off, pl[0], pl[1], pl[2], pl[3]);
+    }
+}
+
+// Output layer of one ray row from its TMEM accumulator columns c0 .. c0+31:
+// acc += w_out . sin(D + b), the bias additions and the products on unit
+// pairs (two packed accumulators, for units 4j, 4j+1 and 4j+2, 4j+3).
+__device__ __forceinline__ void output_dot32(const float (&v)[32], const float* bl, const float* wo, float2& acc01,
+                                             float2& acc23) {
+#pragma unroll
+    for (int j4 = 0; j4 < 8; ++j4) {
+        const float4 b4 = reinterpret_cast<const float4*>(bl)[j4];
+        const float4 w4 = reinterpret_cast<const float4*>(wo)[j4];
+        const float2 x01 = __fadd2_rn(make_float2(v[4 * j4 + 0], v[4 * j4 + 1]), make_float2(b4.x, b4.y));
+        const float2 x23 = __fadd2_rn(make_float2(v[4 * j4 + 2], v[4 * j4 + 3]), make_float2(b4.z, b4.w));
+        acc01 = __ffma2_rn(make_float2(w4.x, w4.y), make_float2(sin_fast(x01.x), sin_fast(x01.y)), acc01);
+        acc23 = __ffma2_rn(make_float2(w4.z, w4.w), make_float2(sin_fast(x23.x), sin_fast(x23.y)), acc23);
+    }
+}
+
+// Hidden epilogue of one ray row for columns c0 .. c0+31: X row chunk =
+// 16-bit sin(D + b) (head, and with SPLIT the remainder), bias additions on
+// unit pairs.
+template <bool F16, bool SPLIT>
+__device__ __forceinline__ void hidden_epilogue32(const float (&v)[32], const float* bl, int row, int c0,
+                                                  uint32_t x_s, uint32_t xlo_s) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t pk[4], pl[4];
+        const float4 ba = reinterpret_cast<const float4*>(bl + c0)[2 * q];
+        const float4 bb = reinterpret_cast<const float4*>(bl + c0)[2 * q + 1];
+        const float2 b2[4] = {make_float2(ba.x, ba.y), make_float2(ba.z, ba.w), make_float2(bb.x, bb.y),
+                              make_float2(bb.z, bb.w)};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int j = q * 8 + 2 * e;
+            const float2 x = __fadd2_rn(make_float2(v[j], v[j + 1]), b2[e]);
+            const float s0 = sin_fast(x.x), s1 = sin_fast(x.y);
+            if (SPLIT)
+                pack_split<F16>(s0, s1, pk[e], pl[e]);
+            else
+                pk[e] = pack16x2<F16>(s0, s1);
+        }
+        const uint32_t off = sw128_chunk_offset(row, (c0 >> 3) + q, 128);
         st_shared_v4(x_s + off, pk[0], pk[1], pk[2], pk[3]);
         if (SPLIT) st_shared_v4(xlo_s + off, pl[0], pl[1], pl[2], pl[3]);
     }
@@ -195,7 +260,7 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
     }
     const bool timed = a.ray_time != nullptr && net.in_dim == 4;
     for (int i = tid; i < W; i += blockDim.x) {
-        stage_layer0(net, a.time, timed, i, w0s, wts);
+        stage_layer0_pairs(net, a.time, timed, i, w0s, wts);
         wos[i] = net.wout[i];
         for (int l = 0; l < KH; ++l) bhs[l * W + i] = net.bh[l][i];
     }
@@ -343,47 +408,21 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
                         float v[32];
                         tmem_ld32(tmem + lane_base + c0, v);
                         tmem_wait_ld();
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            uint32_t pk[4], pl[4];
-                            const float4 ba = reinterpret_cast<const float4*>(bl + c0)[2 * q];
-                            const float4 bb = reinterpret_cast<const float4*>(bl + c0)[2 * q + 1];
-                            const float b8[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const int j = q * 8 + 2 * e;
-                                const float s0 = sin_fast(v[j] + b8[2 * e]), s1 = sin_fast(v[j + 1] + b8[2 * e + 1]);
-                                if (SPLIT)
-                                    pack_split<F16>(s0, s1, pk[e], pl[e]);
-                                else
-                                    pk[e] = pack16x2<F16>(s0, s1);
-                            }
-                            const uint32_t off = sw128_chunk_offset(ttid, (c0 >> 3) + q, 128);
-                            st_shared_v4(x_s + off, pk[0], pk[1], pk[2], pk[3]);
-                            if (SPLIT) st_shared_v4(xlo_s + off, pl[0], pl[1], pl[2], pl[3]);
-                        }
+                        hidden_epilogue32<F16, SPLIT>(v, bl, ttid, c0, x_s, xlo_s);
                     }
                     fence_proxy_async_smem();
                     tc_fence_before();
                     bar_named(bar_id, 128);
                 } else {
                     // output layer in FP32: f = w_out . sin(D + b) + b_out
-                    float dot = 0.0f;
+                    float2 acc01 = make_float2(0.0f, 0.0f), acc23 = make_float2(0.0f, 0.0f);
                     for (int c0 = 0; c0 < W && rd; c0 += 32) {
                         float v[32];
                         tmem_ld32(tmem + lane_base + c0, v);
                         tmem_wait_ld();
-#pragma unroll
-                        for (int j4 = 0; j4 < 8; ++j4) {
-                            const float4 b4 = reinterpret_cast<const float4*>(bl + c0)[j4];
-                            const float4 w4 = reinterpret_cast<const float4*>(wos + c0)[j4];
-                            dot = fmaf(w4.x, sin_fast(v[4 * j4 + 0] + b4.x), dot);
-                            dot = fmaf(w4.y, sin_fast(v[4 * j4 + 1] + b4.y), dot);
-                            dot = fmaf(w4.z, sin_fast(v[4 * j4 + 2] + b4.z), dot);
-                            dot = fmaf(w4.w, sin_fast(v[4 * j4 + 3] + b4.w), dot);
-                        }
+                        output_dot32(v, bl + c0, wos + c0, acc01, acc23);
                     }
-                    f = dot + net.bout;
+                    f = ((acc01.x + acc01.y) + (acc23.x + acc23.y)) + net.bout;
                 }
             }
             tc_fence_before();
@@ -484,7 +523,7 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
     }
     const bool timed = a.ray_time != nullptr && net.in_dim == 4;
     for (int i = tid; i < W; i += kStreamThreads) {
-        stage_layer0(net, a.time, timed, i, w0s, wts);
+        stage_layer0_pairs(net, a.time, timed, i, w0s, wts);
         wos[i] = net.wout[i];
         for (int l = 0; l < KH; ++l) bhs[l * W + i] = net.bh[l][i];
     }
@@ -583,41 +622,20 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
                         float v[32];
                         tmem_ld32(tmem + lane_base + c0, v);
                         tmem_wait_ld();
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            uint32_t pk[4];
-                            const float4 ba = reinterpret_cast<const float4*>(bl + c0)[2 * q];
-                            const float4 bb = reinterpret_cast<const float4*>(bl + c0)[2 * q + 1];
-                            const float b8[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const int j = q * 8 + 2 * e;
-                                pk[e] = pack16x2<F16>(sin_fast(v[j] + b8[2 * e]), sin_fast(v[j + 1] + b8[2 * e + 1]));
-                            }
-                            st_shared_v4(x_s + sw128_chunk_offset(tid, (c0 >> 3) + q, 128), pk[0], pk[1], pk[2],
-                                         pk[3]);
-                        }
+                        hidden_epilogue32<F16, false>(v, bl, tid, c0, x_s, x_s);
                     }
                     fence_proxy_async_smem();
                     tc_fence_before();
                     bar_named(1, 128);
                 } else {
-                    float dot = 0.0f;
+                    float2 acc01 = make_float2(0.0f, 0.0f), acc23 = make_float2(0.0f, 0.0f);
                     for (int c0 = 0; c0 < W && rd; c0 += 32) {
                         float v[32];
                         tmem_ld32(tmem + lane_base + c0, v);
                         tmem_wait_ld();
-#pragma unroll
-                        for (int j4 = 0; j4 < 8; ++j4) {
-                            const float4 b4 = reinterpret_cast<const float4*>(bl + c0)[j4];
-                            const float4 w4 = reinterpret_cast<const float4*>(wos + c0)[j4];
-                            dot = fmaf(w4.x, sin_fast(v[4 * j4 + 0] + b4.x), dot);
-                            dot = fmaf(w4.y, sin_fast(v[4 * j4 + 1] + b4.y), dot);
-                            dot = fmaf(w4.z, sin_fast(v[4 * j4 + 2] + b4.z), dot);
-                            dot = fmaf(w4.w, sin_fast(v[4 * j4 + 3] + b4.w), dot);
-                        }
+                        output_dot32(v, bl + c0, wos + c0, acc01, acc23);
                     }
-                    f = dot + net.bout;
+                    f = ((acc01.x + acc01.y) + (acc23.x + acc23.y)) + net.bout;
                 }
             }
             tc_fence_before();
