@@ -445,28 +445,31 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
 // ---------------------------------------------------------------------------
 // trace kernel, width 256 with streamed weights
 // ---------------------------------------------------------------------------
-// Same per-ray structure as trace_level_tc_kernel, for networks whose hidden
-// weights do not fit in shared memory next to the activations ((256, k >= 2)
-// is 128 KB per layer).  A producer warp streams the 64-wide K blocks of every
-// hidden layer (256 rows x 128 bytes = 32 KB) from L2 through a 3-stage ring
-// in the order the MMAs consume them, cycling over the layers for as long as
-// rays remain; thread 0 issues the MMAs as stages arrive.
+// Same per-ray structure as trace_level_tc_kernel, for width 256, whose
+// hidden weights (128 KB per layer) leave no room for a second tile of
+// activations when held in shared memory.  A producer warp streams the 64-wide K blocks of every
+// hidden layer (256 rows x 128 bytes = 32 KB) from L2 through a ring in the
+// order the MMAs consume them, cycling over the layers for as long as rays
+// remain; thread 0 issues the MMAs as stages arrive.  ST ray tiles of 128
+// (TMEM columns [t*256, (t+1)*256), 64 KB of activations each) share every
+// weight stage: with two tiles each streamed byte serves twice the rays and
+// eight warps instead of four overlap their layer-0 and epilogue work.
 constexpr int kStreamW = 256;
-constexpr int kStreamStages = 3;
 constexpr uint32_t kStreamStageBytes = kStreamW * 128u;
-constexpr int kStreamThreads = 160;  // 128 ray threads + 1 producer warp
+__host__ __device__ constexpr int stream_stages(int ST) { return ST == 1 ? 3 : 2; }
+__host__ __device__ constexpr int stream_threads(int ST) { return 128 * ST + 32; }  // ray threads + producer warp
 
 struct StreamLayout {
     uint32_t x, ring, w0, wt, bh, wout, bars, misc, total;
 };
 
-__host__ __device__ inline StreamLayout stream_layout(int KH) {
+__host__ __device__ inline StreamLayout stream_layout(int KH, int ST) {
     StreamLayout L;
     uint32_t o = 0;
     L.x = o;
-    o += 128u * kStreamW * 2u;
+    o += static_cast<uint32_t>(ST) * 128u * kStreamW * 2u;
     L.ring = o;
-    o += kStreamStages * kStreamStageBytes;
+    o += stream_stages(ST) * kStreamStageBytes;
     L.w0 = o;
     o += kStreamW * 4u * 4u;
     L.wt = o;
@@ -476,7 +479,7 @@ __host__ __device__ inline StreamLayout stream_layout(int KH) {
     L.wout = o;
     o += kStreamW * 4u;
     L.bars = o;
-    o += (2 * kStreamStages + 1) * 8u;
+    o += (2 * stream_stages(ST) + 1) * 8u;
     o = (o + 15u) & ~15u;
     L.misc = o;
     o += 32u;
@@ -484,16 +487,16 @@ __host__ __device__ inline StreamLayout stream_layout(int KH) {
     return L;
 }
 
-template <bool F16>
-__global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(const LevelArgs a) {
-    constexpr int W = kStreamW, KB = W / 64, NS = kStreamStages;
+template <bool F16, int ST>
+__global__ void __launch_bounds__(stream_threads(ST)) trace_level_tc_stream_kernel(const LevelArgs a) {
+    constexpr int W = kStreamW, KB = W / 64, NS = stream_stages(ST), NRAY = 128 * ST;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const uint32_t raw_s = smem_u32(smem_raw);
     const uint32_t base_s = (raw_s + 1023u) & ~1023u;
     uint8_t* base = smem_raw + (base_s - raw_s);
     const NetView& net = a.net;
     const int KH = net.n_hidden;
-    const StreamLayout L = stream_layout(KH);
+    const StreamLayout L = stream_layout(KH, ST);
     float* w0s = reinterpret_cast<float*>(base + L.w0);
     float* wts = reinterpret_cast<float*>(base + L.wt);
     float* bhs = reinterpret_cast<float*>(base + L.bh);
@@ -504,7 +507,10 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
     volatile int* done_flag = reinterpret_cast<volatile int*>(base + L.misc + 8);
     volatile uint32_t* consumed = reinterpret_cast<volatile uint32_t*>(base + L.misc + 12);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t x_s = base_s + L.x, ring_s = base_s + L.ring;
+    const int tile = tid >> 7, ttid = tid & 127;
+    constexpr uint32_t xbytes = 128u * W * 2u;
+    const uint32_t x_s = base_s + L.x + static_cast<uint32_t>(tile < ST ? tile : 0) * xbytes;
+    const uint32_t ring_s = base_s + L.ring;
 
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -518,11 +524,11 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
         fence_mbar_init();
     }
     if (warp == 0) {
-        tmem_alloc(smem_u32(tmem_slot), W);
+        tmem_alloc(smem_u32(tmem_slot), W * ST);
         tmem_relinquish();
     }
     const bool timed = a.ray_time != nullptr && net.in_dim == 4;
-    for (int i = tid; i < W; i += kStreamThreads) {
+    for (int i = tid; i < W; i += stream_threads(ST)) {
         stage_layer0_pairs(net, a.time, timed, i, w0s, wts);
         wos[i] = net.wout[i];
         for (int l = 0; l < KH; ++l) bhs[l * W + i] = net.bh[l][i];
@@ -530,9 +536,9 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
+    const uint32_t tmem0 = *tmem_slot;
 
-    if (warp == 4) {
+    if (warp == 4 * ST) {
         // producer: K blocks of layer 0..KH-1 in consumption order, cyclically
         if (lane == 0) {
             uint32_t g = 0;
@@ -566,9 +572,10 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
         }
     } else {
         const long long n_work = a.in_list ? static_cast<long long>(*a.in_count) : a.n;
-        const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+        const uint32_t lane_base = static_cast<uint32_t>((ttid >> 5) * 32) << 16;
+        const uint32_t tmem = tmem0 + static_cast<uint32_t>(tile * W);
         constexpr uint32_t idesc = idesc_f32acc(128, W, F16);
-        const uint64_t xd0 = desc_kmajor_sw128(x_s), rd0 = desc_kmajor_sw128(ring_s);
+        const uint64_t rd0 = desc_kmajor_sw128(ring_s);
         uint32_t mma_phase = 0, g = 0;
         bool issue_ok = true;  // thread 0: every weight stage so far arrived in time
         Ray ray;
@@ -577,7 +584,7 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
         while (true) {
             refill_ray(a, ray, n_work);
             if (a.cap <= 0) {
-                if (!bar_or(1, 128, ray.state == kSlotActive)) break;
+                if (!bar_or(1, NRAY, ray.state == kSlotActive)) break;
                 pass_ray(a, ray);
                 continue;
             }
@@ -585,13 +592,13 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
             const bool wact = __any_sync(0xffffffffu, ray.state == kSlotActive);
             if (wact) {
                 if (timed)
-                    trace_layer0<W, F16, false, true>(a, w0s, wts, ray, tid, x_s, x_s);
+                    trace_layer0<W, F16, false, true>(a, w0s, wts, ray, ttid, x_s, x_s);
                 else
-                    trace_layer0<W, F16, false, false>(a, w0s, wts, ray, tid, x_s, x_s);
+                    trace_layer0<W, F16, false, false>(a, w0s, wts, ray, ttid, x_s, x_s);
             }
             fence_proxy_async_smem();
             tc_fence_before();
-            if (!bar_or(1, 128, ray.state == kSlotActive)) break;
+            if (!bar_or(1, NRAY, ray.state == kSlotActive)) break;
 
             float f = 0.0f;
             bool good = true;
@@ -604,9 +611,14 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
                         if (!issue_ok) break;
                         tc_fence_after();
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            mma_f16kind(tmem, desc_add(xd0, kb * 128u * 128u + kk * 32u),
-                                        desc_add(rd0, stage * kStreamStageBytes + kk * 32u), idesc, (kb | kk) != 0);
+                        for (int t = 0; t < ST; ++t) {
+                            const uint64_t xd0 = desc_kmajor_sw128(base_s + L.x + t * xbytes);
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                mma_f16kind(tmem0 + t * W, desc_add(xd0, kb * 128u * 128u + kk * 32u),
+                                            desc_add(rd0, stage * kStreamStageBytes + kk * 32u), idesc,
+                                            (kb | kk) != 0);
+                        }
                         mma_commit(bar_empty + 8u * stage);
                     }
                     if (issue_ok) mma_commit(bar_mma);
@@ -622,11 +634,11 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
                         float v[32];
                         tmem_ld32(tmem + lane_base + c0, v);
                         tmem_wait_ld();
-                        hidden_epilogue32<F16, false>(v, bl, tid, c0, x_s, x_s);
+                        hidden_epilogue32<F16, false>(v, bl, ttid, c0, x_s, x_s);
                     }
                     fence_proxy_async_smem();
                     tc_fence_before();
-                    bar_named(1, 128);
+                    bar_named(1, NRAY);
                 } else {
                     float2 acc01 = make_float2(0.0f, 0.0f), acc23 = make_float2(0.0f, 0.0f);
                     for (int c0 = 0; c0 < W && rd; c0 += 32) {
@@ -645,7 +657,7 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
                 ray.state = kSlotDone;
         }
         if (tid == 0) *consumed = g;
-        bar_named(1, 128);
+        bar_named(1, NRAY);
         if (tid == 0) {
             __threadfence_block();
             *done_flag = 1;
@@ -656,7 +668,7 @@ __global__ void __launch_bounds__(kStreamThreads) trace_level_tc_stream_kernel(c
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem, W);
+        tmem_dealloc(tmem0, W * ST);
     }
 }
 
@@ -1321,10 +1333,20 @@ int trace_tiles_max(const NetView& net) {
     case 128:
         return f16 ? trace_tiles_resident<128, true>(net) : trace_tiles_resident<128, false>(net);
     case 256:
-        if (net.n_hidden == 1) return f16 ? trace_tiles_resident<256, true>(net) : trace_tiles_resident<256, false>(net);
-        return 1;  // the streamed-weight kernel has one tile
+        return 2;  // the streamed-weight kernel: one or two tiles
     }
     return 0;
+}
+
+// Streamed-weight trace: two ray tiles per CTA unless a.tiles asks for one.
+template <bool F16>
+static cudaError_t launch_trace_stream(const LevelArgs& a, int num_sms, cudaStream_t s) {
+    const int KH = a.net.n_hidden;
+    if (a.tiles == 1)
+        return launch_tc(trace_level_tc_stream_kernel<F16, 1>, stream_threads(1), stream_layout(KH, 1).total + 1024,
+                         kStreamW, num_sms, s, &a);
+    return launch_tc(trace_level_tc_stream_kernel<F16, 2>, stream_threads(2), stream_layout(KH, 2).total + 1024,
+                     2 * kStreamW, num_sms, s, &a);
 }
 
 cudaError_t launch_trace_level_tc(const LevelArgs& a, int num_sms, cudaStream_t s) {
@@ -1335,14 +1357,7 @@ cudaError_t launch_trace_level_tc(const LevelArgs& a, int num_sms, cudaStream_t 
     case 128:
         return f16 ? launch_trace_resident<128, true>(a, num_sms, s) : launch_trace_resident<128, false>(a, num_sms, s);
     case 256:
-        if (a.net.n_hidden == 1)
-            return f16 ? launch_trace_resident<256, true>(a, num_sms, s)
-                       : launch_trace_resident<256, false>(a, num_sms, s);
-        {
-            const size_t ssm = stream_layout(a.net.n_hidden).total + 1024;
-            return f16 ? launch_tc(trace_level_tc_stream_kernel<true>, kStreamThreads, ssm, 256, num_sms, s, &a)
-                       : launch_tc(trace_level_tc_stream_kernel<false>, kStreamThreads, ssm, 256, num_sms, s, &a);
-        }
+        return f16 ? launch_trace_stream<true>(a, num_sms, s) : launch_trace_stream<false>(a, num_sms, s);
     }
     return cudaErrorInvalidValue;
 }
