@@ -13,7 +13,10 @@
 //   against the resident 16-bit weights; each thread reads its own row back
 //   with tcgen05.ld, adds the bias and applies the sine in registers.  The
 //   output layer is an FP32 dot product of the last sine layer straight from
-//   TMEM, so the step t = f - d is never rounded to 16 bits.
+//   TMEM, so the step t = f - d is never rounded to 16 bits.  Once the work
+//   list is empty the CTA regroups its remaining rays into its first tiles
+//   every few iterations.  Width 256 (trace_level_tc_stream): two tiles share
+//   hidden weights streamed through a ring of bulk-copied stages.
 //
 // grad_tc : analytic gradients (Alg. 2).  Tiles of 64 points in two halves;
 //   the MMA runs with the features as rows (M = 128 per TMEM tile,
