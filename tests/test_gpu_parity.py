@@ -405,10 +405,17 @@ def test_render_host_three_levels(sdf, memory):
     _render_host_vs_device(sdf, workloads.get("three_level_512"), memory)
 
 
-def _render_host_vs_device(sdf, wl, memory):
+@pytest.mark.parametrize("precision", [0, 3], ids=["fp32", "fp16"])
+def test_render_host_other_precisions(sdf, precision):
+    """Page-locked host frames with the FP32 (SIMT) and FP16 kernels equal their device calls."""
+    _render_host_vs_device(sdf, workloads.get("normal_map_1080p", 160, 90), "pinned", precision)
+
+
+def _render_host_vs_device(sdf, wl, memory, precision=None):
+    precision = sdf.SDF_BF16 if precision is None else precision
     orig, dirs = wl.rays()
-    nets = [sdf.Net(b, sdf.SDF_BF16) for b in wl.level_bytes()]
-    fine = sdf.Net(wl.fine_bytes(), sdf.SDF_BF16)
+    nets = [sdf.Net(b, precision) for b in wl.level_bytes()]
+    fine = sdf.Net(wl.fine_bytes(), precision)
     n = orig.shape[1]
     pin = (lambda t: t.pin_memory()) if memory == "pinned" else (lambda t: t)
     hp = pin(torch.full((3, n), float("nan")))
