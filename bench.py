@@ -378,6 +378,22 @@ def main():
             torch.cuda.synchronize()
             bt.append(a.elapsed_time(b))
         plain_bf16_value = n / (statistics.mean(bt[1:]) / 1e3) / 1e6
+        # the plain (256,3) trace with E4M3 hidden layers (its normals E4M3 too)
+        p8 = [sdfnn.Net(b, sdfnn.SDF_FP8, local) for b in plain.level_bytes()]
+        p8f = sdfnn.Net(plain.fine_bytes(), sdfnn.SDF_FP8, local)
+        et8 = []
+        for _ in range(4):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sdfnn.trace_multiscale(p8, plain.delta, plain.caps, plain.eps, orig, dirs, step_scale=plain.step_scale,
+                                   final_mode=plain.final_mode, out_pos=pos, out_t=tt, out_hit=hit, want_iters=False)
+            sdfnn.normal_map(p8f, pos, hit, out=nrm)
+            b.record(stream)
+            torch.cuda.synchronize()
+            et8.append(a.elapsed_time(b))
+        plain_fp8_value = n / (statistics.mean(et8[1:]) / 1e3) / 1e6
         # multiscale with FP32 hidden layers: isolates the algorithm from the precision
         c32 = [sdfnn.Net(b, sdfnn.SDF_FP32, local) for b in wl.level_bytes()]
         f32 = sdfnn.Net(wl.fine_bytes(), sdfnn.SDF_FP32, local)
@@ -433,6 +449,7 @@ def main():
                                  "fp8_normal_map_ms": fp8_nm_ms,
                                  "plain_fp32_256x3_Mrays_s": plain_value,
                                  "plain_bf16_256x3_Mrays_s": plain_bf16_value,
+                                 "plain_fp8_256x3_Mrays_s": plain_fp8_value,
                                  "speedup_precision_only_plain": plain_bf16_value / plain_value,
                                  "speedup_vs_plain_fp32": value / ws / plain_value,
                                  "multiscale_fp32_Mrays_s": ms_fp32_value,

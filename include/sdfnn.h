@@ -66,14 +66,16 @@ enum {
     SDF_FP32 = 0, /* SIMT FP32 contractions (the plain comparison path) */
     SDF_BF16 = 1, /* tcgen05 tensor-core contractions, bfloat16 operands, FP32 accumulation */
     SDF_FP8 = 2,  /* tcgen05 kind::f8f6f4 contractions with E4M3 operands, FP32 accumulation, for
-                     sdf_normals / sdf_normal_map(_timed) of width 128 or 256 networks
-                     (SDF_ERR_UNSUPPORTED at load for width 64, and for tracing).  Hidden
-                     weights are stored as W_l * 448 / max|W_l|; the sine activations as
-                     256 sin; the tangents of Alg. 2 with per-layer scales fixed at load
-                     from their largest value on a 7^3 grid over [-1, 1]^3 (mapped to 64,
-                     leaving 7x headroom before the conversion saturates at 448); w_out
-                     as an E4M3 head plus a remainder.  E4M3 keeps 3 mantissa bits:
-                     normals are accurate to a few degrees, not to SDF_BF16's bound. */
+                     sdf_normals / sdf_normal_map(_timed) of width 128 or 256 networks and
+                     for tracing with width 256 networks (SDF_ERR_UNSUPPORTED at load for
+                     width 64, and when tracing with width 128).  Hidden weights are
+                     stored as W_l * 448 / max|W_l|; the sine activations as 256 sin; the
+                     tangents of Alg. 2 with per-layer scales fixed at load from their
+                     largest value on a 7^3 grid over [-1, 1]^3 (mapped to 64, leaving 7x
+                     headroom before the conversion saturates at 448); w_out as an E4M3
+                     head plus a remainder.  E4M3 keeps 3 mantissa bits: normals are
+                     accurate to a few degrees and hit points to ~1e-2, not to SDF_BF16's
+                     bounds. */
     SDF_FP16 = 3  /* tcgen05 tensor-core contractions, IEEE half operands, FP32 accumulation:
                      same tensor rate as SDF_BF16 with 3 more mantissa bits; the sine
                      activations lie in [-1, 1] and need no wider exponent range */

@@ -474,8 +474,8 @@ int validate_trace_params(const sdf_trace_params* P, int* dev_out) {
             return fail(SDF_ERR_ARG, "step_scale[%d] must be finite and > 0", j);
         if (!P->step_scale && !(net->lipschitz > 0.0))
             return fail(SDF_ERR_ARG, "nets[%d] has a zero Lipschitz bound; pass step_scale", j);
-        if (net->precision == SDF_FP8)
-            return fail(SDF_ERR_UNSUPPORTED, "nets[%d]: tracing with E4M3 hidden layers is not built", j);
+        if (net->precision == SDF_FP8 && net->width != 256)
+            return fail(SDF_ERR_UNSUPPORTED, "nets[%d]: tracing with E4M3 hidden layers is built for width 256", j);
         if (net->precision != SDF_FP32 && !tc_trace_supported(net->width, net->n_hidden))
             return fail(SDF_ERR_UNSUPPORTED, "tensor-core tracing of a (%d,%d) network is not built", net->width,
                         net->n_hidden);

@@ -40,6 +40,11 @@
 namespace sdfnn {
 namespace {
 
+// Operand types of the tensor-core contractions: bfloat16 or IEEE half
+// (kind::f16), or E4M3 (kind::f8f6f4; sine activations stored as 256 sin).
+enum : int { kOpBF16 = 0, kOpF16 = 1, kOpE4M3 = 2 };
+constexpr float kFp8ActScale = 256.0f;
+
 // ---------------------------------------------------------------------------
 // trace kernel
 // ---------------------------------------------------------------------------
@@ -179,14 +184,18 @@ __device__ __forceinline__ void trace_layer0(const LevelArgs& a, const float* w0
 // Output layer of one ray row from its TMEM accumulator columns c0 .. c0+31:
 // acc += w_out . sin(D + b), the bias additions and the products on unit
 // pairs (two packed accumulators, for units 4j, 4j+1 and 4j+2, 4j+3).
+template <bool SCALED = false>
 __device__ __forceinline__ void output_dot32(const float (&v)[32], const float* bl, const float* wo, float2& acc01,
-                                             float2& acc23) {
+                                             float2& acc23, float sc = 1.0f) {
+    const float2 sc2 = make_float2(sc, sc);
 #pragma unroll
     for (int j4 = 0; j4 < 8; ++j4) {
         const float4 b4 = reinterpret_cast<const float4*>(bl)[j4];
         const float4 w4 = reinterpret_cast<const float4*>(wo)[j4];
-        const float2 x01 = __fadd2_rn(make_float2(v[4 * j4 + 0], v[4 * j4 + 1]), make_float2(b4.x, b4.y));
-        const float2 x23 = __fadd2_rn(make_float2(v[4 * j4 + 2], v[4 * j4 + 3]), make_float2(b4.z, b4.w));
+        const float2 v01 = make_float2(v[4 * j4 + 0], v[4 * j4 + 1]), v23 = make_float2(v[4 * j4 + 2], v[4 * j4 + 3]);
+        // SCALED (E4M3 operands): the accumulator times the inverse of the operand scales
+        const float2 x01 = SCALED ? __ffma2_rn(v01, sc2, make_float2(b4.x, b4.y)) : __fadd2_rn(v01, make_float2(b4.x, b4.y));
+        const float2 x23 = SCALED ? __ffma2_rn(v23, sc2, make_float2(b4.z, b4.w)) : __fadd2_rn(v23, make_float2(b4.z, b4.w));
         acc01 = __ffma2_rn(make_float2(w4.x, w4.y), make_float2(sin_fast(x01.x), sin_fast(x01.y)), acc01);
         acc23 = __ffma2_rn(make_float2(w4.z, w4.w), make_float2(sin_fast(x23.x), sin_fast(x23.y)), acc23);
     }
@@ -445,6 +454,56 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
     }
 }
 
+// Layer 0 of one ray row as E4M3 bytes of 256 sin(W_0 (p, t) + b_0): K-major
+// rows of 128-element blocks with the 128-byte swizzle, one 16-byte chunk
+// (16 units) per vector store; the units in pairs as in trace_layer0.
+template <int W, bool TIMED>
+__device__ __forceinline__ void trace_layer0_e4m3(const LevelArgs& a, const float* w0s, const float* wts,
+                                                  const Ray& ray, int row, uint32_t x_s) {
+    const float tm = (TIMED && ray.state == kSlotActive) ? __ldg(a.ray_time + ray.idx) : 0.0f;
+    const float2 px = make_float2(ray.px, ray.px), py = make_float2(ray.py, ray.py), pz = make_float2(ray.pz, ray.pz);
+    const float2 t2 = make_float2(tm, tm);
+    for (int j16 = 0; j16 < W / 16; ++j16) {
+        float sv[16];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int pr = j16 * 8 + q;
+            const float4 A = reinterpret_cast<const float4*>(w0s)[2 * pr];
+            const float4 B = reinterpret_cast<const float4*>(w0s)[2 * pr + 1];
+            float2 c = make_float2(B.z, B.w);
+            if (TIMED) c = __ffma2_rn(reinterpret_cast<const float2*>(wts)[pr], t2, c);
+            const float2 z = __ffma2_rn(make_float2(A.x, A.y), px,
+                                        __ffma2_rn(make_float2(A.z, A.w), py, __ffma2_rn(make_float2(B.x, B.y), pz, c)));
+            sv[2 * q] = kFp8ActScale * sin_fast(z.x);
+            sv[2 * q + 1] = kFp8ActScale * sin_fast(z.y);
+        }
+        st_shared_v4(x_s + sw128_chunk_offset(row, j16, 128), pack_e4m3x4(sv[0], sv[1], sv[2], sv[3]),
+                     pack_e4m3x4(sv[4], sv[5], sv[6], sv[7]), pack_e4m3x4(sv[8], sv[9], sv[10], sv[11]),
+                     pack_e4m3x4(sv[12], sv[13], sv[14], sv[15]));
+    }
+}
+
+// Hidden epilogue of one ray row for accumulator columns c0 .. c0+31 with
+// E4M3 operands: X = E4M3(256 sin(D * mf + b)), two 16-byte chunks.
+__device__ __forceinline__ void hidden_epilogue32_e4m3(const float (&v)[32], const float* bl, float mf, int row,
+                                                       int c0, uint32_t x_s) {
+    const float2 mf2 = make_float2(mf, mf);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float sv[16];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int j = h * 16 + 2 * e;
+            const float2 x = __ffma2_rn(make_float2(v[j], v[j + 1]), mf2, make_float2(bl[c0 + j], bl[c0 + j + 1]));
+            sv[2 * e] = kFp8ActScale * sin_fast(x.x);
+            sv[2 * e + 1] = kFp8ActScale * sin_fast(x.y);
+        }
+        st_shared_v4(x_s + sw128_chunk_offset(row, (c0 >> 4) + h, 128), pack_e4m3x4(sv[0], sv[1], sv[2], sv[3]),
+                     pack_e4m3x4(sv[4], sv[5], sv[6], sv[7]), pack_e4m3x4(sv[8], sv[9], sv[10], sv[11]),
+                     pack_e4m3x4(sv[12], sv[13], sv[14], sv[15]));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // trace kernel, width 256 with streamed weights
 // ---------------------------------------------------------------------------
@@ -466,11 +525,11 @@ struct StreamLayout {
     uint32_t x, ring, w0, wt, bh, wout, bars, misc, total;
 };
 
-__host__ __device__ inline StreamLayout stream_layout(int KH, int ST) {
+__host__ __device__ inline StreamLayout stream_layout(int KH, int ST, int EB) {
     StreamLayout L;
     uint32_t o = 0;
     L.x = o;
-    o += static_cast<uint32_t>(ST) * 128u * kStreamW * 2u;
+    o += static_cast<uint32_t>(ST) * 128u * kStreamW * static_cast<uint32_t>(EB);
     L.ring = o;
     o += stream_stages(ST) * kStreamStageBytes;
     L.w0 = o;
@@ -490,16 +549,19 @@ __host__ __device__ inline StreamLayout stream_layout(int KH, int ST) {
     return L;
 }
 
-template <bool F16, int ST>
+template <int OP, int ST>
 __global__ void __launch_bounds__(stream_threads(ST)) trace_level_tc_stream_kernel(const LevelArgs a) {
-    constexpr int W = kStreamW, KB = W / 64, NS = stream_stages(ST), NRAY = 128 * ST;
+    constexpr bool F16 = OP == kOpF16, FP8 = OP == kOpE4M3;
+    constexpr int EB = FP8 ? 1 : 2;  // operand bytes per element
+    // 128-byte K blocks per layer; a stage is one K block of all 256 rows (32 KB)
+    constexpr int W = kStreamW, KB = W * EB / 128, NS = stream_stages(ST), NRAY = 128 * ST;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const uint32_t raw_s = smem_u32(smem_raw);
     const uint32_t base_s = (raw_s + 1023u) & ~1023u;
     uint8_t* base = smem_raw + (base_s - raw_s);
     const NetView& net = a.net;
     const int KH = net.n_hidden;
-    const StreamLayout L = stream_layout(KH, ST);
+    const StreamLayout L = stream_layout(KH, ST, EB);
     float* w0s = reinterpret_cast<float*>(base + L.w0);
     float* wts = reinterpret_cast<float*>(base + L.wt);
     float* bhs = reinterpret_cast<float*>(base + L.bh);
@@ -511,7 +573,7 @@ __global__ void __launch_bounds__(stream_threads(ST)) trace_level_tc_stream_kern
     volatile uint32_t* consumed = reinterpret_cast<volatile uint32_t*>(base + L.misc + 12);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tile = tid >> 7, ttid = tid & 127;
-    constexpr uint32_t xbytes = 128u * W * 2u;
+    constexpr uint32_t xbytes = 128u * W * EB;
     const uint32_t x_s = base_s + L.x + static_cast<uint32_t>(tile < ST ? tile : 0) * xbytes;
     const uint32_t ring_s = base_s + L.ring;
 
@@ -577,7 +639,8 @@ __global__ void __launch_bounds__(stream_threads(ST)) trace_level_tc_stream_kern
         const long long n_work = a.in_list ? static_cast<long long>(*a.in_count) : a.n;
         const uint32_t lane_base = static_cast<uint32_t>((ttid >> 5) * 32) << 16;
         const uint32_t tmem = tmem0 + static_cast<uint32_t>(tile * W);
-        constexpr uint32_t idesc = idesc_f32acc(128, W, F16);
+        // E4M3: the format fields 0 of this descriptor select E4M3 under kind::f8f6f4
+        constexpr uint32_t idesc = idesc_f32acc(128, W, F16 || FP8);
         const uint64_t rd0 = desc_kmajor_sw128(ring_s);
         uint32_t mma_phase = 0, g = 0;
         bool issue_ok = true;  // thread 0: every weight stage so far arrived in time
@@ -594,10 +657,16 @@ __global__ void __launch_bounds__(stream_threads(ST)) trace_level_tc_stream_kern
             // a warp with no active slot skips its rows (as in trace_level_tc_kernel)
             const bool wact = __any_sync(0xffffffffu, ray.state == kSlotActive);
             if (wact) {
-                if (timed)
+                if (FP8) {
+                    if (timed)
+                        trace_layer0_e4m3<W, true>(a, w0s, wts, ray, ttid, x_s);
+                    else
+                        trace_layer0_e4m3<W, false>(a, w0s, wts, ray, ttid, x_s);
+                } else if (timed) {
                     trace_layer0<W, F16, false, true>(a, w0s, wts, ray, ttid, x_s, x_s);
-                else
+                } else {
                     trace_layer0<W, F16, false, false>(a, w0s, wts, ray, ttid, x_s, x_s);
+                }
             }
             fence_proxy_async_smem();
             tc_fence_before();
@@ -617,10 +686,14 @@ __global__ void __launch_bounds__(stream_threads(ST)) trace_level_tc_stream_kern
                         for (int t = 0; t < ST; ++t) {
                             const uint64_t xd0 = desc_kmajor_sw128(base_s + L.x + t * xbytes);
 #pragma unroll
-                            for (int kk = 0; kk < 4; ++kk)
-                                mma_f16kind(tmem0 + t * W, desc_add(xd0, kb * 128u * 128u + kk * 32u),
-                                            desc_add(rd0, stage * kStreamStageBytes + kk * 32u), idesc,
-                                            (kb | kk) != 0);
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint64_t xd = desc_add(xd0, kb * 128u * 128u + kk * 32u);
+                                const uint64_t wd = desc_add(rd0, stage * kStreamStageBytes + kk * 32u);
+                                if (FP8)
+                                    mma_f8kind(tmem0 + t * W, xd, wd, idesc, (kb | kk) != 0);
+                                else
+                                    mma_f16kind(tmem0 + t * W, xd, wd, idesc, (kb | kk) != 0);
+                            }
                         }
                         mma_commit(bar_empty + 8u * stage);
                     }
@@ -632,12 +705,17 @@ __global__ void __launch_bounds__(stream_threads(ST)) trace_level_tc_stream_kern
                 tc_fence_after();
                 const float* bl = bhs + l * W;
                 const bool rd = good && wact;
+                // E4M3: accumulator -> value (the operand scales q_w and 256 divided out)
+                const float mf = FP8 ? 1.0f / (net.q_w[l] * kFp8ActScale) : 1.0f;
                 if (l + 1 < KH) {
                     for (int c0 = 0; c0 < W && rd; c0 += 32) {
                         float v[32];
                         tmem_ld32(tmem + lane_base + c0, v);
                         tmem_wait_ld();
-                        hidden_epilogue32<F16, false>(v, bl, ttid, c0, x_s, x_s);
+                        if (FP8)
+                            hidden_epilogue32_e4m3(v, bl, mf, ttid, c0, x_s);
+                        else
+                            hidden_epilogue32<F16, false>(v, bl, ttid, c0, x_s, x_s);
                     }
                     fence_proxy_async_smem();
                     tc_fence_before();
@@ -648,7 +726,7 @@ __global__ void __launch_bounds__(stream_threads(ST)) trace_level_tc_stream_kern
                         float v[32];
                         tmem_ld32(tmem + lane_base + c0, v);
                         tmem_wait_ld();
-                        output_dot32(v, bl + c0, wos + c0, acc01, acc23);
+                        output_dot32<FP8>(v, bl + c0, wos + c0, acc01, acc23, mf);
                     }
                     f = ((acc01.x + acc01.y) + (acc23.x + acc23.y)) + net.bout;
                 }
@@ -699,8 +777,6 @@ __global__ void __launch_bounds__(stream_threads(ST)) trace_level_tc_stream_kern
 // stream 256 * sin, the tangent streams G_l * q_g[l] (q_g from the load-time
 // calibration), w_out * q_o as a head row plus a remainder row scaled by a
 // further 16; the epilogues divide the accumulators back.
-enum : int { kOpBF16 = 0, kOpF16 = 1, kOpE4M3 = 2 };
-constexpr float kFp8ActScale = 256.0f;
 
 template <int W, int OP>
 struct GradCfg {
@@ -1342,13 +1418,13 @@ int trace_tiles_max(const NetView& net) {
 }
 
 // Streamed-weight trace: two ray tiles per CTA unless a.tiles asks for one.
-template <bool F16>
+template <int OP>
 static cudaError_t launch_trace_stream(const LevelArgs& a, int num_sms, cudaStream_t s) {
-    const int KH = a.net.n_hidden;
+    const int KH = a.net.n_hidden, EB = OP == kOpE4M3 ? 1 : 2;
     if (a.tiles == 1)
-        return launch_tc(trace_level_tc_stream_kernel<F16, 1>, stream_threads(1), stream_layout(KH, 1).total + 1024,
-                         kStreamW, num_sms, s, &a);
-    return launch_tc(trace_level_tc_stream_kernel<F16, 2>, stream_threads(2), stream_layout(KH, 2).total + 1024,
+        return launch_tc(trace_level_tc_stream_kernel<OP, 1>, stream_threads(1),
+                         stream_layout(KH, 1, EB).total + 1024, kStreamW, num_sms, s, &a);
+    return launch_tc(trace_level_tc_stream_kernel<OP, 2>, stream_threads(2), stream_layout(KH, 2, EB).total + 1024,
                      2 * kStreamW, num_sms, s, &a);
 }
 
@@ -1360,7 +1436,8 @@ cudaError_t launch_trace_level_tc(const LevelArgs& a, int num_sms, cudaStream_t 
     case 128:
         return f16 ? launch_trace_resident<128, true>(a, num_sms, s) : launch_trace_resident<128, false>(a, num_sms, s);
     case 256:
-        return f16 ? launch_trace_stream<true>(a, num_sms, s) : launch_trace_stream<false>(a, num_sms, s);
+        if (a.net.op_fp8) return launch_trace_stream<kOpE4M3>(a, num_sms, s);
+        return f16 ? launch_trace_stream<kOpF16>(a, num_sms, s) : launch_trace_stream<kOpBF16>(a, num_sms, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -31,6 +31,14 @@ RANDOM_NET_ANGLE_FACTOR = 2.0
 FP8_ANGLE_MEDIAN_DEG = 3.0
 FP8_ANGLE_P999_DEG = 10.0
 FP8_MAGNITUDE_REL = 0.2
+# E4M3 tracing (width 256, the plain (256,3) tracer): measured on the 1080p
+# frame (row sample of 46 k rays) against FP64: hit agreement 99.7 %, hit point
+# median 2.5e-3, p99 2.0e-2, and 33 of 11,894 common hits (0.3 %) on another
+# part of the surface (up to 0.42 away: the value error moves the first zero
+# crossing past thin features).  Bounds: agreement 99 %, median 1e-2, p99 5e-2.
+FP8_TRACE_AGREEMENT = 0.99
+FP8_TRACE_POS_MEDIAN = 1e-2
+FP8_TRACE_POS_P99 = 5e-2
 PRECISIONS = [0, 1, 3]
 PRECISION_IDS = ["fp32", "bf16", "fp16"]
 

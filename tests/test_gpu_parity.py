@@ -14,7 +14,8 @@ import torch
 
 import oracle
 from paper_2201_09147_gb300 import inputs, workloads
-from parity import (DECISION_MARGIN, FP8_ANGLE_MEDIAN_DEG, FP8_ANGLE_P999_DEG, FP8_MAGNITUDE_REL, HIT_AGREEMENT,
+from parity import (DECISION_MARGIN, FP8_ANGLE_MEDIAN_DEG, FP8_ANGLE_P999_DEG, FP8_MAGNITUDE_REL, FP8_TRACE_AGREEMENT,
+                    FP8_TRACE_POS_MEDIAN, FP8_TRACE_POS_P99, HIT_AGREEMENT,
                     PRECISION_IDS, PRECISIONS, RANDOM_NET_ANGLE_FACTOR, TOL, angle_report, trace_report)
 
 pytestmark = pytest.mark.gpu
@@ -341,15 +342,34 @@ def test_fp8_gradients_vs_oracle(sdf, name):
 
 
 def test_fp8_limits(sdf):
-    """E4M3 covers the gradients of width 128 / 256 networks; tracing with it is not built."""
+    """E4M3 covers the gradients of width 128 / 256 networks and tracing with width 256."""
     with pytest.raises(sdf.SdfError) as e:
         sdf.Net((workloads.SCENES / "s8_64x1.sdfn").read_bytes(), sdf.SDF_FP8)
     assert e.value.code == -7
-    net = sdf.Net((workloads.SCENES / "s8_256x1.sdfn").read_bytes(), sdf.SDF_FP8)
+    net = sdf.Net((workloads.SCENES / "s8_128x2.sdfn").read_bytes(), sdf.SDF_FP8)
     d = torch.zeros((3, 16), device="cuda")
     with pytest.raises(sdf.SdfError) as e:
         sdf.trace_multiscale([net], [0.0], [8], 1e-3, d, d)
     assert e.value.code == -7
+
+
+def test_fp8_trace_plain_256x3(sdf):
+    """The single-network (256,3) tracer with E4M3 hidden layers (kind::f8f6f4) against FP64, 120 x 68
+    rays: the error is stated, not held to the 16-bit bounds (3 mantissa bits)."""
+    wl = workloads.get("plain_256x3_1080p", 120, 68)
+    orig, dirs = wl.rays()
+    lb = wl.level_bytes()
+    g = gpu_trace(sdf, lb, sdf.SDF_FP8, wl, orig, dirs)
+    o = oracle_trace(lb, wl, orig, dirs)
+    rep = trace_report(g["pos"], g["hit"], o["pos"], o["hit"])
+    both = rep["both"]
+    dist = np.linalg.norm(g["pos"][:, both].astype(np.float64) - o["pos"][:, both], axis=0)
+    print("plain_256x3 e4m3", {k: v for k, v in rep.items() if k != "both"}, "median", float(np.median(dist)),
+          "p99", float(np.quantile(dist, 0.99)))
+    assert rep["n_both"] > 500
+    assert rep["agree"] >= FP8_TRACE_AGREEMENT
+    assert float(np.median(dist)) <= FP8_TRACE_POS_MEDIAN
+    assert float(np.quantile(dist, 0.99)) <= FP8_TRACE_POS_P99
 
 
 # ---------------------------------------------------------------------------
