@@ -907,6 +907,7 @@ __device__ __forceinline__ int grad_point_index(const GradArgs& a, long long n_w
     if (j < 0 || k >= n_work) return -1;
     return a.list ? a.list[k] : static_cast<int>(k);
 }
+
 // The same index written to the int at shared address dst: copied there
 // asynchronously when it comes from the list (complete after
 // cp_async_wait_all in the same thread).
