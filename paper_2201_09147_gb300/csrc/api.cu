@@ -79,12 +79,19 @@ int device_info(int dev, DeviceInfo* out) {
     if (static_cast<int>(g_devices.size()) <= dev) g_devices.resize(dev + 1);
     DeviceInfo& d = g_devices[dev];
     if (d.num_sms == 0) {
-        cudaError_t e = cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev);
+        // Filled in a local record and published only once complete, so a
+        // failed step is retried by the next call instead of leaving a record
+        // without its status word or pool.
+        DeviceInfo n;
+        cudaError_t e = cudaDeviceGetAttribute(&n.num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-        e = cudaMalloc(&d.d_status, sizeof(int));
+        e = cudaMalloc(&n.d_status, sizeof(int));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(status)");
-        e = cudaMemset(d.d_status, 0, sizeof(int));
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(status)");
+        e = cudaMemset(n.d_status, 0, sizeof(int));
+        if (e != cudaSuccess) {
+            cudaFree(n.d_status);
+            return cuda_fail(e, "cudaMemset(status)");
+        }
         // Per-call scratch comes from a pool of the library that keeps what it
         // has reserved (a release threshold of 0, the default pool's, would
         // return freed memory at every synchronisation and make the next
@@ -93,11 +100,19 @@ int device_info(int dev, DeviceInfo* out) {
         props.allocType = cudaMemAllocationTypePinned;
         props.location.type = cudaMemLocationTypeDevice;
         props.location.id = dev;
-        e = cudaMemPoolCreate(&d.pool, &props);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolCreate");
+        e = cudaMemPoolCreate(&n.pool, &props);
+        if (e != cudaSuccess) {
+            cudaFree(n.d_status);
+            return cuda_fail(e, "cudaMemPoolCreate");
+        }
         uint64_t keep = ~uint64_t(0);
-        e = cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &keep);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolSetAttribute");
+        e = cudaMemPoolSetAttribute(n.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(n.pool);
+            cudaFree(n.d_status);
+            return cuda_fail(e, "cudaMemPoolSetAttribute");
+        }
+        d = n;
     }
     *out = d;
     return SDF_OK;
