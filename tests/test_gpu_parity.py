@@ -455,3 +455,37 @@ def _render_host_vs_device(sdf, wl, memory, precision=None):
     assert torch.equal(hh, hit.cpu())
     assert torch.equal(hp, pos.cpu())
     assert torch.equal(hn, nrm.cpu())
+
+
+def test_concurrent_streams_match_one_call(sdf):
+    """Chunks of a frame traced and normal-mapped on two streams at once (each call with its own
+    scratch from the library's pool) equal the single call bit for bit."""
+    wl = workloads.get("normal_map_1080p", 640, 480)
+    orig, dirs = wl.rays()
+    nets = [sdf.Net(b, sdf.SDF_BF16) for b in wl.level_bytes()]
+    fine = sdf.Net(wl.fine_bytes(), sdf.SDF_BF16)
+    o = torch.from_numpy(orig).cuda()
+    d = torch.from_numpy(dirs).cuda()
+    kw = dict(step_scale=wl.step_scale, final_mode=wl.final_mode, want_iters=False)
+    pos, _, hit, _ = sdf.trace_multiscale(nets, wl.delta, wl.caps, wl.eps, o, d, **kw)
+    nrm = sdf.normal_map(fine, pos, hit)
+    n = orig.shape[1]
+    cuts = [0, n // 3 + 5, 2 * n // 3 - 7, n]  # ragged chunks
+    main = torch.cuda.current_stream()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    chunks = [(o[:, a:b].contiguous(), d[:, a:b].contiguous()) for a, b in zip(cuts, cuts[1:])]
+    start = torch.cuda.Event()
+    start.record(main)
+    outs = []
+    for c, (oc, dc) in enumerate(chunks):
+        s = streams[c % 2]
+        s.wait_event(start)
+        with torch.cuda.stream(s):
+            pc, _, hc, _ = sdf.trace_multiscale(nets, wl.delta, wl.caps, wl.eps, oc, dc, stream=s, **kw)
+            outs.append((pc, hc, sdf.normal_map(fine, pc, hc, stream=s)))
+    for s in streams:
+        main.wait_stream(s)
+    sdf.sync_status()
+    assert torch.equal(torch.cat([x[0] for x in outs], 1), pos)
+    assert torch.equal(torch.cat([x[1] for x in outs]), hit)
+    assert torch.equal(torch.cat([x[2] for x in outs], 1), nrm)
