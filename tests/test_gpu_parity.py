@@ -489,3 +489,29 @@ def test_concurrent_streams_match_one_call(sdf):
     assert torch.equal(torch.cat([x[0] for x in outs], 1), pos)
     assert torch.equal(torch.cat([x[1] for x in outs]), hit)
     assert torch.equal(torch.cat([x[2] for x in outs], 1), nrm)
+
+
+def test_headline_bf16_frame_meets_the_stated_bounds(sdf):
+    """The benchmark frame (BF16 coarse trace + BF16 (256,3) normal mapping, 1920 x 1080, full size)
+    against the FP64 oracle on every 32nd image row (65,280 rays): hit/miss agreement >= 99.9 %,
+    hit point <= 1e-3 and normal angle <= 0.5 deg at p99.9, the bounds stated for this frame rather
+    than the precision-scaled BF16 bounds of the other tests."""
+    wl = workloads.get("normal_map_1080p")
+    orig, dirs = wl.rays()
+    lb = wl.level_bytes()
+    g = gpu_trace(sdf, lb, sdf.SDF_BF16, wl, orig, dirs)
+    fine = sdf.Net(wl.fine_bytes(), sdf.SDF_BF16)
+    nrm = sdf.normal_map(fine, g["pos_dev"], g["hit_dev"]).cpu().numpy()
+    sdf.sync_status()
+    rows = np.arange(0, wl.height, 32)
+    idx = (rows[:, None] * wl.width + np.arange(wl.width)[None, :]).ravel()
+    o = oracle_trace(lb, wl, orig, dirs, idx=idx)
+    rep = trace_report(g["pos"][:, idx], g["hit"][idx], o["pos"], o["hit"])
+    print({k: v for k, v in rep.items() if k != "both"})
+    assert rep["n_both"] > 10000
+    assert rep["agree"] >= 0.999 and rep["pos_p999"] <= 1e-3
+    hit = g["hit"][idx].astype(bool)
+    ref = oracle.Net(wl.fine_bytes()).normal_map(g["pos"][:, idx].astype(np.float64), g["hit"][idx])
+    ar = angle_report(nrm[:, idx], ref, hit)
+    print(ar)
+    assert ar["angle_p999"] <= 0.5
