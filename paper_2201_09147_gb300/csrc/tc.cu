@@ -181,15 +181,15 @@ __device__ __forceinline__ void trace_layer0(const LevelArgs& a, const float* w0
     }
 }
 
-// Output layer of one ray row from its TMEM accumulator columns c0 .. c0+31:
+// Output layer of one ray row from N of its TMEM accumulator columns:
 // acc += w_out . sin(D + b), the bias additions and the products on unit
 // pairs (two packed accumulators, for units 4j, 4j+1 and 4j+2, 4j+3).
-template <bool SCALED = false>
-__device__ __forceinline__ void output_dot32(const float (&v)[32], const float* bl, const float* wo, float2& acc01,
-                                             float2& acc23, float sc = 1.0f) {
+template <int N, bool SCALED = false>
+__device__ __forceinline__ void output_dot(const float (&v)[N], const float* bl, const float* wo, float2& acc01,
+                                           float2& acc23, float sc = 1.0f) {
     const float2 sc2 = make_float2(sc, sc);
 #pragma unroll
-    for (int j4 = 0; j4 < 8; ++j4) {
+    for (int j4 = 0; j4 < N / 4; ++j4) {
         const float4 b4 = reinterpret_cast<const float4*>(bl)[j4];
         const float4 w4 = reinterpret_cast<const float4*>(wo)[j4];
         const float2 v01 = make_float2(v[4 * j4 + 0], v[4 * j4 + 1]), v23 = make_float2(v[4 * j4 + 2], v[4 * j4 + 3]);
@@ -201,14 +201,20 @@ __device__ __forceinline__ void output_dot32(const float (&v)[32], const float* 
     }
 }
 
-// Hidden epilogue of one ray row for columns c0 .. c0+31: X row chunk =
-// 16-bit sin(D + b) (head, and with SPLIT the remainder), bias additions on
-// unit pairs.
-template <bool F16, bool SPLIT>
-__device__ __forceinline__ void hidden_epilogue32(const float (&v)[32], const float* bl, int row, int c0,
-                                                  uint32_t x_s, uint32_t xlo_s) {
+template <bool SCALED = false>
+__device__ __forceinline__ void output_dot32(const float (&v)[32], const float* bl, const float* wo, float2& acc01,
+                                             float2& acc23, float sc = 1.0f) {
+    output_dot<32, SCALED>(v, bl, wo, acc01, acc23, sc);
+}
+
+// Hidden epilogue of one ray row for N columns from c0 (N a multiple of 8):
+// X row chunks = 16-bit sin(D + b) (head, and with SPLIT the remainder),
+// bias additions on unit pairs.
+template <int N, bool F16, bool SPLIT>
+__device__ __forceinline__ void hidden_epilogue(const float (&v)[N], const float* bl, int row, int c0, uint32_t x_s,
+                                                uint32_t xlo_s) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < N / 8; ++q) {
         uint32_t pk[4], pl[4];
         const float4 ba = reinterpret_cast<const float4*>(bl + c0)[2 * q];
         const float4 bb = reinterpret_cast<const float4*>(bl + c0)[2 * q + 1];
@@ -228,6 +234,12 @@ __device__ __forceinline__ void hidden_epilogue32(const float (&v)[32], const fl
         st_shared_v4(x_s + off, pk[0], pk[1], pk[2], pk[3]);
         if (SPLIT) st_shared_v4(xlo_s + off, pl[0], pl[1], pl[2], pl[3]);
     }
+}
+
+template <bool F16, bool SPLIT>
+__device__ __forceinline__ void hidden_epilogue32(const float (&v)[32], const float* bl, int row, int c0,
+                                                  uint32_t x_s, uint32_t xlo_s) {
+    hidden_epilogue<32, F16, SPLIT>(v, bl, row, c0, x_s, xlo_s);
 }
 
 // T = blockDim.x / 128 independent ray tiles per CTA.  Tile t owns warps
@@ -414,13 +426,24 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
                 tc_fence_after();
                 const float* bl = bhs + l * W;
                 const bool rd = good && wact;
+                // the accumulator row in 16-column chunks, the next chunk loading from
+                // TMEM while the current one is processed
+                float va[16], vb[16];
+                if (rd) {
+                    tmem_ld16(tmem + lane_base, va);
+                    tmem_wait_ld();
+                }
                 if (l + 1 < KH) {
                     // hidden epilogue: X row = 16-bit sin(D + b)
-                    for (int c0 = 0; c0 < W && rd; c0 += 32) {
-                        float v[32];
-                        tmem_ld32(tmem + lane_base + c0, v);
-                        tmem_wait_ld();
-                        hidden_epilogue32<F16, SPLIT>(v, bl, ttid, c0, x_s, xlo_s);
+                    if (rd) {
+#pragma unroll
+                        for (int q = 0; q < W / 16; ++q) {
+                            float(&v)[16] = (q & 1) ? vb : va;
+                            float(&vn)[16] = (q & 1) ? va : vb;
+                            if (q + 1 < W / 16) tmem_ld16(tmem + lane_base + (q + 1) * 16u, vn);
+                            hidden_epilogue<16, F16, SPLIT>(v, bl, ttid, q * 16, x_s, xlo_s);
+                            tmem_wait_ld();
+                        }
                     }
                     fence_proxy_async_smem();
                     tc_fence_before();
@@ -428,11 +451,15 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
                 } else {
                     // output layer in FP32: f = w_out . sin(D + b) + b_out
                     float2 acc01 = make_float2(0.0f, 0.0f), acc23 = make_float2(0.0f, 0.0f);
-                    for (int c0 = 0; c0 < W && rd; c0 += 32) {
-                        float v[32];
-                        tmem_ld32(tmem + lane_base + c0, v);
-                        tmem_wait_ld();
-                        output_dot32(v, bl + c0, wos + c0, acc01, acc23);
+                    if (rd) {
+#pragma unroll
+                        for (int q = 0; q < W / 16; ++q) {
+                            float(&v)[16] = (q & 1) ? vb : va;
+                            float(&vn)[16] = (q & 1) ? va : vb;
+                            if (q + 1 < W / 16) tmem_ld16(tmem + lane_base + (q + 1) * 16u, vn);
+                            output_dot<16>(v, bl + q * 16, wos + q * 16, acc01, acc23);
+                            tmem_wait_ld();
+                        }
                     }
                     f = ((acc01.x + acc01.y) + (acc23.x + acc23.y)) + net.bout;
                 }
@@ -707,26 +734,41 @@ __global__ void __launch_bounds__(stream_threads(ST)) trace_level_tc_stream_kern
                 const bool rd = good && wact;
                 // E4M3: accumulator -> value (the operand scales q_w and 256 divided out)
                 const float mf = FP8 ? 1.0f / (net.q_w[l] * kFp8ActScale) : 1.0f;
+                // 32-column chunks, the next one loading from TMEM while the current
+                // one is processed
+                float va[32], vb[32];
+                if (rd) {
+                    tmem_ld32(tmem + lane_base, va);
+                    tmem_wait_ld();
+                }
                 if (l + 1 < KH) {
-                    for (int c0 = 0; c0 < W && rd; c0 += 32) {
-                        float v[32];
-                        tmem_ld32(tmem + lane_base + c0, v);
-                        tmem_wait_ld();
-                        if (FP8)
-                            hidden_epilogue32_e4m3(v, bl, mf, ttid, c0, x_s);
-                        else
-                            hidden_epilogue32<F16, false>(v, bl, ttid, c0, x_s, x_s);
+                    if (rd) {
+#pragma unroll
+                        for (int q = 0; q < W / 32; ++q) {
+                            float(&v)[32] = (q & 1) ? vb : va;
+                            float(&vn)[32] = (q & 1) ? va : vb;
+                            if (q + 1 < W / 32) tmem_ld32(tmem + lane_base + (q + 1) * 32u, vn);
+                            if (FP8)
+                                hidden_epilogue32_e4m3(v, bl, mf, ttid, q * 32, x_s);
+                            else
+                                hidden_epilogue32<F16, false>(v, bl, ttid, q * 32, x_s, x_s);
+                            tmem_wait_ld();
+                        }
                     }
                     fence_proxy_async_smem();
                     tc_fence_before();
                     bar_named(1, NRAY);
                 } else {
                     float2 acc01 = make_float2(0.0f, 0.0f), acc23 = make_float2(0.0f, 0.0f);
-                    for (int c0 = 0; c0 < W && rd; c0 += 32) {
-                        float v[32];
-                        tmem_ld32(tmem + lane_base + c0, v);
-                        tmem_wait_ld();
-                        output_dot32<FP8>(v, bl + c0, wos + c0, acc01, acc23, mf);
+                    if (rd) {
+#pragma unroll
+                        for (int q = 0; q < W / 32; ++q) {
+                            float(&v)[32] = (q & 1) ? vb : va;
+                            float(&vn)[32] = (q & 1) ? va : vb;
+                            if (q + 1 < W / 32) tmem_ld32(tmem + lane_base + (q + 1) * 32u, vn);
+                            output_dot32<FP8>(v, bl + q * 32, wos + q * 32, acc01, acc23, mf);
+                            tmem_wait_ld();
+                        }
                     }
                     f = ((acc01.x + acc01.y) + (acc23.x + acc23.y)) + net.bout;
                 }
