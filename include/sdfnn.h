@@ -270,6 +270,55 @@ int sdf_plan_launch(sdf_plan_t plan, void *cuda_stream);
 int sdf_plan_info(sdf_plan_t plan, int *tiles, int max_levels, int64_t *n_graph_nodes);
 void sdf_plan_free(sdf_plan_t plan);
 
+/* Frame queues: host frames rendered back to back.
+ *
+ * The paper renders image after image (its frame rates, Tab. 3; its
+ * animations, Sec. 6).  sdf_render_host does one frame per call and returns
+ * with the results in host memory, so each call pays for its own copies.  A
+ * queue keeps `depth` frames in flight instead: every slot holds device
+ * copies of one frame's rays and results and a plan (one CUDA graph: all
+ * levels of Alg. 1, then sdf_normal_map of the fine network at the hits),
+ * and while frame k's graph runs, the rays of frame k + 1 are copied in and
+ * the results of frame k - 1 copied out on two copy streams of the queue.
+ * The results are the bytes sdf_trace_multiscale + sdf_normal_map give.
+ *
+ * sdf_frame_queue_create(params, fine, n, depth, &queue)
+ *   params : as for sdf_trace_multiscale (copied; ray_time must be NULL).
+ *            The networks are not copied: keep them and `fine` alive while
+ *            the queue exists.
+ *   fine   : the normal-mapping network (not NULL).
+ *   n      : rays per frame (1 .. 2^31 - 1), the same for every frame.
+ *   depth  : frames in flight, 1 .. 4 (2 overlaps copies and kernels).
+ *   The queue owns per slot 4 * 12n + 4n + n bytes of device memory
+ *   (cudaMalloc) plus the plan's scratch.
+ * sdf_frame_queue_submit(queue, orig, dir, out_pos, out_hit, out_normal, &ticket)
+ *   Enqueues one frame: host orig, dir (3, n); host out_pos (3, n), out_hit
+ *   (n), out_normal (3, n) receive the end points, hit flags and unit
+ *   normals ((0,0,0) at misses).  Returns at once with the frame's ticket
+ *   (0, 1, 2, ... in submission order; `ticket` may be NULL), after waiting
+ *   for the frame that last used the slot when `depth` frames are in flight.
+ *   The host buffers must stay valid, and the outputs untouched, until the
+ *   frame is waited for.  Page-locked host memory lets the copies overlap the
+ *   kernels; pageable memory gives the same bytes with less overlap.
+ * sdf_frame_queue_wait(queue, ticket)
+ *   Returns when frame `ticket` and every earlier frame are in host memory
+ *   (ticket < 0: every frame submitted); a device-side timeout of any frame
+ *   since the last check (the status word of sdf_sync_status) is returned
+ *   as SDF_ERR_TIMEOUT.  A ticket not yet issued is SDF_ERR_ARG.
+ * sdf_frame_queue_free: waits for the frames in flight, then frees; NULL is
+ *   a no-op.
+ * A queue is used by one host thread at a time.
+ * Errors: as sdf_plan_create; SDF_ERR_ARG for a bad n, depth or NULL
+ * buffer; SDF_ERR_CUDA for a failed copy, launch or wait. */
+typedef struct sdf_frame_queue *sdf_frame_queue_t;
+
+int sdf_frame_queue_create(const sdf_trace_params *params, sdf_net_t fine, int64_t n, int depth,
+                           sdf_frame_queue_t *queue);
+int sdf_frame_queue_submit(sdf_frame_queue_t queue, const float *orig, const float *dir, float *out_pos,
+                           uint8_t *out_hit, float *out_normal, int64_t *ticket);
+int sdf_frame_queue_wait(sdf_frame_queue_t queue, int64_t ticket);
+void sdf_frame_queue_free(sdf_frame_queue_t queue);
+
 /* Training (FP32).
  *
  * The paper fits every network of a sequence with an external framework

@@ -1015,6 +1015,162 @@ int render_mapped(const sdf_trace_params* params, sdf_net_t fine, const float* o
     return SDF_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Frame queues: host frames rendered back to back.  Every slot owns device
+// copies of one frame's rays and results and a plan (CUDA graph) over them;
+// the rays of frame k + 1 go in and the results of frame k - 1 come out on
+// the copy streams while frame k's graph runs on the compute stream.
+// ---------------------------------------------------------------------------
+constexpr int kMaxQueueDepth = 4;
+
+struct QueueSlot {
+    void* block = nullptr;  // orig, dir, pos, normal (3n floats each), t (n floats), hit (n bytes)
+    float *orig = nullptr, *dir = nullptr, *pos = nullptr, *nrm = nullptr, *t = nullptr;
+    uint8_t* hit = nullptr;
+    sdf_plan_t plan = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_cmp = nullptr, ev_out = nullptr;
+    int64_t ticket = -1;  // frame in this slot (-1: none yet)
+};
+
+}  // namespace
+
+struct sdf_frame_queue {
+    int device = 0;
+    int depth = 0;
+    int64_t n = 0;
+    int64_t next = 0;  // ticket of the next frame
+    cudaStream_t in = nullptr, cmp = nullptr, out = nullptr;
+    QueueSlot slot[kMaxQueueDepth];
+};
+
+namespace {
+
+void free_queue(sdf_frame_queue* q) {
+    if (!q) return;
+    DeviceGuard g(q->device);
+    for (cudaStream_t st : {q->in, q->cmp, q->out})
+        if (st) cudaStreamSynchronize(st);
+    for (QueueSlot& sl : q->slot) {
+        if (sl.plan) free_plan(sl.plan);
+        if (sl.block) cudaFree(sl.block);
+        for (cudaEvent_t ev : {sl.ev_in, sl.ev_cmp, sl.ev_out})
+            if (ev) cudaEventDestroy(ev);
+    }
+    for (cudaStream_t st : {q->in, q->cmp, q->out})
+        if (st) cudaStreamDestroy(st);
+    delete q;
+}
+
+int queue_create(const sdf_trace_params* P, sdf_net_t fine, int64_t n, int depth, sdf_frame_queue_t* out) {
+    if (!out) return fail(SDF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!P) return fail(SDF_ERR_ARG, "params is NULL");
+    if (!fine) return fail(SDF_ERR_ARG, "fine is NULL");
+    if (n < 1 || n > 0x7fffffffLL) return fail(SDF_ERR_ARG, "n = %lld out of range", static_cast<long long>(n));
+    if (depth < 1 || depth > kMaxQueueDepth) return fail(SDF_ERR_ARG, "depth = %d out of range 1..%d", depth, kMaxQueueDepth);
+    if (P->ray_time) return fail(SDF_ERR_ARG, "frame queues take no per-ray times");
+    int dev = -1;
+    int rc = validate_trace_params(P, &dev);
+    if (rc) return rc;
+    if (fine->device != dev) return fail(SDF_ERR_ARG, "fine network on another device");
+    DeviceGuard g(dev);
+    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", dev);
+    sdf_frame_queue* q = new sdf_frame_queue;
+    q->device = dev;
+    q->depth = depth;
+    q->n = n;
+    cudaError_t e = cudaSuccess;
+    for (cudaStream_t* st : {&q->in, &q->cmp, &q->out})
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
+    const size_t un = static_cast<size_t>(n);
+    const size_t f3 = (3 * un * sizeof(float) + 255) & ~size_t(255), f1 = (un * sizeof(float) + 255) & ~size_t(255);
+    for (int k = 0; k < depth && e == cudaSuccess && rc == SDF_OK; ++k) {
+        QueueSlot& sl = q->slot[k];
+        for (cudaEvent_t* ev : {&sl.ev_in, &sl.ev_cmp, &sl.ev_out})
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMalloc(&sl.block, 4 * f3 + f1 + un);
+        if (e != cudaSuccess) break;
+        uint8_t* b = static_cast<uint8_t*>(sl.block);
+        sl.orig = reinterpret_cast<float*>(b);
+        sl.dir = reinterpret_cast<float*>(b + f3);
+        sl.pos = reinterpret_cast<float*>(b + 2 * f3);
+        sl.nrm = reinterpret_cast<float*>(b + 3 * f3);
+        sl.t = reinterpret_cast<float*>(b + 4 * f3);
+        sl.hit = b + 4 * f3 + f1;
+        sdf_frame_batch fb{};
+        fb.orig = sl.orig;
+        fb.dir = sl.dir;
+        fb.n = n;
+        fb.out_pos = sl.pos;
+        fb.out_t = sl.t;
+        fb.out_hit = sl.hit;
+        fb.out_normal = sl.nrm;
+        rc = plan_create(P, fine, &fb, 0, q->cmp, &sl.plan);
+    }
+    if (rc == SDF_OK && e != cudaSuccess) rc = cuda_fail(e, "creating the frame queue");
+    if (rc) {
+        free_queue(q);
+        return rc;
+    }
+    *out = q;
+    return SDF_OK;
+}
+
+int queue_submit(sdf_frame_queue* q, const float* orig, const float* dir, float* out_pos, uint8_t* out_hit,
+                 float* out_normal, int64_t* ticket) {
+    if (!q) return fail(SDF_ERR_ARG, "queue is NULL");
+    if (!orig || !dir || !out_pos || !out_hit || !out_normal) return fail(SDF_ERR_ARG, "NULL host buffer");
+    DeviceGuard g(q->device);
+    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", q->device);
+    QueueSlot& sl = q->slot[q->next % q->depth];
+    cudaError_t e = cudaSuccess;
+    // the slot's previous frame is out of its buffers once its results have left
+    if (sl.ticket >= 0 && (e = cudaEventSynchronize(sl.ev_out)) != cudaSuccess)
+        return cuda_fail(e, "waiting for the slot's previous frame");
+    const size_t b3 = 3 * static_cast<size_t>(q->n) * sizeof(float), b1 = static_cast<size_t>(q->n);
+    if ((e = cudaMemcpyAsync(sl.orig, orig, b3, cudaMemcpyHostToDevice, q->in)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(sl.dir, dir, b3, cudaMemcpyHostToDevice, q->in)) != cudaSuccess ||
+        (e = cudaEventRecord(sl.ev_in, q->in)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(q->cmp, sl.ev_in, 0)) != cudaSuccess ||
+        (e = cudaGraphLaunch(sl.plan->exec, q->cmp)) != cudaSuccess ||
+        (e = cudaEventRecord(sl.ev_cmp, q->cmp)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(q->out, sl.ev_cmp, 0)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(out_pos, sl.pos, b3, cudaMemcpyDeviceToHost, q->out)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(out_hit, sl.hit, b1, cudaMemcpyDeviceToHost, q->out)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(out_normal, sl.nrm, b3, cudaMemcpyDeviceToHost, q->out)) != cudaSuccess ||
+        (e = cudaEventRecord(sl.ev_out, q->out)) != cudaSuccess)
+        return cuda_fail(e, "enqueueing the frame");
+    sl.ticket = q->next;
+    if (ticket) *ticket = q->next;
+    ++q->next;
+    return SDF_OK;
+}
+
+int queue_wait(sdf_frame_queue* q, int64_t ticket) {
+    if (!q) return fail(SDF_ERR_ARG, "queue is NULL");
+    if (ticket >= q->next) return fail(SDF_ERR_ARG, "frame %lld was not submitted", static_cast<long long>(ticket));
+    if (ticket < 0) ticket = q->next - 1;
+    if (ticket < 0) return SDF_OK;  // nothing submitted
+    DeviceGuard g(q->device);
+    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", q->device);
+    // the copies out run in frame order on one stream: the event of the frame's
+    // slot (or of a later frame that reused it) covers the frame and all before it
+    cudaError_t e = cudaEventSynchronize(q->slot[ticket % q->depth].ev_out);
+    if (e != cudaSuccess) return cuda_fail(e, "waiting for the frame");
+    DeviceInfo di;
+    int rc = device_info(q->device, &di);
+    if (rc) return rc;
+    int status = 0;
+    e = cudaMemcpy(&status, di.d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the status word");
+    if (status != 0) {
+        const int zero = 0;
+        cudaMemcpy(di.d_status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        return fail(status, "device reported status %d (a bounded wait expired)", status);
+    }
+    return SDF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1237,6 +1393,20 @@ int sdf_plan_info(sdf_plan_t plan, int* tiles, int max_levels, int64_t* n_graph_
 }
 
 void sdf_plan_free(sdf_plan_t plan) { free_plan(plan); }
+
+int sdf_frame_queue_create(const sdf_trace_params* params, sdf_net_t fine, int64_t n, int depth,
+                           sdf_frame_queue_t* queue) {
+    return queue_create(params, fine, n, depth, queue);
+}
+
+int sdf_frame_queue_submit(sdf_frame_queue_t queue, const float* orig, const float* dir, float* out_pos,
+                           uint8_t* out_hit, float* out_normal, int64_t* ticket) {
+    return queue_submit(queue, orig, dir, out_pos, out_hit, out_normal, ticket);
+}
+
+int sdf_frame_queue_wait(sdf_frame_queue_t queue, int64_t ticket) { return queue_wait(queue, ticket); }
+
+void sdf_frame_queue_free(sdf_frame_queue_t queue) { free_queue(queue); }
 
 // ---------------------------------------------------------------------------
 // training path

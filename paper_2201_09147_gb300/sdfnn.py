@@ -25,7 +25,8 @@ EXPORTS = ["sdf_net_load", "sdf_net_load_mem", "sdf_net_info", "sdf_net_set_time
            "sdf_last_error", "sdf_trace_multiscale_noalloc", "sdf_normal_map_timed", "sdf_plan_create",
            "sdf_plan_launch", "sdf_plan_info", "sdf_plan_free", "sdf_train_shape_info", "sdf_train_forward",
            "sdf_train_backward", "sdf_fit_loss", "sdf_adam_step", "sdf_selftest_wait_timeout",
-           "sdf_measure_sine_rate"]
+           "sdf_measure_sine_rate", "sdf_frame_queue_create", "sdf_frame_queue_submit", "sdf_frame_queue_wait",
+           "sdf_frame_queue_free"]
 
 
 class SdfError(RuntimeError):
@@ -77,6 +78,11 @@ def lib():
         L.sdf_plan_free.argtypes = [vp]
         L.sdf_plan_free.restype = None
         L.sdf_render_host.argtypes = [C.POINTER(TraceParamsC), vp, vp, vp, C.c_int64, vp, vp, vp, vp]
+        L.sdf_frame_queue_create.argtypes = [C.POINTER(TraceParamsC), vp, C.c_int64, C.c_int, C.POINTER(vp)]
+        L.sdf_frame_queue_submit.argtypes = [vp, vp, vp, vp, vp, vp, C.POINTER(C.c_int64)]
+        L.sdf_frame_queue_wait.argtypes = [vp, C.c_int64]
+        L.sdf_frame_queue_free.argtypes = [vp]
+        L.sdf_frame_queue_free.restype = None
         i64p = C.POINTER(C.c_int64)
         L.sdf_train_shape_info.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, i64p, i64p]
         L.sdf_train_forward.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_int64, vp, vp, vp, vp]
@@ -279,6 +285,52 @@ def render_host(nets, delta, max_iters, eps, fine: Net, orig, dirs, out_pos, out
     _check(lib().sdf_render_host(C.byref(p), fine.handle, _ptr(orig), _ptr(dirs), n, _ptr(out_pos), _ptr(out_hit),
                                  _ptr(out_normal), C.c_void_p(_stream(stream))))
     del keep
+
+
+class FrameQueue:
+    """Host frames rendered back to back (sdf_frame_queue_*): up to `depth`
+    frames in flight, the copies of one frame overlapping the kernels of
+    another.  submit() takes host (CPU, ideally pinned) tensors that must stay
+    alive and untouched until wait() covers the frame; it returns the
+    frame's ticket."""
+
+    def __init__(self, nets, delta, max_iters, eps, fine: Net, n: int, *, depth=2, step_scale=None,
+                 box=(-1.0, 1.0), final_mode=0, time=0.0):
+        p, keep = make_params(nets, delta, max_iters, eps, step_scale, box, final_mode, time)
+        h = C.c_void_p()
+        _check(lib().sdf_frame_queue_create(C.byref(p), fine.handle, int(n), int(depth), C.byref(h)))
+        del keep
+        self.handle, self.n, self.nets, self.fine = h, int(n), list(nets), fine
+        self._pending = {}  # ticket -> the frame's host tensors, kept alive until waited for
+
+    def submit(self, orig, dirs, out_pos, out_hit, out_normal) -> int:
+        for t, shape in ((orig, (3, self.n)), (dirs, (3, self.n)), (out_pos, (3, self.n)), (out_hit, (self.n,)),
+                         (out_normal, (3, self.n))):
+            if t.device.type != "cpu" or tuple(t.shape) != shape or not t.is_contiguous():
+                raise ValueError(f"frame buffers are contiguous host tensors of shape {shape}")
+        ticket = C.c_int64()
+        _check(lib().sdf_frame_queue_submit(self.handle, _ptr(orig), _ptr(dirs), _ptr(out_pos), _ptr(out_hit),
+                                            _ptr(out_normal), C.byref(ticket)))
+        self._pending[ticket.value] = (orig, dirs, out_pos, out_hit, out_normal)
+        return ticket.value
+
+    def wait(self, ticket: int = -1):
+        _check(lib().sdf_frame_queue_wait(self.handle, int(ticket)))
+        last = max(self._pending) if ticket < 0 and self._pending else ticket
+        for k in [k for k in self._pending if k <= last]:
+            del self._pending[k]
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().sdf_frame_queue_free(self.handle)
+            self.handle = C.c_void_p()
+            self._pending.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def selftest_wait_timeout(budget_us: int = 20000, device: int = 0, stream=None):

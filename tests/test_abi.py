@@ -81,6 +81,16 @@ def test_null_arguments_are_rejected(lib):
     assert lib.sdf_plan_info(None, None, 0, None) == -1
     lib.sdf_plan_free.argtypes = [C.c_void_p]
     lib.sdf_plan_free(None)
+    # frame queues likewise
+    lib.sdf_frame_queue_create.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.POINTER(C.c_void_p)]
+    assert lib.sdf_frame_queue_create(None, None, 16, 2, C.byref(h)) == -1 and h.value is None
+    assert lib.sdf_frame_queue_create(None, None, 16, 2, None) == -1
+    lib.sdf_frame_queue_submit.argtypes = [C.c_void_p] * 6 + [C.c_void_p]
+    assert lib.sdf_frame_queue_submit(None, None, None, None, None, None, None) == -1
+    lib.sdf_frame_queue_wait.argtypes = [C.c_void_p, C.c_int64]
+    assert lib.sdf_frame_queue_wait(None, -1) == -1
+    lib.sdf_frame_queue_free.argtypes = [C.c_void_p]
+    lib.sdf_frame_queue_free(None)
 
 
 def test_training_shapes_and_null_arguments(lib):
