@@ -321,22 +321,23 @@ def main():
             e2e_step()
             e2e_times.append(time.perf_counter() - t0)
         e2e_call_value = ws * n / statistics.mean(e2e_times) / 1e6
-        # frames back to back through a frame queue (two frames in flight): each frame's rays are
+        # frames back to back through a frame queue (three frames in flight): each frame's rays are
         # copied in and its end points, hit flags and normals copied out while its neighbours'
         # kernels run; host wall clock from the first submission until the last frame's results
         # are in host memory
-        queue = sdfnn.FrameQueue(coarse, wl.delta, wl.caps, wl.eps, fine, n, depth=2, step_scale=wl.step_scale,
-                                 final_mode=wl.final_mode)
+        q_depth = 3
+        queue = sdfnn.FrameQueue(coarse, wl.delta, wl.caps, wl.eps, fine, n, depth=q_depth,
+                                 step_scale=wl.step_scale, final_mode=wl.final_mode)
         qouts = [(torch.empty((3, n)).pin_memory(), torch.empty(n, dtype=torch.uint8).pin_memory(),
-                  torch.empty((3, n)).pin_memory()) for _ in range(2)]
+                  torch.empty((3, n)).pin_memory()) for _ in range(q_depth)]
         for k in range(max(3, args.warmup)):
-            queue.submit(ho, hd, *qouts[k % 2])
+            queue.submit(ho, hd, *qouts[k % q_depth])
         queue.wait()
         q_frames = max(10, args.steps // 2)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(q_frames):
-            queue.submit(ho, hd, *qouts[k % 2])
+            queue.submit(ho, hd, *qouts[k % q_depth])
         queue.wait()
         q_dt = time.perf_counter() - t0
         queue.close()
@@ -352,7 +353,7 @@ def main():
               "clocks": clk, "gpu_launches": 3 * args.steps,
               "e2e": ({"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 3 * 4 * n,
                        "d2h_bytes_per_step": (3 + 3) * 4 * n + n,
-                       "api": "sdf_frame_queue (two frames in flight)",
+                       "api": "sdf_frame_queue (three frames in flight, alternating two compute streams)",
                        "transfer": "pinned host buffers: every frame's rays copied in and its end points, hit "
                                    "flags and normals copied out by the queue's copy streams while the "
                                    "neighbouring frames' kernels run (no L2 flush: each frame's rays arrive "

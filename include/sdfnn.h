@@ -279,7 +279,9 @@ void sdf_plan_free(sdf_plan_t plan);
  * copies of one frame's rays and results and a plan (one CUDA graph: all
  * levels of Alg. 1, then sdf_normal_map of the fine network at the hits),
  * and while frame k's graph runs, the rays of frame k + 1 are copied in and
- * the results of frame k - 1 copied out on two copy streams of the queue.
+ * the results of frame k - 1 copied out on two copy streams of the queue;
+ * consecutive frames alternate between two compute streams, so a frame's
+ * kernels may start while the previous frame's last rays are still traced.
  * The results are the bytes sdf_trace_multiscale + sdf_normal_map give.
  *
  * sdf_frame_queue_create(params, fine, n, depth, &queue)

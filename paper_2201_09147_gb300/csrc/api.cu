@@ -1019,7 +1019,9 @@ int render_mapped(const sdf_trace_params* params, sdf_net_t fine, const float* o
 // Frame queues: host frames rendered back to back.  Every slot owns device
 // copies of one frame's rays and results and a plan (CUDA graph) over them;
 // the rays of frame k + 1 go in and the results of frame k - 1 come out on
-// the copy streams while frame k's graph runs on the compute stream.
+// the copy streams while frame k's graph runs.  Consecutive frames run on
+// two compute streams, so one frame's trace can start on the SMs the tail of
+// the previous frame's trace leaves idle.
 // ---------------------------------------------------------------------------
 constexpr int kMaxQueueDepth = 4;
 
@@ -1039,7 +1041,7 @@ struct sdf_frame_queue {
     int depth = 0;
     int64_t n = 0;
     int64_t next = 0;  // ticket of the next frame
-    cudaStream_t in = nullptr, cmp = nullptr, out = nullptr;
+    cudaStream_t in = nullptr, cmp[2] = {}, out = nullptr;
     QueueSlot slot[kMaxQueueDepth];
 };
 
@@ -1048,7 +1050,7 @@ namespace {
 void free_queue(sdf_frame_queue* q) {
     if (!q) return;
     DeviceGuard g(q->device);
-    for (cudaStream_t st : {q->in, q->cmp, q->out})
+    for (cudaStream_t st : {q->in, q->cmp[0], q->cmp[1], q->out})
         if (st) cudaStreamSynchronize(st);
     for (QueueSlot& sl : q->slot) {
         if (sl.plan) free_plan(sl.plan);
@@ -1056,7 +1058,7 @@ void free_queue(sdf_frame_queue* q) {
         for (cudaEvent_t ev : {sl.ev_in, sl.ev_cmp, sl.ev_out})
             if (ev) cudaEventDestroy(ev);
     }
-    for (cudaStream_t st : {q->in, q->cmp, q->out})
+    for (cudaStream_t st : {q->in, q->cmp[0], q->cmp[1], q->out})
         if (st) cudaStreamDestroy(st);
     delete q;
 }
@@ -1080,7 +1082,7 @@ int queue_create(const sdf_trace_params* P, sdf_net_t fine, int64_t n, int depth
     q->depth = depth;
     q->n = n;
     cudaError_t e = cudaSuccess;
-    for (cudaStream_t* st : {&q->in, &q->cmp, &q->out})
+    for (cudaStream_t* st : {&q->in, &q->cmp[0], &q->cmp[1], &q->out})
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
     const size_t un = static_cast<size_t>(n);
     const size_t f3 = (3 * un * sizeof(float) + 255) & ~size_t(255), f1 = (un * sizeof(float) + 255) & ~size_t(255);
@@ -1105,7 +1107,7 @@ int queue_create(const sdf_trace_params* P, sdf_net_t fine, int64_t n, int depth
         fb.out_t = sl.t;
         fb.out_hit = sl.hit;
         fb.out_normal = sl.nrm;
-        rc = plan_create(P, fine, &fb, 0, q->cmp, &sl.plan);
+        rc = plan_create(P, fine, &fb, 0, q->cmp[0], &sl.plan);
     }
     if (rc == SDF_OK && e != cudaSuccess) rc = cuda_fail(e, "creating the frame queue");
     if (rc) {
@@ -1123,6 +1125,7 @@ int queue_submit(sdf_frame_queue* q, const float* orig, const float* dir, float*
     DeviceGuard g(q->device);
     if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", q->device);
     QueueSlot& sl = q->slot[q->next % q->depth];
+    const cudaStream_t cmp = q->cmp[q->next & 1];
     cudaError_t e = cudaSuccess;
     // the slot's previous frame is out of its buffers once its results have left
     if (sl.ticket >= 0 && (e = cudaEventSynchronize(sl.ev_out)) != cudaSuccess)
@@ -1131,9 +1134,9 @@ int queue_submit(sdf_frame_queue* q, const float* orig, const float* dir, float*
     if ((e = cudaMemcpyAsync(sl.orig, orig, b3, cudaMemcpyHostToDevice, q->in)) != cudaSuccess ||
         (e = cudaMemcpyAsync(sl.dir, dir, b3, cudaMemcpyHostToDevice, q->in)) != cudaSuccess ||
         (e = cudaEventRecord(sl.ev_in, q->in)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(q->cmp, sl.ev_in, 0)) != cudaSuccess ||
-        (e = cudaGraphLaunch(sl.plan->exec, q->cmp)) != cudaSuccess ||
-        (e = cudaEventRecord(sl.ev_cmp, q->cmp)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(cmp, sl.ev_in, 0)) != cudaSuccess ||
+        (e = cudaGraphLaunch(sl.plan->exec, cmp)) != cudaSuccess ||
+        (e = cudaEventRecord(sl.ev_cmp, cmp)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(q->out, sl.ev_cmp, 0)) != cudaSuccess ||
         (e = cudaMemcpyAsync(out_pos, sl.pos, b3, cudaMemcpyDeviceToHost, q->out)) != cudaSuccess ||
         (e = cudaMemcpyAsync(out_hit, sl.hit, b1, cudaMemcpyDeviceToHost, q->out)) != cudaSuccess ||
