@@ -515,3 +515,26 @@ def test_headline_bf16_frame_meets_the_stated_bounds(sdf):
     ar = angle_report(nrm[:, idx], ref, hit)
     print(ar)
     assert ar["angle_p999"] <= 0.5
+
+
+def test_headline_bf16_full_frame_against_the_oracle(sdf):
+    """Every ray of the benchmark frame (2,073,600 rays: BF16 coarse trace + BF16 (256,3) normal mapping)
+    against the FP64 oracle run on the whole frame: hit/miss agreement, hit point and normal angle at the
+    same point over all common hits, with the bounds stated for this frame."""
+    wl = workloads.get("normal_map_1080p")
+    orig, dirs = wl.rays()
+    lb = wl.level_bytes()
+    g = gpu_trace(sdf, lb, sdf.SDF_BF16, wl, orig, dirs)
+    fine = sdf.Net(wl.fine_bytes(), sdf.SDF_BF16)
+    nrm = sdf.normal_map(fine, g["pos_dev"], g["hit_dev"]).cpu().numpy()
+    sdf.sync_status()
+    o = oracle_trace(lb, wl, orig, dirs)
+    rep = trace_report(g["pos"], g["hit"], o["pos"], o["hit"])
+    print({k: v for k, v in rep.items() if k != "both"})
+    assert rep["n_both"] > 300000
+    assert rep["agree"] >= 0.999 and rep["pos_p999"] <= 1e-3
+    hit = g["hit"].astype(bool)
+    ref = oracle.Net(wl.fine_bytes()).normal_map(g["pos"].astype(np.float64), g["hit"])
+    ar = angle_report(nrm, ref, hit)
+    print(ar)
+    assert ar["angle_p999"] <= 0.5
