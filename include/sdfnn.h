@@ -13,8 +13,8 @@
  *   - Buffers passed to sdf_trace_multiscale, sdf_normals and sdf_normal_map
  *     are caller-owned DEVICE memory (cudaMalloc / torch CUDA tensors) on the
  *     device the networks were loaded on.  Host pointers are rejected with
- *     SDF_ERR_ARG before any kernel runs.  sdf_render_host is the one call
- *     that takes host memory.
+ *     SDF_ERR_ARG before any kernel runs.  sdf_render_host and
+ *     sdf_frame_queue_submit are the calls that take host memory.
  *   - Calls are asynchronous on `cuda_stream` (a cudaStream_t; NULL means the
  *     legacy default stream).  Argument errors are returned immediately.
  *     Errors a kernel detects on the device (a bounded wait that expired:
