@@ -320,7 +320,7 @@ def main():
             t0 = time.perf_counter()
             e2e_step()
             e2e_times.append(time.perf_counter() - t0)
-        e2e_call_value = ws * n / statistics.mean(e2e_times) / 1e6
+        e2e_call_value, _ = job_throughput(1e3 * sum(e2e_times), n, len(e2e_times), ws, "cuda")
         # frames back to back through a frame queue (three frames in flight): each frame's rays are
         # copied in and its end points, hit flags and normals copied out while its neighbours'
         # kernels run; host wall clock from the first submission until the last frame's results
@@ -341,7 +341,7 @@ def main():
         queue.wait()
         q_dt = time.perf_counter() - t0
         queue.close()
-        e2e_value = ws * n * q_frames / q_dt / 1e6
+        e2e_value, _ = job_throughput(1e3 * q_dt, n, q_frames, ws, "cuda")
 
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
