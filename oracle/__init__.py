@@ -78,7 +78,6 @@ def lib():
         L.oracle_net_from_bytes.argtypes = [C.c_char_p, C.c_size_t]
         L.oracle_net_free.argtypes = [vp]
         L.oracle_net_shape.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
-        L.oracle_net_round_hidden_bf16.argtypes = [vp]
         L.oracle_net_eval.restype = C.c_double
         L.oracle_net_eval.argtypes = [vp, dp]
         L.oracle_net_grad.argtypes = [vp, dp, dp]
@@ -117,12 +116,10 @@ def default_threads() -> int:
 class Net:
     """An SDFN network loaded by the oracle (folded, float64)."""
 
-    def __init__(self, data: bytes, round_hidden_bf16: bool = False):
+    def __init__(self, data: bytes):
         self._h = lib().oracle_net_from_bytes(data, len(data))
         if not self._h:
             raise ValueError("oracle could not parse the SDFN image")
-        if round_hidden_bf16:
-            lib().oracle_net_round_hidden_bf16(self._h)
         a, b, c = C.c_int(), C.c_int(), C.c_int()
         lib().oracle_net_shape(self._h, C.byref(a), C.byref(b), C.byref(c))
         self.in_dim, self.width, self.n_hidden = a.value, b.value, c.value

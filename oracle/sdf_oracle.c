@@ -138,26 +138,6 @@ void oracle_net_shape(const oracle_net *n, int *in_dim, int *width, int *n_hidde
     *n_hidden = n->n_hidden;
 }
 
-/* Round every folded sine-layer weight of the hidden (width x width) layers
- * to bfloat16 (round to nearest even).  Used to separate weight-quantisation
- * error from arithmetic error; not part of the method. */
-static double round_bf16(double x) {
-    float f = (float)x;
-    uint32_t u;
-    memcpy(&u, &f, 4);
-    if ((u & 0x7f800000u) == 0x7f800000u) return x;
-    uint32_t lsb = (u >> 16) & 1u;
-    u += 0x7fffu + lsb;
-    u &= 0xffff0000u;
-    memcpy(&f, &u, 4);
-    return (double)f;
-}
-
-void oracle_net_round_hidden_bf16(oracle_net *n) {
-    for (int l = 1; l < n->n_sine; ++l)
-        for (size_t i = 0; i < (size_t)n->width * n->width; ++i) n->W[l][i] = round_bf16(n->W[l][i]);
-}
-
 /* Eq. 2: f(p) = W_n f_{n-1}(...f_0(p)) + b_n with f_i(x) = sin(W_i x + b_i). */
 double oracle_net_eval(const oracle_net *n, const double *p) {
     int w = n->width;

@@ -276,6 +276,66 @@ def test_nested_sphere_shells_equal_single_level():
         assert abs(a.tau - b.tau) <= 2e-8 / cosang + 1e-12
 
 
+def test_final_mode_stops_on_the_last_shell_and_mode_0_ignores_it():
+    """delta_m is used only with final_mode 1 (reading R4): on the exact sphere SDF |p - c| - r a
+    level with final_mode 1 and delta 0.1 ends on the sphere of radius r + 0.1 (the first root of
+    f - delta, a quadratic), while final_mode 0 ends on the surface itself whatever delta_m says."""
+    c, r, d = np.array([0.05, 0.0, -0.1]), 0.4, 0.1
+    shell = oracle.TraceParams([oracle.SDF.sphere(c, r)], [d], [300], [1.0], 1e-9, final_mode=1)
+    surface = oracle.TraceParams([oracle.SDF.sphere(c, r)], [d], [300], [1.0], 1e-9, final_mode=0)
+    o_all, v_all = inputs.random_rays(8, 300)
+    checked = 0
+    for i in range(o_all.shape[1]):
+        o = o_all[:, i].astype(np.float64)
+        v = v_all[:, i].astype(np.float64)
+        v /= np.linalg.norm(v)
+        t_shell, t_surf = ray_sphere(o, v, c, r + d), ray_sphere(o, v, c, r)
+        a, b = shell.trace_ray(o, v), surface.trace_ray(o, v)
+        if t_shell is None:
+            assert a.hit == 0 and b.hit == 0
+            continue
+        cos_shell = abs((o + t_shell * v - c) @ v) / (r + d)
+        if cos_shell < 0.2 or (t_surf is not None and abs((o + t_surf * v - c) @ v) / r < 0.2):
+            continue  # grazing
+        checked += 1
+        assert a.hit == 1 and abs(a.tau - t_shell) <= 1e-9 / cos_shell + 1e-12
+        assert abs(np.linalg.norm(a.p - c) - (r + d)) <= 1e-9
+        if t_surf is None:
+            assert b.hit == 0
+        else:
+            assert b.hit == 1 and abs(np.linalg.norm(b.p - c) - r) <= 1e-9
+    assert checked > 50
+
+
+def test_normal_map_is_the_unit_gradient_masked_and_zero_at_critical_points():
+    """Normal mapping (Sec. 5, reading R10) on a (w, 0) network whose gradient is known in closed
+    form, sum_k c_k cos(w_k . p + b_k) w_k: the unit vector where the mask is set, (0, 0, 0) where it
+    is not, and (0, 0, 0) where |grad f| < 1e-12 (output weights scaled to make the gradient vanish)."""
+    net = single_sine_layer_net(23, 16)
+    W = net.weights[0].astype(np.float64)
+    b = net.biases[0].astype(np.float64)
+    cw = net.weights[1][0].astype(np.float64)
+    rng = np.random.default_rng(3)
+    pts = rng.uniform(-1, 1, (3, 40))
+    mask = (np.arange(40) % 3 != 0).astype(np.uint8)
+    out = oracle.Net(inputs.net_to_bytes(net)).normal_map(pts, mask)
+    for i in range(40):
+        if not mask[i]:
+            assert np.all(out[:, i] == 0.0)
+            continue
+        g = (cw * np.cos(W @ pts[:, i] + b)) @ W
+        assert np.max(np.abs(out[:, i] - g / np.linalg.norm(g))) <= 1e-12
+    # a network with a vanishing gradient everywhere, and one just above the threshold
+    for scale, zero in ((1e-16, True), (1e-6, False)):
+        tiny = single_sine_layer_net(23, 16)
+        tiny.weights[1] = (tiny.weights[1].astype(np.float64) * scale).astype(tiny.weights[1].dtype)
+        got = oracle.Net(inputs.net_to_bytes(tiny)).normal_map(pts[:, :5])
+        if zero:
+            assert np.all(got == 0.0)
+        else:
+            assert np.allclose(np.linalg.norm(got, axis=0), 1.0, atol=1e-12)
+
+
 def test_alg1_steps_before_testing():
     """Alg. 1 applies p = p + t v before re-testing t: one step lands exactly on a plane SDF."""
     # a sphere of huge radius is a plane to within 1e-12 near the ray
