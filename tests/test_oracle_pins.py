@@ -336,6 +336,24 @@ def test_normal_map_is_the_unit_gradient_masked_and_zero_at_critical_points():
             assert np.allclose(np.linalg.norm(got, axis=0), 1.0, atol=1e-12)
 
 
+def test_batch_driver_is_the_pinned_single_ray_trace():
+    """The threaded batch driver (all rays, or an index subset, several threads) gives, in list order,
+    exactly the single-ray trace that the closed-form pins above check."""
+    c, r = np.array([0.0, 0.1, 0.0]), 0.45
+    tp = oracle.TraceParams([oracle.SDF.sphere(c, r + 0.05), oracle.SDF.sphere(c, r)], [0.05, 0.0], [60, 60],
+                            [1.0, 1.0], 1e-7)
+    o_all, v_all = inputs.random_rays(9, 257)
+    o32, v32 = o_all.astype(np.float32), v_all.astype(np.float32)
+    idx = np.array([256, 3, 3, 100, 0, 17], np.int64)
+    for sel, threads in ((None, 5), (idx, 3)):
+        res = tp.trace_batch(o32, v32, idx=sel, threads=threads)
+        rows = range(o32.shape[1]) if sel is None else sel
+        for k, i in enumerate(rows):
+            one = tp.trace_ray(o32[:, i].astype(np.float64), v32[:, i].astype(np.float64))
+            assert res["hit"][k] == one.hit and res["iters"][k] == one.iters
+            assert np.array_equal(res["pos"][:, k], np.array(one.p[:3]))
+
+
 def test_alg1_steps_before_testing():
     """Alg. 1 applies p = p + t v before re-testing t: one step lands exactly on a plane SDF."""
     # a sphere of huge radius is a plane to within 1e-12 near the ray
