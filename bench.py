@@ -521,6 +521,16 @@ def main():
             result["comparisons"][f"{name}_hits"] = int(plan3.hit.sum().item())
             plan3.close()
 
+        # neural normal mapping onto the full-size mesh (displaced icosphere, subdivision 7), BF16
+        mesh_h, _ = workloads.mesh_points(7)
+        mesh = torch.from_numpy(mesh_h).cuda()
+        mesh_out = torch.empty_like(mesh)
+        ms_mesh = timed_ms(lambda: sdfnn.normal_map(fine, mesh, out=mesh_out), 20)
+        result["comparisons"]["mesh_normal_map"] = {"vertices": int(mesh.shape[1]), "ms": ms_mesh,
+                                                    "Mvertices_s": mesh.shape[1] / (ms_mesh / 1e3) / 1e6,
+                                                    "net": "(256,3) BF16"}
+        del mesh, mesh_out
+
         # 32 animated frames of mixed sizes: one autotuned plan (CUDA graph) against per-frame calls
         wa = workloads.get("animation_32")
         if all((workloads.SCENES / f).exists() for f in wa.levels + [wa.fine]):

@@ -314,6 +314,29 @@ def test_mesh_normal_map(sdf, precision):
     assert ar["angle_p999"] <= TOL[precision][2]
 
 
+_MESH7 = {}
+
+
+@pytest.mark.parametrize("precision", [1, 3], ids=["bf16", "fp16"])
+def test_mesh_normal_map_full_size_sampled(sdf, precision):
+    """Neural normal mapping onto the full-size mesh (displaced icosphere, subdivision 7: 163,842
+    vertices, the benchmark's size): every normal unit length, the oracle on 3,000 sampled vertices."""
+    if "pts" not in _MESH7:
+        _MESH7["pts"], _MESH7["frac"] = workloads.mesh_points(subdivisions=7)
+    pts = _MESH7["pts"]
+    assert pts.shape[1] == 163842 and _MESH7["frac"] > 0.9
+    fine_b = (workloads.SCENES / "s8_256x3.sdfn").read_bytes()
+    fine = sdf.Net(fine_b, precision)
+    out = sdf.normal_map(fine, torch.from_numpy(pts).cuda()).cpu().numpy()
+    sdf.sync_status()
+    assert np.allclose(np.linalg.norm(out, axis=0), 1.0, atol=1e-5)
+    idx = np.sort(np.unique((inputs.uniform01(77, 3000) * pts.shape[1]).astype(np.int64)))
+    ref = oracle.Net(fine_b).normal_map(pts[:, idx].astype(np.float64))
+    ar = angle_report(out[:, idx], ref)
+    print(ar)
+    assert ar["angle_p999"] <= TOL[precision][2]
+
+
 @pytest.mark.parametrize("name", ["s8_256x3", "s8_256x2", "s8_128x2", "s8_256x1"])
 def test_fp8_gradients_vs_oracle(sdf, name):
     """E4M3 hidden layers (kind::f8f6f4) against FP64: surface points of the displaced
