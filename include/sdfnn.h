@@ -205,8 +205,10 @@ int sdf_render_host(const sdf_trace_params *params, sdf_net_t fine, const float 
  *   - Every call uses the same array: it zeroes the counters at its start,
  *     and calls whose work overlaps on the GPU (other streams, other host
  *     threads) race on it and corrupt each other's results.  Serialise them.
- *   - Device-side timeouts of these launches are latched in the array, not
- *     in the status word sdf_sync_status reads. */
+ *   - Device-side timeouts of these launches are latched in a status word
+ *     inside the array; sdf_sync_status reads and clears it together with
+ *     the library's per-device status word, so a timed-out call is reported
+ *     as SDF_ERR_TIMEOUT by the next sdf_sync_status on that device. */
 int sdf_trace_multiscale_noalloc(const sdf_trace_params *params, const float *orig, const float *dir, int64_t n,
                                  float *out_pos, float *out_t, uint8_t *out_hit, uint16_t *out_iters,
                                  void *cuda_stream);
@@ -386,6 +388,28 @@ int sdf_sync_status(void *cuda_stream);
  * Errors: SDF_ERR_ARG, SDF_ERR_CUDA (also when the expiry was not reported),
  * or a status already pending on the device before the call. */
 int sdf_selftest_wait_timeout(int device, int64_t budget_us, void *cuda_stream);
+
+/* Self-test of the timeout reporting of sdf_trace_multiscale_noalloc (the
+ * paper has no counterpart): the bounded wait of sdf_selftest_wait_timeout,
+ * latching into the status word of the allocation-free entry point's static
+ * array instead of the library's per-device word.  Returns SDF_OK when the
+ * wait expired and sdf_sync_status reported (and cleared) SDF_ERR_TIMEOUT
+ * from that array.  Sets the array up on `device` like the entry point's
+ * first call does (allocates nothing).
+ * Errors: SDF_ERR_ARG, SDF_ERR_CUDA, or a status already pending. */
+int sdf_selftest_noalloc_timeout(int device, int64_t budget_us, void *cuda_stream);
+
+/* Step a1 on the host, for the training calls: the folded parameter vector
+ * theta (Eq. 2 with the sine frequencies multiplied in: W_0, b_0 by omega0,
+ * the hidden W_i, b_i by omega, the output row unchanged; FP64 products
+ * rounded to FP32) of an SDFN image, in the file's order.  Host memory only;
+ * no device is touched.
+ *   theta    : host float32 buffer of `capacity` entries, or NULL to query.
+ *   count, in_dim, width, n_hidden : outputs (each may be NULL).
+ * Errors: SDF_ERR_ARG (NULL bytes, capacity below the parameter count),
+ * SDF_ERR_FORMAT, SDF_ERR_NONFINITE. */
+int sdf_theta_from_image(const void *bytes, size_t n_bytes, float *theta, int64_t capacity, int64_t *count,
+                         int *in_dim, int *width, int *n_hidden);
 
 /* Measurement helper: the throughput, in sines per second on all SMs, of the
  * hardware sine the tensor-core kernels use (independent chains of

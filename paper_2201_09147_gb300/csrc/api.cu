@@ -287,12 +287,20 @@ void free_net(sdf_net* n) {
     delete n;
 }
 
-int load_from_memory(const uint8_t* buf, size_t len, int precision, int device, sdf_net_t* out) {
-    if (!out) return fail(SDF_ERR_ARG, "out is NULL");
-    *out = nullptr;
+// An SDFN image parsed on the host: shape and the folded parameters of
+// Eq. 2 in FP64 (layer 0 multiplied by omega0, hidden layers by omega, the
+// output layer unchanged), so every sine layer reads plain sin(W x + b).
+struct ParsedImage {
+    int IN = 0, W = 0, KH = 0;
+    std::vector<std::vector<double>> Wl, bl;  // layers 0..KH: [W][fan_in] row-major, [W]
+    std::vector<double> wout;
+    float bout = 0.0f;
+};
+
+// Parses and folds an SDFN image; checks the header, the size and that every
+// parameter is finite (shape support is the caller's business).
+int parse_image(const uint8_t* buf, size_t len, ParsedImage* P) {
     if (!buf) return fail(SDF_ERR_ARG, "bytes is NULL");
-    if (precision != SDF_FP32 && precision != SDF_BF16 && precision != SDF_FP16 && precision != SDF_FP8)
-        return fail(SDF_ERR_ARG, "unknown precision %d", precision);
     if (len < 32 || std::memcmp(buf, "SDFN", 4) != 0) return fail(SDF_ERR_FORMAT, "not an SDFN image");
     const uint32_t version = rd_u32(buf + 4), in_dim = rd_u32(buf + 8), width = rd_u32(buf + 12);
     const uint32_t n_hidden = rd_u32(buf + 16), flags = rd_u32(buf + 28);
@@ -303,33 +311,52 @@ int load_from_memory(const uint8_t* buf, size_t len, int precision, int device, 
     const size_t count = static_cast<size_t>(width) * in_dim + width +
                          static_cast<size_t>(n_hidden) * (static_cast<size_t>(width) * width + width) + width + 1;
     if (len != 32 + 4 * count) return fail(SDF_ERR_FORMAT, "SDFN size %zu, expected %zu", len, 32 + 4 * count);
-    if ((in_dim != 3 && in_dim != 4) || (width != 64 && width != 128 && width != 256) || n_hidden < 1 ||
-        n_hidden > static_cast<uint32_t>(kMaxHidden))
-        return fail(SDF_ERR_UNSUPPORTED, "shape in=%u (w=%u, k=%u) not supported (in 3|4, w 64|128|256, 1<=k<=%d)",
-                    in_dim, width, n_hidden, kMaxHidden);
-    if (precision == SDF_FP8 && width < 128)
-        return fail(SDF_ERR_UNSUPPORTED, "E4M3 hidden layers need width 128 or 256 (got %u)", width);
     if (!std::isfinite(omega0) || !std::isfinite(omega)) return fail(SDF_ERR_NONFINITE, "non-finite omega");
     const uint8_t* q = buf + 32;
     for (size_t i = 0; i < count; ++i)
         if (!std::isfinite(rd_f32(q + 4 * i))) return fail(SDF_ERR_NONFINITE, "non-finite parameter %zu", i);
-
     const int W = static_cast<int>(width), IN = static_cast<int>(in_dim), KH = static_cast<int>(n_hidden);
     const bool folded = (flags & 1u) != 0;
-    // folded FP64 copies: layer 0 by omega0, hidden layers by omega, output unchanged
-    std::vector<std::vector<double>> Wl(KH + 1), bl(KH + 1);
+    P->IN = IN;
+    P->W = W;
+    P->KH = KH;
+    P->Wl.assign(KH + 1, {});
+    P->bl.assign(KH + 1, {});
     size_t o = 0;
     for (int l = 0; l <= KH; ++l) {
         const int fan_in = l == 0 ? IN : W;
         const double s = folded ? 1.0 : (l == 0 ? omega0 : omega);
-        Wl[l].resize(static_cast<size_t>(W) * fan_in);
-        bl[l].resize(W);
-        for (auto& v : Wl[l]) v = s * rd_f32(q + 4 * o++);
-        for (auto& v : bl[l]) v = s * rd_f32(q + 4 * o++);
+        P->Wl[l].resize(static_cast<size_t>(W) * fan_in);
+        P->bl[l].resize(W);
+        for (auto& v : P->Wl[l]) v = s * rd_f32(q + 4 * o++);
+        for (auto& v : P->bl[l]) v = s * rd_f32(q + 4 * o++);
     }
-    std::vector<double> wout(W);
-    for (auto& v : wout) v = rd_f32(q + 4 * o++);
-    const float bout = rd_f32(q + 4 * o++);
+    P->wout.resize(W);
+    for (auto& v : P->wout) v = rd_f32(q + 4 * o++);
+    P->bout = rd_f32(q + 4 * o++);
+    return SDF_OK;
+}
+
+int load_from_memory(const uint8_t* buf, size_t len, int precision, int device, sdf_net_t* out) {
+    if (!out) return fail(SDF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!buf) return fail(SDF_ERR_ARG, "bytes is NULL");
+    if (precision != SDF_FP32 && precision != SDF_BF16 && precision != SDF_FP16 && precision != SDF_FP8)
+        return fail(SDF_ERR_ARG, "unknown precision %d", precision);
+    ParsedImage img;
+    int rc = parse_image(buf, len, &img);
+    if (rc) return rc;
+    if ((img.IN != 3 && img.IN != 4) || (img.W != 64 && img.W != 128 && img.W != 256) || img.KH < 1 ||
+        img.KH > kMaxHidden)
+        return fail(SDF_ERR_UNSUPPORTED, "shape in=%d (w=%d, k=%d) not supported (in 3|4, w 64|128|256, 1<=k<=%d)",
+                    img.IN, img.W, img.KH, kMaxHidden);
+    if (precision == SDF_FP8 && img.W < 128)
+        return fail(SDF_ERR_UNSUPPORTED, "E4M3 hidden layers need width 128 or 256 (got %d)", img.W);
+    const int W = img.W, IN = img.IN, KH = img.KH;
+    const std::vector<std::vector<double>>& Wl = img.Wl;
+    const std::vector<std::vector<double>>& bl = img.bl;
+    const std::vector<double>& wout = img.wout;
+    const float bout = img.bout;
 
     // Lipschitz bound of Eq. 2 (sin is 1-Lipschitz)
     double L = top_singular_value(Wl[0], W, IN);
@@ -715,6 +742,28 @@ int noalloc_setup(int dev, NoAllocDevice* out) {
         d.ready = true;
     }
     *out = d;
+    return SDF_OK;
+}
+
+// Reads and clears the status word of the static scratch on `dev` (the
+// caller has made `dev` current).  *status is 0 when no call of the
+// allocation-free entry point has set the array up on this device.
+int noalloc_take_status(int dev, int* status) {
+    *status = 0;
+    if (dev < 0 || dev >= 64) return SDF_OK;
+    NoAllocLayout* sc = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_dev[dev].ready) return SDF_OK;
+        sc = g_noalloc_dev[dev].scratch;
+    }
+    cudaError_t e = cudaMemcpy(status, &sc->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the status word of the static scratch");
+    if (*status != 0) {
+        const int zero = 0;
+        e = cudaMemcpy(&sc->status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "clearing the status word of the static scratch");
+    }
     return SDF_OK;
 }
 
@@ -1345,8 +1394,14 @@ int sdf_sync_status(void* cuda_stream) {
     if (status != 0) {
         const int zero = 0;
         cudaMemcpy(di.d_status, &zero, sizeof(int), cudaMemcpyHostToDevice);
-        return fail(status, "device reported status %d (a bounded wait expired)", status);
     }
+    // the allocation-free entry point latches its kernels' errors in its own array
+    int na_status = 0;
+    if ((rc = noalloc_take_status(dev, &na_status))) return rc;
+    if (status != 0) return fail(status, "device reported status %d (a bounded wait expired)", status);
+    if (na_status != 0)
+        return fail(na_status, "device reported status %d in sdf_trace_multiscale_noalloc (a bounded wait expired)",
+                    na_status);
     return SDF_OK;
 }
 
@@ -1586,6 +1641,54 @@ int sdf_selftest_wait_timeout(int device, int64_t budget_us, void* cuda_stream) 
     rc = sdf_sync_status(cuda_stream);
     if (rc == SDF_ERR_TIMEOUT) return SDF_OK;
     return rc ? rc : fail(SDF_ERR_CUDA, "the bounded wait did not report its expiry");
+}
+
+int sdf_selftest_noalloc_timeout(int device, int64_t budget_us, void* cuda_stream) {
+    if (budget_us < 1 || budget_us > 10000000) return fail(SDF_ERR_ARG, "budget_us out of range 1..1e7");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return fail(SDF_ERR_ARG, "device %d not available", device);
+    }
+    DeviceGuard g(device);
+    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", device);
+    NoAllocDevice nd;
+    int rc = noalloc_setup(device, &nd);
+    if (rc) return rc;
+    rc = sdf_sync_status(cuda_stream);
+    if (rc) return rc;
+    cudaError_t e = launch_wait_timeout_selftest(&nd.scratch->status,
+                                                 static_cast<unsigned long long>(budget_us) * 1000ull,
+                                                 static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "launching the timeout self-test");
+    rc = sdf_sync_status(cuda_stream);
+    if (rc == SDF_ERR_TIMEOUT) return SDF_OK;
+    return rc ? rc : fail(SDF_ERR_CUDA, "the expiry latched in the static scratch was not reported");
+}
+
+int sdf_theta_from_image(const void* bytes, size_t n_bytes, float* theta, int64_t capacity, int64_t* count,
+                         int* in_dim, int* width, int* n_hidden) {
+    ParsedImage img;
+    int rc = parse_image(static_cast<const uint8_t*>(bytes), n_bytes, &img);
+    if (rc) return rc;
+    const int64_t W = img.W, IN = img.IN, KH = img.KH;
+    const int64_t total = W * IN + W + KH * (W * W + W) + W + 1;
+    if (count) *count = total;
+    if (in_dim) *in_dim = img.IN;
+    if (width) *width = img.W;
+    if (n_hidden) *n_hidden = img.KH;
+    if (!theta) return SDF_OK;
+    if (capacity < total)
+        return fail(SDF_ERR_ARG, "theta holds %lld floats, the image has %lld parameters",
+                    static_cast<long long>(capacity), static_cast<long long>(total));
+    int64_t o = 0;
+    for (int l = 0; l <= img.KH; ++l) {
+        for (double v : img.Wl[l]) theta[o++] = static_cast<float>(v);
+        for (double v : img.bl[l]) theta[o++] = static_cast<float>(v);
+    }
+    for (double v : img.wout) theta[o++] = static_cast<float>(v);
+    theta[o++] = img.bout;
+    return SDF_OK;
 }
 
 int sdf_measure_sine_rate(int device, double* sines_per_s, void* cuda_stream) {

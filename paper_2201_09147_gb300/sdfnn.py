@@ -26,7 +26,7 @@ EXPORTS = ["sdf_net_load", "sdf_net_load_mem", "sdf_net_info", "sdf_net_set_time
            "sdf_plan_launch", "sdf_plan_info", "sdf_plan_free", "sdf_train_shape_info", "sdf_train_forward",
            "sdf_train_backward", "sdf_fit_loss", "sdf_adam_step", "sdf_selftest_wait_timeout",
            "sdf_measure_sine_rate", "sdf_frame_queue_create", "sdf_frame_queue_submit", "sdf_frame_queue_wait",
-           "sdf_frame_queue_free"]
+           "sdf_frame_queue_free", "sdf_selftest_noalloc_timeout", "sdf_theta_from_image"]
 
 
 class SdfError(RuntimeError):
@@ -91,6 +91,9 @@ def lib():
         L.sdf_adam_step.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int,
                                     vp]
         L.sdf_selftest_wait_timeout.argtypes = [C.c_int, C.c_int64, vp]
+        L.sdf_selftest_noalloc_timeout.argtypes = [C.c_int, C.c_int64, vp]
+        L.sdf_theta_from_image.argtypes = [C.c_char_p, C.c_size_t, vp, C.c_int64, i64p, C.POINTER(C.c_int),
+                                           C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.sdf_measure_sine_rate.argtypes = [C.c_int, C.POINTER(C.c_double), vp]
         L.sdf_sync_status.argtypes = [vp]
         L.sdf_last_error.restype = C.c_char_p
@@ -110,7 +113,15 @@ def _stream(stream) -> int:
 
 
 def _ptr(t: torch.Tensor | None):
-    return None if t is None else C.c_void_p(t.data_ptr())
+    """Device (or host) address of a tensor's data.  The C calls read SoA arrays at plain offsets,
+    so a tensor with other strides (a transposed or sliced view, e.g. one made from a numpy array
+    in Fortran order) is refused rather than read in the wrong order."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError(f"tensor of shape {tuple(t.shape)} and strides {t.stride()} is not contiguous; "
+                         "pass .contiguous()")
+    return C.c_void_p(t.data_ptr())
 
 
 class Net:
@@ -155,7 +166,7 @@ def make_params(nets, delta, max_iters, eps, step_scale=None, box=(-1.0, 1.0), f
     p = TraceParamsC(m, C.cast(hs, C.POINTER(C.c_void_p)), C.cast(d, C.POINTER(C.c_float)),
                      C.cast(it, C.POINTER(C.c_int)), float(eps),
                      None if ss is None else C.cast(ss, C.POINTER(C.c_float)), float(box[0]), float(box[1]),
-                     int(final_mode), float(time), None if ray_time is None else ray_time.data_ptr())
+                     int(final_mode), float(time), None if ray_time is None else _ptr(ray_time).value)
     return p, (hs, d, it, ss, nets, ray_time)
 
 
@@ -245,7 +256,7 @@ class Plan:
         self.normal = torch.empty((3, n), dtype=torch.float32, device=dev) if fine is not None else None
         self.nets, self.fine, self.n_levels = list(nets), fine, len(nets)
         p, keep = make_params(nets, delta, max_iters, eps, step_scale, box, final_mode, time)
-        b = FrameBatchC(orig.data_ptr(), dirs.data_ptr(), None if ray_time is None else ray_time.data_ptr(), n,
+        b = FrameBatchC(_ptr(orig).value, _ptr(dirs).value, None if ray_time is None else _ptr(ray_time).value, n,
                         self.pos.data_ptr(), self.t.data_ptr(), self.hit.data_ptr(),
                         None if self.iters is None else self.iters.data_ptr(),
                         None if self.normal is None else self.normal.data_ptr())
@@ -338,6 +349,11 @@ def selftest_wait_timeout(budget_us: int = 20000, device: int = 0, stream=None):
     _check(lib().sdf_selftest_wait_timeout(device, int(budget_us), C.c_void_p(_stream(stream))))
 
 
+def selftest_noalloc_timeout(budget_us: int = 20000, device: int = 0, stream=None):
+    """Timeout self-test of the allocation-free entry point's status word (raises if not reported)."""
+    _check(lib().sdf_selftest_noalloc_timeout(device, int(budget_us), C.c_void_p(_stream(stream))))
+
+
 def measure_sine_rate(device: int = 0, stream=None) -> float:
     """Sines per second of the kernels' hardware sine on all SMs."""
     r = C.c_double()
@@ -362,18 +378,16 @@ def train_shape_info(in_dim: int, width: int, n_hidden: int, n: int = 0):
 
 
 def theta_from_sdfn(data: bytes):
-    """(shape, theta) of an SDFN image: the folded parameters as a float32 numpy vector."""
+    """(shape, theta) of an SDFN image: the folded parameters as a float32 numpy
+    vector, folded by the library (sdf_theta_from_image, host only)."""
     import numpy as np
-    hdr = np.frombuffer(data[:32], dtype="<u4")
-    in_dim, width, n_hidden, flags = int(hdr[2]), int(hdr[3]), int(hdr[4]), int(hdr[7])
-    omega0, omega = np.frombuffer(data[20:28], dtype="<f4")
-    theta = np.frombuffer(data[32:], dtype="<f4").astype(np.float64)
-    if not flags & 1:
-        n0 = width * in_dim + width
-        theta[:n0] *= omega0
-        per = width * width + width
-        theta[n0:n0 + n_hidden * per] *= omega
-    return (in_dim, width, n_hidden), theta.astype(np.float32)
+    data = bytes(data)
+    count, a, b, c = C.c_int64(), C.c_int(), C.c_int(), C.c_int()
+    _check(lib().sdf_theta_from_image(data, len(data), None, 0, C.byref(count), C.byref(a), C.byref(b), C.byref(c)))
+    theta = np.empty(count.value, np.float32)
+    _check(lib().sdf_theta_from_image(data, len(data), C.c_void_p(theta.ctypes.data), theta.size, None, None, None,
+                                      None))
+    return (a.value, b.value, c.value), theta
 
 
 def sdfn_from_theta(shape, theta) -> bytes:

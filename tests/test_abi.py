@@ -130,3 +130,31 @@ def test_selftest_argument_check_without_a_gpu(lib):
     lib.sdf_selftest_wait_timeout.argtypes = [C.c_int, C.c_int64, C.c_void_p]
     assert lib.sdf_selftest_wait_timeout(0, 0, None) == -1
     assert lib.sdf_selftest_wait_timeout(0, 10 ** 8, None) == -1
+    lib.sdf_selftest_noalloc_timeout.argtypes = [C.c_int, C.c_int64, C.c_void_p]
+    assert lib.sdf_selftest_noalloc_timeout(0, 0, None) == -1
+
+
+def test_theta_from_image_folds_the_frequencies():
+    """sdf_theta_from_image (host only) multiplies omega0 into layer 0 and omega into the hidden
+    layers (Eq. 2 as plain sin(W x + b)) and leaves the output row; a folded image passes through."""
+    import numpy as np
+    from paper_2201_09147_gb300 import sdfnn
+    net = inputs.siren_init(4, 64, 2)
+    b = inputs.net_to_bytes(net)
+    shape, theta = sdfnn.theta_from_sdfn(b)
+    raw = np.frombuffer(b[32:], "<f4").astype(np.float64)
+    w, k = 64, 2
+    n0 = w * 3 + w
+    per = w * w + w
+    expect = raw.copy()
+    expect[:n0] *= 30.0
+    expect[n0:n0 + k * per] *= 30.0
+    assert shape == (3, 64, 2)
+    assert np.array_equal(theta, expect.astype(np.float32))
+    assert np.array_equal(sdfnn.theta_from_sdfn(sdfnn.sdfn_from_theta(shape, theta))[1], theta)
+    with pytest.raises(sdfnn.SdfError) as e:
+        sdfnn.theta_from_sdfn(b[:-4])
+    assert e.value.code == -3
+    small = np.empty(10, np.float32)
+    assert sdfnn.lib().sdf_theta_from_image(b, len(b), C.c_void_p(small.ctypes.data), 10, None, None, None,
+                                            None) == -1

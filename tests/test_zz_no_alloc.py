@@ -41,19 +41,48 @@ def test_noalloc_matches_regular_entry_point(sdf, name, w, h, precision):
         assert torch.equal(it, ref_it)
         assert float((pos - ref_pos).abs().max()) <= tol
         assert float((t - ref_t).abs().max()) <= tol
+        # no bounded wait of these launches expired: the array's status word is clear
+        sdf.sync_status()
     assert int(ref_hit.sum()) > 0
 
 
 def test_noalloc_rejects_more_rays_than_its_scratch_holds(sdf):
+    """One ray more than the static scratch holds is refused before any launch.  The buffers
+    passed are sized for that many rays, so a regression that launched anyway would still stay
+    inside them."""
     wl = workloads.get("normal_map_1080p", 4, 4)
     nets = [sdf.Net(b, sdf.SDF_FP16) for b in wl.level_bytes()]
     p, keep = sdf.make_params(nets, wl.delta, wl.caps, wl.eps, wl.step_scale, (-1.0, 1.0), wl.final_mode, 0.0)
-    small = torch.zeros((3, 4), device="cuda")
-    out = torch.zeros((3, 4), device="cuda")
-    hit = torch.zeros(4, dtype=torch.uint8, device="cuda")
-    rc = sdf.lib().sdf_trace_multiscale_noalloc(C.byref(p), C.c_void_p(small.data_ptr()), C.c_void_p(small.data_ptr()),
-                                                (1 << 21) + 1, C.c_void_p(out.data_ptr()), C.c_void_p(out.data_ptr()),
+    n = (1 << 21) + 1
+    rays = torch.zeros((3, n), device="cuda")
+    rays[2] = 1.0  # unit directions (and origins on the z axis)
+    pos = torch.zeros((3, n), device="cuda")
+    t = torch.zeros(n, device="cuda")
+    hit = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    rc = sdf.lib().sdf_trace_multiscale_noalloc(C.byref(p), C.c_void_p(rays.data_ptr()), C.c_void_p(rays.data_ptr()),
+                                                n, C.c_void_p(pos.data_ptr()), C.c_void_p(t.data_ptr()),
                                                 C.c_void_p(hit.data_ptr()), None, None)
     assert rc == -1
     assert b"at most" in sdf.lib().sdf_last_error()
+    torch.cuda.synchronize()
+    assert int(hit.sum()) == 0 and float(pos.abs().max()) == 0.0  # nothing ran
     del keep
+
+
+def test_noalloc_timeout_is_reported_by_sync_status(sdf):
+    """A bounded wait that expires while latching into the static array's status word (the
+    self-test's wait on a barrier nothing signals, 20 ms) is reported by sdf_sync_status as
+    SDF_ERR_TIMEOUT and cleared; the entry point then traces as before."""
+    for _ in range(2):
+        sdf.selftest_noalloc_timeout(20000)
+    sdf.sync_status()
+    wl = workloads.get("normal_map_1080p", 64, 36)
+    orig, dirs = wl.rays()
+    nets = [sdf.Net(b, sdf.SDF_BF16) for b in wl.level_bytes()]
+    o = torch.from_numpy(orig).cuda()
+    d = torch.from_numpy(dirs).cuda()
+    kw = dict(step_scale=wl.step_scale, final_mode=wl.final_mode)
+    ref = sdf.trace_multiscale(nets, wl.delta, wl.caps, wl.eps, o, d, **kw)
+    got = sdf.trace_multiscale_noalloc(nets, wl.delta, wl.caps, wl.eps, o, d, **kw)
+    sdf.sync_status()
+    assert torch.equal(got[2], ref[2]) and torch.equal(got[0], ref[0])
