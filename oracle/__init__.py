@@ -67,6 +67,7 @@ class _RayResult(C.Structure):
 
 
 _lib = None
+_POOL = None  # threads of eval_batch
 
 
 def lib():
@@ -244,6 +245,124 @@ def first_root(sdf: SDF, o, v, t0, t1, h=1e-4, tol=1e-13):
     t = C.c_double()
     ok = lib().oracle_first_root(C.byref(sdf.s), _dp(o), _dp(v), t0, t1, h, tol, C.byref(t))
     return t.value if ok else None
+
+
+def _parse_sdfn(data: bytes):
+    """(in_dim, width, n_hidden, folded sine-layer weights [(W, b)], w_out, b_out) of an SDFN image,
+    FP64; the frequencies multiplied in as in Eq. 2 written with plain sin(W x + b): layer 0 by
+    omega0, the hidden layers by omega, the linear output row unchanged."""
+    hdr = np.frombuffer(data[4:32], dtype="<u4")
+    in_dim, width, n_hidden, flags = int(hdr[1]), int(hdr[2]), int(hdr[3]), int(hdr[6])
+    omega0, omega = (float(x) for x in np.frombuffer(data[20:28], dtype="<f4"))
+    q = np.frombuffer(data[32:], dtype="<f4").astype(np.float64)
+    layers, o = [], 0
+    for li in range(n_hidden + 1):
+        fan_in = in_dim if li == 0 else width
+        s = 1.0 if flags & 1 else (omega0 if li == 0 else omega)
+        W = q[o:o + width * fan_in].reshape(width, fan_in) * s
+        o += width * fan_in
+        b = q[o:o + width] * s
+        o += width
+        layers.append((W, b))
+    w_out = q[o:o + width]
+    b_out = float(q[o + width])
+    return in_dim, width, n_hidden, layers, w_out, b_out
+
+
+def eval_batch(net_bytes: bytes, pts, threads: int | None = None) -> np.ndarray:
+    """Eq. 2 at many points in FP64 with numpy: rows of `pts` (in_dim, n) are x, y, z (and t for
+    4-D networks); f_0 = sin(W_0 p + b_0), f_i = sin(W_i f_{i-1} + b_i), f = w_out . f_k + b_out.
+    The matrix products are library calls; chunks of points run on `threads` threads.  The
+    per-point loops of oracle_net_eval compute the same values (pinned against them)."""
+    import concurrent.futures as cf
+    global _POOL
+    in_dim, width, n_hidden, layers, w_out, b_out = _parse_sdfn(net_bytes)
+    P = np.ascontiguousarray(np.asarray(pts, np.float64)[:in_dim])
+    n = P.shape[1]
+    out = np.empty(n)
+
+    def run(lo, hi):
+        x = P[:, lo:hi]
+        for W, b in layers:
+            x = np.sin(W @ x + b[:, None])
+        out[lo:hi] = w_out @ x + b_out
+
+    nt = threads or default_threads()
+    chunk = max(256, min(16384, -(-n // nt)))
+    if n <= chunk:
+        run(0, n)
+        return out
+    if _POOL is None or _POOL._max_workers != nt:
+        _POOL = cf.ThreadPoolExecutor(max_workers=nt)
+    list(_POOL.map(lambda lo: run(lo, min(n, lo + chunk)), range(0, n, chunk)))
+    return out
+
+
+def first_roots_batch(net_bytes: bytes, offset: float, orig, dirs, t0, t1, h: float = 1e-3, time=None,
+                      bisections: int = 60):
+    """The plain definition of the first hit, for many rays at once: the first root of f - offset
+    along o + t v for t in [t0, t1], found as oracle_first_root does (march with step h until the
+    sign changes or f - offset == 0, then bisect), all rays in lockstep with eval_batch.
+
+    orig, dirs: (3, n); t0, t1: (n,).  Returns (t_root (nan where no root), the smallest
+    f - offset seen on the march) per ray."""
+    o = np.asarray(orig, np.float64)
+    v = np.asarray(dirs, np.float64)
+    t0 = np.asarray(t0, np.float64)
+    t1 = np.asarray(t1, np.float64)
+    n = o.shape[1]
+
+    def f(idx, t):
+        p = o[:, idx] + t * v[:, idx]
+        if time is not None:
+            p = np.vstack([p, np.full((1, idx.size), float(time))])
+        return eval_batch(net_bytes, p) - offset
+
+    t_root = np.full(n, np.nan)
+    fmin = np.full(n, np.inf)
+    lo = np.full(n, np.nan)
+    hi = np.full(n, np.nan)
+    t = t0.copy()
+    fa = np.full(n, np.nan)
+    idx = np.nonzero(t1 >= t0)[0]
+    fa[idx] = f(idx, t[idx])
+    fmin[idx] = fa[idx]
+    at_root = idx[fa[idx] == 0.0]
+    t_root[at_root] = t[at_root]
+    idx = idx[fa[idx] != 0.0]
+    while idx.size:
+        tb = np.minimum(t[idx] + h, t1[idx])
+        fb = f(idx, tb)
+        fmin[idx] = np.minimum(fmin[idx], fb)
+        zero = fb == 0.0
+        t_root[idx[zero]] = tb[zero]
+        cross = ~zero & ((fa[idx] > 0.0) != (fb > 0.0))
+        lo[idx[cross]] = t[idx[cross]]
+        hi[idx[cross]] = tb[cross]
+        done = zero | cross | (tb >= t1[idx])
+        t[idx] = tb
+        fa[idx] = fb
+        idx = idx[~done]
+    b = np.nonzero(~np.isnan(lo))[0]
+    if b.size:
+        L, H = lo[b].copy(), hi[b].copy()
+        fL = f(b, L)
+        for _ in range(bisections):
+            M = 0.5 * (L + H)
+            same = (f(b, M) > 0.0) == (fL > 0.0)
+            L = np.where(same, M, L)
+            H = np.where(same, H, M)
+        t_root[b] = 0.5 * (L + H)
+    return t_root, fmin
+
+
+def nesting_violations(coarse: np.ndarray, delta_c: float, fine: np.ndarray, delta_f: float):
+    """Eq. 1 on samples: the points in [|f_fine| <= delta_f] that are outside [|f_coarse| <= delta_c].
+    Returns (number of samples in the fine neighbourhood, number of violations, the largest
+    |f_coarse| over the fine neighbourhood)."""
+    inner = np.abs(fine) <= delta_f
+    worst = float(np.abs(coarse[inner]).max()) if inner.any() else 0.0
+    return int(inner.sum()), int(np.sum(np.abs(coarse[inner]) > delta_c)), worst
 
 
 def thresholds_prop1(eps):
