@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -35,6 +36,10 @@ METRIC = "Mrays/s to hit+normal at 1080p (multiscale BF16 vs plain FP32, same GP
 UNIT = "Mrays/s"
 WORKLOAD = "normal_map_1080p"
 ORACLE_ROW_STRIDE = 32  # the CPU-baseline sample: every 32nd image row
+SCHEDULE_ROW_STRIDE = 32  # error of the 512 x 512 schedules against the oracle: every 32nd row
+ANIM_SAMPLE = 256  # error of the animation batch: rays per frame (seeded), all 32 frames
+MESH_SAMPLE = 3000  # error of the mesh normal mapping: vertices (seeded)
+DECISION_MARGIN_BF16 = 5e-4  # value error of the BF16 path: decisions within it of eps are ambiguous
 
 
 def peaks():
@@ -109,6 +114,44 @@ def dist_info():
     return ws, rank, local
 
 
+def rank_view(ws: int, rank: int):
+    """The frame a rank renders in an N-GPU job (`--split frames`, weak scaling): view k = rank of an
+    N-view orbit, camera eye 2.5 (sin a, 0, cos a) with a = 2 pi k / N, looking at the origin, up +y.
+    View 0 is the headline camera (0, 0, 2.5).  Rays are independent (Alg. 1 per ray, Alg. 2 per
+    point), so the ranks exchange nothing but the timing."""
+    a = 2.0 * math.pi * rank / ws
+    return rank, (2.5 * math.sin(a), 0.0, 2.5 * math.cos(a))
+
+
+def row_band(height: int, ws: int, rank: int):
+    """Rows [lo, hi) of one frame that a rank renders (`--split rows`, strong scaling): contiguous
+    bands, the first height % ws ranks one row taller."""
+    base, extra = divmod(height, ws)
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
+def rank_rays(wl, ws: int, rank: int, split: str):
+    """(orig, dir) of this rank's share of the job and a description of the partition."""
+    from paper_2201_09147_gb300 import inputs
+    if split == "rows":
+        lo, hi = row_band(wl.height, ws, rank)
+        return (*inputs.camera_rays(wl.width, wl.height, rows=np.arange(lo, hi)),
+                f"rows: rank r renders rows [r H/N, (r+1) H/N) of the {wl.width}x{wl.height} frame (strong)")
+    _, eye = rank_view(ws, rank)
+    return (*inputs.camera_rays(wl.width, wl.height, eye=eye),
+            f"frames: rank r renders view r of an N-view orbit at {wl.width}x{wl.height} (weak; view 0 = the "
+            "headline camera)")
+
+
+def spawn_ranks(n: int) -> int:
+    """Relaunches this command as n ranks on this node (torch.distributed.run, 127.0.0.1)."""
+    port = 29400 + os.getpid() % 2000
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}", "--master-addr",
+           "127.0.0.1", "--master-port", str(port), str(Path(__file__).resolve()), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
 def job_throughput(local_total_ms: float, units_per_rank: int, steps: int, ws: int, device="cpu"):
     """Whole-job throughput in millions of units per second: the units of all ranks over the
     slowest rank's timed region (max over ranks); returns (value, max_ms)."""
@@ -135,6 +178,95 @@ def oracle_sample(wl, rows, threads=None):
     nrm = fine.normal_map(res["pos"], res["hit"], threads=threads)
     dt = time.perf_counter() - t0
     return res, nrm, dt, orig.shape[1]
+
+
+def _decisions(gh, oh, amb):
+    una = ~amb
+    return {"hit_agreement": float(np.mean(gh == oh)) if gh.size else None,
+            "ambiguous_share": float(np.mean(amb)) if gh.size else None,
+            "hit_agreement_unambiguous": float(np.mean(gh[una] == oh[una])) if una.any() else None}
+
+
+def _q(x, q):
+    return float(np.quantile(x, q)) if x.size else None
+
+
+def _angles(gn, ref):
+    """Angle in degrees between the columns of two (3, n) arrays (atan2 of |a x b| and a . b, which
+    stays accurate near zero where arccos of the dot product does not)."""
+    a, b = np.asarray(gn, np.float64), np.asarray(ref, np.float64)
+    return np.degrees(np.arctan2(np.linalg.norm(np.cross(a.T, b.T), axis=1), np.sum(a * b, axis=0)))
+
+
+def schedule_errors(samples):
+    """Error of every timed schedule against the FP64 oracle on its sample: hit/miss agreement (all
+    rays, and on the rays whose FP64 decision does not flip when eps moves by the BF16 value error),
+    end-point distance on common hits, normal angle at the GPU's own end points."""
+    import dataclasses
+
+    import oracle
+    out = {}
+    for name in ("three_level_512", "silhouette_512"):
+        if name not in samples:
+            continue
+        sm = samples[name]
+        wl, orig, dirs = sm["wl"], *sm["orig"]
+        lb = wl.level_bytes()
+
+        def tr(eps):
+            onets = [oracle.Net(b) for b in lb]
+            tp = oracle.TraceParams([oracle.SDF.of_net(n) for n in onets], wl.delta, wl.caps, wl.step_scale, eps,
+                                    final_mode=wl.final_mode)
+            return tp.trace_batch(orig, dirs)
+
+        o = tr(wl.eps)
+        amb = tr(wl.eps - DECISION_MARGIN_BF16)["hit"] != tr(wl.eps + DECISION_MARGIN_BF16)["hit"]
+        gh, oh = sm["hit"].astype(bool), o["hit"].astype(bool)
+        both = gh & oh
+        dp = np.linalg.norm(sm["pos"][:, both] - o["pos"][:, both], axis=0)
+        ref = oracle.Net(wl.fine_bytes()).normal_map(sm["pos"].astype(np.float64), sm["hit"])
+        ang = _angles(sm["normal"][:, gh], ref[:, gh])
+        out[name] = {"rays": int(gh.size), "sample": f"every {SCHEDULE_ROW_STRIDE}th row", **_decisions(gh, oh, amb),
+                     "hit_point_p999": _q(dp, 0.999), "hit_point_max": float(dp.max()) if dp.size else None,
+                     "normal_deg_p999": _q(ang, 0.999), "normal_deg_max": float(ang.max()) if ang.size else None}
+    if "animation_32" in samples:
+        sm = samples["animation_32"]
+        wa = sm["wl"]
+        gh_all, oh_all, amb_all, dps, angs = [], [], [], [], []
+        onets = [oracle.Net(b) for b in wa.level_bytes()]
+        ofine = oracle.Net(wa.fine_bytes())
+        from paper_2201_09147_gb300 import inputs as _inputs
+        for fr in sm["frames"]:
+            fw, fh = fr["size"]
+            orig, dirs = _inputs.camera_rays(fw, fh)
+            res = {}
+            for key, eps in (("n", wa.eps), ("lo", wa.eps - DECISION_MARGIN_BF16), ("hi", wa.eps + DECISION_MARGIN_BF16)):
+                tp = oracle.TraceParams([oracle.SDF.of_net(n, time=fr["time"]) for n in onets], wa.delta, wa.caps,
+                                        wa.step_scale, eps, final_mode=wa.final_mode)
+                res[key] = tp.trace_batch(orig, dirs, idx=fr["idx"])
+            gh, oh = fr["hit"].astype(bool), res["n"]["hit"].astype(bool)
+            both = gh & oh
+            dps.append(np.linalg.norm(fr["pos"][:, both] - res["n"]["pos"][:, both], axis=0))
+            ref = ofine.normal_map(fr["pos"].astype(np.float64), fr["hit"], time=fr["time"])
+            angs.append(_angles(fr["normal"][:, gh], ref[:, gh]))
+            gh_all.append(gh)
+            oh_all.append(oh)
+            amb_all.append(res["lo"]["hit"] != res["hi"]["hit"])
+        gh, oh, amb = np.concatenate(gh_all), np.concatenate(oh_all), np.concatenate(amb_all)
+        dp, ang = np.concatenate(dps), np.concatenate(angs)
+        out["animation_32"] = {"rays": int(gh.size), "sample": f"{ANIM_SAMPLE} seeded rays of each of the 32 frames",
+                               **_decisions(gh, oh, amb), "hit_point_p999": _q(dp, 0.999),
+                               "hit_point_max": float(dp.max()) if dp.size else None,
+                               "normal_deg_p999": _q(ang, 0.999), "normal_deg_max": float(ang.max()) if ang.size else None}
+    if "mesh_normal_map" in samples:
+        sm = samples["mesh_normal_map"]
+        from paper_2201_09147_gb300 import workloads as _wl
+        ref = oracle.Net(_wl.get("normal_map_1080p").fine_bytes()).normal_map(sm["pts"].astype(np.float64))
+        ang = _angles(sm["normal"], ref)
+        out["mesh_normal_map"] = {"vertices": int(ang.size), "sample": f"{MESH_SAMPLE} seeded vertices",
+                                  "normal_deg_p999": _q(ang, 0.999), "normal_deg_median": _q(ang, 0.5),
+                                  "normal_deg_max": float(ang.max()) if ang.size else None}
+    return out
 
 
 def reference_arm(args):
@@ -175,6 +307,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--split", default="frames", choices=["frames", "rows"],
+                    help="N-GPU partition: each rank its own frame (weak) or a row band of one frame (strong)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--profile", action="store_true",
@@ -184,6 +318,8 @@ def main():
     args = ap.parse_args()
     if args.profile:
         args.no_cpu_baseline = args.no_plain = True
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        return spawn_ranks(args.gpus)
     if args.impl == "reference":
         return reference_arm(args)
 
@@ -198,8 +334,8 @@ def main():
     pk = peaks()
 
     wl = workloads.get(WORKLOAD)
-    n = wl.n_rays
-    orig_h, dirs_h = wl.rays()
+    orig_h, dirs_h, partition = rank_rays(wl, ws, rank, args.split)
+    n = orig_h.shape[1]
     orig = torch.from_numpy(orig_h).cuda()
     dirs = torch.from_numpy(dirs_h).cuda()
     coarse = [sdfnn.Net(b, sdfnn.SDF_BF16, local) for b in wl.level_bytes()]
@@ -253,6 +389,7 @@ def main():
     trace_ms = [a.elapsed_time(b) for a, b, _ in evs]
     nmap_ms = [b.elapsed_time(c) for _, b, c in evs]
     value, total_ms = job_throughput(sum(step_ms), n, args.steps, ws, "cuda")
+    median_value, _ = job_throughput(statistics.median(step_ms) * args.steps, n, args.steps, ws, "cuda")
     n_hit = int(hit.sum().item())
 
     # roofline of the dominant kernel (algorithmic work / event-timed duration)
@@ -344,12 +481,15 @@ def main():
         e2e_value, _ = job_throughput(1e3 * q_dt, n, q_frames, ws, "cuda")
 
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-              "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-              "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-              "config": {"workload": WORKLOAD, "rays_per_frame": n, "resolution": [wl.width, wl.height],
+              "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+              "ms_per_step_median": statistics.median(step_ms), "value_from_median_step": median_value,
+              "higher_is_better": True,
+              "scaling": "strong" if args.split == "rows" else "weak", "vs_baseline": None, "dtype": "bf16",
+              "data": "synthetic",
+              "config": {"workload": WORKLOAD, "rays_per_rank": n, "resolution": [wl.width, wl.height],
                          "coarse": "(64,1) BF16, final_mode 1, delta_0 0.04, cap 40",
                          "fine": "(256,3) BF16 normal mapping", "l2": "flushed between steps (512 MB write)",
-                         "parallelism": f"replicas x{ws}"},
+                         "parallelism": f"{args.split} x{ws}", "partition": partition},
               "clocks": clk, "gpu_launches": 3 * args.steps,
               "e2e": ({"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 3 * 4 * n,
                        "d2h_bytes_per_step": (3 + 3) * 4 * n + n,
@@ -375,6 +515,7 @@ def main():
                                "mean_coarse_iters": total_evals / n},
               "wall_s_timed_region": t_wall}
 
+    samples = {}  # sampled GPU outputs of the comparison legs, checked against the oracle at the end
     if not args.no_plain:
         # plain FP32 single-network (256,3) tracer with its own normals: the comparison path
         plain = workloads.get("plain_256x3_1080p")
@@ -519,6 +660,11 @@ def main():
             ms3 = timed_ms(plan3.launch, 20)
             result["comparisons"][f"{name}_Mrays_s"] = w3.n_rays / (ms3 / 1e3) / 1e6
             result["comparisons"][f"{name}_hits"] = int(plan3.hit.sum().item())
+            rows3 = np.arange(0, w3.height, SCHEDULE_ROW_STRIDE)
+            i3 = (rows3[:, None] * w3.width + np.arange(w3.width)[None, :]).ravel()
+            samples[name] = {"wl": w3, "idx": i3, "pos": plan3.pos.cpu().numpy()[:, i3],
+                             "hit": plan3.hit.cpu().numpy()[i3], "normal": plan3.normal.cpu().numpy()[:, i3],
+                             "orig": w3.rays(rows=rows3)}
             plan3.close()
 
         # neural normal mapping onto the full-size mesh (displaced icosphere, subdivision 7), BF16
@@ -529,6 +675,9 @@ def main():
         result["comparisons"]["mesh_normal_map"] = {"vertices": int(mesh.shape[1]), "ms": ms_mesh,
                                                     "Mvertices_s": mesh.shape[1] / (ms_mesh / 1e3) / 1e6,
                                                     "net": "(256,3) BF16"}
+        from paper_2201_09147_gb300 import inputs as _inputs
+        im = np.sort(np.unique((_inputs.uniform01(77, MESH_SAMPLE) * mesh_h.shape[1]).astype(np.int64)))
+        samples["mesh_normal_map"] = {"pts": mesh_h[:, im], "normal": mesh_out.cpu().numpy()[:, im]}
         del mesh, mesh_out
 
         # 32 animated frames of mixed sizes: one autotuned plan (CUDA graph) against per-frame calls
@@ -544,6 +693,17 @@ def main():
             ms_plan = timed_ms(plan_a.launch, 5)
             tiles, nodes = plan_a.info()
             n_hits_a = int(plan_a.hit.sum().item())
+            # ANIM_SAMPLE rays of every frame (seeded), for the error against the oracle
+            from paper_2201_09147_gb300 import inputs as _inputs
+            a_pos, a_hit, a_nrm = plan_a.pos.cpu().numpy(), plan_a.hit.cpu().numpy(), plan_a.normal.cpu().numpy()
+            a_frames = []
+            for k, (fw, fh, tk) in enumerate(wa.frames):
+                lo_ = int(off[k])
+                fi = np.sort(np.unique((_inputs.uniform01(500 + k, ANIM_SAMPLE) * fw * fh).astype(np.int64)))
+                a_frames.append({"size": (fw, fh), "time": float(tk), "idx": fi, "pos": a_pos[:, lo_ + fi],
+                                 "hit": a_hit[lo_ + fi], "normal": a_nrm[:, lo_ + fi]})
+            samples["animation_32"] = {"wl": wa, "frames": a_frames}
+            del a_pos, a_hit, a_nrm
             plan_a.close()
             frames = []
             for k, (fw, fh, tk) in enumerate(wa.frames):
@@ -623,18 +783,20 @@ def main():
             both = gh & oh
             dp = np.linalg.norm(gp[:, both] - res["pos"][:, both], axis=0)
             ref = fine_oracle.normal_map(gp.astype(np.float64), gh.astype(np.uint8))
-            c = np.clip(np.sum(gn[:, gh] * ref[:, gh], axis=0), -1, 1)
-            ang = np.degrees(np.arccos(c))
+            ang = _angles(gn[:, gh], ref[:, gh])
             return {"rays": int(idx.size), "hits": int(gh.sum()), "hit_agreement": float(np.mean(gh == oh)),
                     "hit_point_p999": float(np.quantile(dp, 0.999)) if dp.size else None,
                     "hit_point_max": float(dp.max()) if dp.size else None,
                     "normal_deg_p999": float(np.quantile(ang, 0.999)) if ang.size else None,
                     "normal_deg_max": float(ang.max()) if ang.size else None}
 
-        result["error_vs_oracle"] = error_of(coarse, fine)
+        if args.split == "frames":  # rank 0 renders the headline frame itself
+            result["error_vs_oracle"] = error_of(coarse, fine)
+            if not args.no_plain:
+                result["error_vs_oracle_fp16"] = error_of(c16, f16)
+                result["error_vs_oracle_fp8_normal_map"] = error_of(coarse, f8)
         if not args.no_plain:
-            result["error_vs_oracle_fp16"] = error_of(c16, f16)
-            result["error_vs_oracle_fp8_normal_map"] = error_of(coarse, f8)
+            result["error_vs_oracle_schedules"] = schedule_errors(samples)
     if rank == 0:
         print(json.dumps(result))
     if ws > 1:

@@ -60,20 +60,51 @@ def q999(x) -> float:
 # Value error of the hidden-layer arithmetic, per precision (about the
 # hit-point error of each path).  Alg. 1 decides hit or miss by comparing a
 # residual with eps; a ray whose FP64 decision changes when eps moves by this
-# margin either way is decided either way by the path's arithmetic, so the
-# hit decision is compared on the other rays (capped schedules end many rays
-# at the threshold).
+# margin either way is decided either way by the path's arithmetic (capped
+# schedules end many rays at the threshold).  Such "ambiguous" rays are
+# checked on their end point instead of their decision (capped_report).
 DECISION_MARGIN = {0: 1e-6, 3: 1e-4, 1: 5e-4}
 
 
-def trace_report(gpu_pos, gpu_hit, orc_pos, orc_hit, ambiguous=None):
+def capped_report(gpu_pos, gpu_hit, orc, orc_lo, orc_hi, end_residual, eps, margin):
+    """Every ray of a capped schedule, checked against FP64.
+
+    orc, orc_lo, orc_hi: oracle traces at eps, eps - margin and eps + margin;
+    a ray is ambiguous when orc_lo and orc_hi decide differently.
+    end_residual: the last level's FP64 residual t = f_m(p) - d_m at the GPU's
+    own end point.  Alg. 1 steps before it tests t > eps, so a ray that ended
+    with t <= eps (a hit), or with t within the margin of eps (an ambiguous
+    ray), ends at most eps + margin from the level set, plus the path's own
+    value error in p: the residual bound is eps + 2 margin.
+
+    Returns the decision agreement on the unambiguous rays, the ambiguous
+    share, and the largest |end residual| over the GPU's hits and over the
+    ambiguous rays (with the bound)."""
+    gh = np.asarray(gpu_hit).astype(bool)
+    oh = np.asarray(orc["hit"]).astype(bool)
+    amb = np.asarray(orc_lo["hit"]).astype(bool) != np.asarray(orc_hi["hit"]).astype(bool)
+    una = ~amb
+    r = np.abs(np.asarray(end_residual, np.float64))
+    both = gh & oh
+    d = np.linalg.norm(np.asarray(gpu_pos, np.float64)[:, both] - np.asarray(orc["pos"], np.float64)[:, both], axis=0)
+    return {"n": int(gh.size), "n_ambiguous": int(amb.sum()), "ambiguous_share": float(amb.mean()) if gh.size else 0.0,
+            "agree_unambiguous": float(np.mean(gh[una] == oh[una])) if una.any() else 1.0,
+            "agree_all": float(np.mean(gh == oh)) if gh.size else 1.0,
+            "ambiguous_gpu_differs": int((gh[amb] != oh[amb]).sum()),
+            "residual_bound": float(eps + 2.0 * margin),
+            "hit_residual_max": float(r[gh].max()) if gh.any() else 0.0,
+            "ambiguous_residual_max": float(r[amb].max()) if amb.any() else 0.0,
+            "n_hit_gpu": int(gh.sum()), "n_both": int(both.sum()), "pos_p999": q999(d),
+            "pos_max": float(d.max()) if d.size else 0.0}
+
+
+def trace_report(gpu_pos, gpu_hit, orc_pos, orc_hit):
     gpu_hit = np.asarray(gpu_hit).astype(bool)
     orc_hit = np.asarray(orc_hit).astype(bool)
-    sel = np.ones(gpu_hit.shape, bool) if ambiguous is None else ~np.asarray(ambiguous, bool)
-    agree = float(np.mean(gpu_hit[sel] == orc_hit[sel])) if sel.any() else 1.0
+    agree = float(np.mean(gpu_hit == orc_hit)) if gpu_hit.size else 1.0
     both = gpu_hit & orc_hit
     d = np.linalg.norm(np.asarray(gpu_pos, np.float64)[:, both] - np.asarray(orc_pos, np.float64)[:, both], axis=0)
-    return {"agree": agree, "n_ambiguous": int((~sel).sum()), "n_hit_gpu": int(gpu_hit.sum()),
+    return {"agree": agree, "n_hit_gpu": int(gpu_hit.sum()),
             "n_hit_oracle": int(orc_hit.sum()),
             "n_both": int(both.sum()), "pos_p999": q999(d), "pos_max": float(d.max()) if d.size else 0.0,
             "both": both}

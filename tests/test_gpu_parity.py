@@ -16,7 +16,8 @@ import oracle
 from paper_2201_09147_gb300 import inputs, workloads
 from parity import (DECISION_MARGIN, FP8_ANGLE_MEDIAN_DEG, FP8_ANGLE_P999_DEG, FP8_MAGNITUDE_REL, FP8_TRACE_AGREEMENT,
                     FP8_TRACE_POS_MEDIAN, FP8_TRACE_POS_P99, HIT_AGREEMENT,
-                    PRECISION_IDS, PRECISIONS, RANDOM_NET_ANGLE_FACTOR, TOL, angle_report, trace_report)
+                    PRECISION_IDS, PRECISIONS, RANDOM_NET_ANGLE_FACTOR, TOL, angle_report, capped_report,
+                    trace_report)
 
 pytestmark = pytest.mark.gpu
 
@@ -271,7 +272,14 @@ def test_normal_map_1080p_sampled(sdf, precision):
 @pytest.mark.parametrize("name", ["nested_3level_512", "three_level_512", "silhouette_512"])
 @pytest.mark.parametrize("precision", [1, 3], ids=["bf16", "fp16"])
 def test_512_workloads_full_size_sampled(sdf, precision, name):
-    """The 512 x 512 workloads at full size as the benchmark runs them; oracle on 2,000 sampled rays."""
+    """The 512 x 512 workloads at full size as the benchmark runs them; oracle on 2,000 sampled rays,
+    every one of them checked.  Capped schedules (Alg. 1 with the iteration counts of Sec. 6) end
+    rays at the eps threshold, where the decision depends on the last bits of the value: a ray whose
+    FP64 decision flips when eps moves by the path's value error is ambiguous.  Asserted: the
+    decision on every unambiguous ray (agreement bound of the precision); for every GPU hit and for
+    every ambiguous ray, that the GPU's own end point lies, in FP64, within eps + 2 margin of the last
+    level's level set (the ray really stopped at the threshold); the end points of the common hits.
+    The ambiguous share is reported, not bounded."""
     wl = workloads.get(name)
     orig, dirs = wl.rays()
     lb = wl.level_bytes()
@@ -282,16 +290,18 @@ def test_512_workloads_full_size_sampled(sdf, precision, name):
     idx = np.sort(np.unique((inputs.uniform01(123, 2000) * wl.n_rays).astype(np.int64)))
     o = oracle_trace(lb, wl, orig, dirs, idx=idx)
     gs = {"pos": g["pos"][:, idx], "hit": g["hit"][idx]}
-    # rays whose FP64 decision moves with eps +- the precision's value error
     m = DECISION_MARGIN[precision]
     lo = oracle_trace(lb, dataclasses.replace(wl, eps=wl.eps - m), orig, dirs, idx=idx)
     hi = oracle_trace(lb, dataclasses.replace(wl, eps=wl.eps + m), orig, dirs, idx=idx)
-    amb = lo["hit"] != hi["hit"]
+    d_last = wl.delta[-1] if wl.final_mode == 1 else 0.0
+    _, v_end = oracle.Net(lb[-1]).grad_batch(gs["pos"].astype(np.float64), with_value=True)
+    rep = capped_report(gs["pos"], gs["hit"], o, lo, hi, v_end - d_last, wl.eps, m)
+    print(name, precision, rep)
     agree_tol, pos_tol, _ = TOL[precision]
-    rep = trace_report(gs["pos"], gs["hit"], o["pos"], o["hit"], ambiguous=amb)
-    print(name, precision, {k: v for k, v in rep.items() if k != "both"})
-    assert rep["agree"] >= agree_tol and rep["pos_p999"] <= pos_tol
-    assert rep["n_ambiguous"] <= 0.06 * idx.size  # BF16 on the 5-step cap: ~4 %
+    assert rep["agree_unambiguous"] >= agree_tol
+    assert rep["hit_residual_max"] <= rep["residual_bound"]
+    assert rep["ambiguous_residual_max"] <= rep["residual_bound"]
+    assert rep["pos_p999"] <= pos_tol
     assert rep["n_both"] > 150
     ref = oracle.Net(wl.fine_bytes()).normal_map(gs["pos"].astype(np.float64), gs["hit"])
     ar = angle_report(nrm.cpu().numpy()[:, idx], ref, gs["hit"].astype(bool))
