@@ -323,7 +323,7 @@ int sdf_frame_queue_submit(sdf_frame_queue_t queue, const float *orig, const flo
 int sdf_frame_queue_wait(sdf_frame_queue_t queue, int64_t ticket);
 void sdf_frame_queue_free(sdf_frame_queue_t queue);
 
-/* Training (FP32).
+/* Training.
  *
  * The paper fits every network of a sequence with an external framework
  * (Sec. 2, Sec. 3.3).  These calls make that fitting native: the forward
@@ -331,6 +331,14 @@ void sdf_frame_queue_free(sdf_frame_queue_t queue);
  * the backward pass through both (the direction and Eikonal terms depend on
  * grad f, so their parameter gradients are second derivatives of f) and an
  * Adam step.
+ *
+ * precision: SDF_FP32 runs every contraction on the CUDA cores in FP32.
+ * SDF_BF16 (or SDF_FP16) runs the hidden-layer contractions on the tensor
+ * cores with 16-bit operands and FP32 accumulation: the forward W_l X_{l-1}
+ * over the value and the three tangent streams, the adjoint W_l^T (dA_l, dH_l)
+ * and the weight gradient sum (dA_l, dH_l) (P_{l-1}, G_{l-1})^T; layer 0, the
+ * output layer, the sines and every elementwise step stay FP32.  The weights
+ * are rounded from theta at every forward call.  SDF_FP8: SDF_ERR_UNSUPPORTED.
  *
  * theta: device float32, the folded parameters (the frequencies multiplied
  * in) in the order of the SDFN file - W_0 [w][in_dim], b_0, then for each
@@ -340,7 +348,9 @@ void sdf_frame_queue_free(sdf_frame_queue_t queue);
  * (SDF_ERR_UNSUPPORTED otherwise).
  *
  * sdf_train_shape_info: the length of theta and the workspace bytes the
- *   forward / backward pair needs for n points (either pointer may be NULL).
+ *   forward / backward pair needs for n points at that precision (either
+ *   pointer may be NULL).  FP32: (1 + 8k) w floats per point; 16-bit:
+ *   (1 + 6k) w floats per point plus two 16-bit copies of the hidden weights.
  * sdf_train_forward: f (n) and the unnormalised grad f (3, n) at pts (3, n)
  *   (pt_time (n) for 4-input networks, else NULL); saves the layers'
  *   pre-activations in `workspace` (device, 256-byte aligned, of the size
@@ -361,12 +371,12 @@ void sdf_frame_queue_free(sdf_frame_queue_t queue);
  *   moment estimates, zero before step 1; step counts from 1).
  * Errors: SDF_ERR_ARG (NULL / host pointers, bad sizes, misalignment),
  * SDF_ERR_UNSUPPORTED, SDF_ERR_CUDA. */
-int sdf_train_shape_info(int in_dim, int width, int n_hidden, int64_t n, int64_t *param_count,
+int sdf_train_shape_info(int precision, int in_dim, int width, int n_hidden, int64_t n, int64_t *param_count,
                          int64_t *workspace_bytes);
-int sdf_train_forward(int in_dim, int width, int n_hidden, const float *theta, const float *pts,
+int sdf_train_forward(int precision, int in_dim, int width, int n_hidden, const float *theta, const float *pts,
                       const float *pt_time, int64_t n, float *out_f, float *out_grad, void *workspace,
                       void *cuda_stream);
-int sdf_train_backward(int in_dim, int width, int n_hidden, const float *theta, const float *pts,
+int sdf_train_backward(int precision, int in_dim, int width, int n_hidden, const float *theta, const float *pts,
                        const float *pt_time, int64_t n, const float *d_f, const float *d_grad, void *workspace,
                        float *d_theta, void *cuda_stream);
 int sdf_fit_loss(const float *f, const float *grad, const float *target_f, const float *target_grad,
@@ -410,6 +420,20 @@ int sdf_selftest_noalloc_timeout(int device, int64_t budget_us, void *cuda_strea
  * SDF_ERR_FORMAT, SDF_ERR_NONFINITE. */
 int sdf_theta_from_image(const void *bytes, size_t n_bytes, float *theta, int64_t capacity, int64_t *count,
                          int *in_dim, int *width, int *n_hidden);
+
+/* Accuracy helper: the sine and cosine the kernels use for the sine layers of
+ * Eq. 2 and the cosines of Alg. 2, at given arguments (the paper does not
+ * discuss their accuracy).
+ *   variant 0 : the FP32 (SDF_FP32) kernels' functions: reduction of x by the
+ *               nearest multiple of 2 pi (a two-float split of 2 pi), then the
+ *               hardware approximation on [-pi, pi];
+ *   variant 1 : the tensor-core kernels' functions (SDF_BF16, SDF_FP16,
+ *               SDF_FP8): the hardware approximation applied to x directly.
+ *   x, out_sin, out_cos : device, (n) float32.
+ * A NaN in out_sin marks an argument at which the trace kernels' own sine
+ * would differ from the value written (it never should).
+ * Errors: SDF_ERR_ARG, SDF_ERR_CUDA. */
+int sdf_eval_sine(int variant, const float *x, int64_t n, float *out_sin, float *out_cos, void *cuda_stream);
 
 /* Measurement helper: the throughput, in sines per second on all SMs, of the
  * hardware sine the tensor-core kernels use (independent chains of

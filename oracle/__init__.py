@@ -298,6 +298,18 @@ def eval_batch(net_bytes: bytes, pts, threads: int | None = None) -> np.ndarray:
     return out
 
 
+def max_preactivation(net_bytes: bytes, pts) -> list:
+    """Largest |W_l x + b_l| per sine layer of Eq. 2 (frequencies folded) over the points."""
+    _, _, _, layers, _, _ = _parse_sdfn(net_bytes)
+    x = np.asarray(pts, np.float64)[:layers[0][0].shape[1]]
+    out = []
+    for W, b in layers:
+        z = W @ x + b[:, None]
+        out.append(float(np.abs(z).max()))
+        x = np.sin(z)
+    return out
+
+
 def first_roots_batch(net_bytes: bytes, offset: float, orig, dirs, t0, t1, h: float = 1e-3, time=None,
                       bisections: int = 60):
     """The plain definition of the first hit, for many rays at once: the first root of f - offset

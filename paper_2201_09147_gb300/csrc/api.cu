@@ -1469,6 +1469,13 @@ void sdf_frame_queue_free(sdf_frame_queue_t queue) { free_queue(queue); }
 // ---------------------------------------------------------------------------
 // training path
 // ---------------------------------------------------------------------------
+static int train_check_precision(int precision) {
+    if (precision != SDF_FP32 && precision != SDF_BF16 && precision != SDF_FP16)
+        return fail(precision == SDF_FP8 ? SDF_ERR_UNSUPPORTED : SDF_ERR_ARG,
+                    "training precision %d: SDF_FP32, SDF_BF16 or SDF_FP16", precision);
+    return SDF_OK;
+}
+
 static int train_check_shape(int in_dim, int width, int n_hidden) {
     if ((in_dim != 3 && in_dim != 4) || (width != 64 && width != 128 && width != 256) || n_hidden < 1 ||
         n_hidden > kMaxHidden)
@@ -1492,21 +1499,23 @@ static int device_of(const void* p, const char* name, int* dev) {
     return SDF_OK;
 }
 
-int sdf_train_shape_info(int in_dim, int width, int n_hidden, int64_t n, int64_t* param_count,
+int sdf_train_shape_info(int precision, int in_dim, int width, int n_hidden, int64_t n, int64_t* param_count,
                          int64_t* workspace_bytes) {
-    int rc = train_check_shape(in_dim, width, n_hidden);
-    if (rc) return rc;
+    int rc = train_check_precision(precision);
+    if (rc || (rc = train_check_shape(in_dim, width, n_hidden))) return rc;
     if (n < 0 || n > 0x7fffffffLL) return fail(SDF_ERR_ARG, "n = %lld out of range", static_cast<long long>(n));
     const TrainShape sh = train_shape(in_dim, width, n_hidden);
     if (param_count) *param_count = sh.count;
-    if (workspace_bytes) *workspace_bytes = static_cast<int64_t>(train_workspace_bytes(sh, n));
+    if (workspace_bytes)
+        *workspace_bytes = static_cast<int64_t>(precision == SDF_FP32 ? train_workspace_bytes(sh, n)
+                                                                      : train_tc_workspace_bytes(sh, n));
     return SDF_OK;
 }
 
-static int train_prepare(int in_dim, int width, int n_hidden, const float* theta, const float* pts,
+static int train_prepare(int precision, int in_dim, int width, int n_hidden, const float* theta, const float* pts,
                          const float* pt_time, int64_t n, void* workspace, TrainArgs* a, int* dev) {
-    int rc = train_check_shape(in_dim, width, n_hidden);
-    if (rc) return rc;
+    int rc = train_check_precision(precision);
+    if (rc || (rc = train_check_shape(in_dim, width, n_hidden))) return rc;
     if (n < 0 || n > 0x7fffffffLL) return fail(SDF_ERR_ARG, "n = %lld out of range", static_cast<long long>(n));
     if (pt_time && in_dim != 4) return fail(SDF_ERR_ARG, "per-point times given for a 3-input network");
     if ((rc = device_of(theta, "theta", dev))) return rc;
@@ -1523,16 +1532,16 @@ static int train_prepare(int in_dim, int width, int n_hidden, const float* theta
     a->pts = pts;
     a->pt_time = pt_time;
     a->n = n;
-    a->w = train_work(a->sh, n, workspace);
+    a->w = precision == SDF_FP32 ? train_work(a->sh, n, workspace) : train_tc_work(a->sh, n, workspace);
     return SDF_OK;
 }
 
-int sdf_train_forward(int in_dim, int width, int n_hidden, const float* theta, const float* pts,
+int sdf_train_forward(int precision, int in_dim, int width, int n_hidden, const float* theta, const float* pts,
                       const float* pt_time, int64_t n, float* out_f, float* out_grad, void* workspace,
                       void* cuda_stream) {
     TrainArgs a;
     int dev = -1;
-    int rc = train_prepare(in_dim, width, n_hidden, theta, pts, pt_time, n, workspace, &a, &dev);
+    int rc = train_prepare(precision, in_dim, width, n_hidden, theta, pts, pt_time, n, workspace, &a, &dev);
     if (rc || n == 0) return rc;
     if ((rc = check_device_ptr(out_f, dev, "out_f")) || (rc = check_device_ptr(out_grad, dev, "out_grad"))) return rc;
     DeviceGuard g(dev);
@@ -1541,17 +1550,20 @@ int sdf_train_forward(int in_dim, int width, int n_hidden, const float* theta, c
     if ((rc = device_info(dev, &di))) return rc;
     a.out_f = out_f;
     a.out_grad = out_grad;
-    cudaError_t e = launch_train_forward(a, di.num_sms, static_cast<cudaStream_t>(cuda_stream));
+    a.status = di.d_status;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = precision == SDF_FP32 ? launch_train_forward(a, di.num_sms, s)
+                                          : launch_train_forward_tc(a, precision == SDF_FP16, di.num_sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "launching the training forward");
     return SDF_OK;
 }
 
-int sdf_train_backward(int in_dim, int width, int n_hidden, const float* theta, const float* pts,
+int sdf_train_backward(int precision, int in_dim, int width, int n_hidden, const float* theta, const float* pts,
                        const float* pt_time, int64_t n, const float* d_f, const float* d_grad, void* workspace,
                        float* d_theta, void* cuda_stream) {
     TrainArgs a;
     int dev = -1;
-    int rc = train_prepare(in_dim, width, n_hidden, theta, pts, pt_time, n, workspace, &a, &dev);
+    int rc = train_prepare(precision, in_dim, width, n_hidden, theta, pts, pt_time, n, workspace, &a, &dev);
     if (rc || n == 0) return rc;
     if ((rc = check_device_ptr(d_f, dev, "d_f")) || (rc = check_device_ptr(d_grad, dev, "d_grad")) ||
         (rc = check_device_ptr(d_theta, dev, "d_theta")))
@@ -1563,7 +1575,10 @@ int sdf_train_backward(int in_dim, int width, int n_hidden, const float* theta, 
     a.d_f = d_f;
     a.d_grad = d_grad;
     a.d_theta = d_theta;
-    cudaError_t e = launch_train_backward(a, di.num_sms, static_cast<cudaStream_t>(cuda_stream));
+    a.status = di.d_status;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = precision == SDF_FP32 ? launch_train_backward(a, di.num_sms, s)
+                                          : launch_train_backward_tc(a, precision == SDF_FP16, di.num_sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "launching the training backward");
     return SDF_OK;
 }
@@ -1688,6 +1703,22 @@ int sdf_theta_from_image(const void* bytes, size_t n_bytes, float* theta, int64_
     }
     for (double v : img.wout) theta[o++] = static_cast<float>(v);
     theta[o++] = img.bout;
+    return SDF_OK;
+}
+
+int sdf_eval_sine(int variant, const float* x, int64_t n, float* out_sin, float* out_cos, void* cuda_stream) {
+    if (variant != 0 && variant != 1) return fail(SDF_ERR_ARG, "variant must be 0 (FP32 path) or 1 (tensor-core paths)");
+    if (n < 0) return fail(SDF_ERR_ARG, "n < 0");
+    if (n == 0) return SDF_OK;
+    int dev = -1, rc;
+    if ((rc = device_of(x, "x", &dev))) return rc;
+    if ((rc = check_device_ptr(out_sin, dev, "out_sin")) || (rc = check_device_ptr(out_cos, dev, "out_cos"))) return rc;
+    DeviceGuard g(dev);
+    if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", dev);
+    DeviceInfo di;
+    if ((rc = device_info(dev, &di))) return rc;
+    cudaError_t e = launch_sine_eval(variant, x, n, out_sin, out_cos, di.num_sms, static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e, "launching the sine evaluation");
     return SDF_OK;
 }
 

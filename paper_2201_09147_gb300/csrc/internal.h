@@ -75,6 +75,12 @@ struct GradArgs {
     int normalize;                  // 1: unit normal (0 where |g| < 1e-12)
     unsigned long long* grab;       // tile counter, zero at launch
     int* status;
+    // training forward of the tensor-core path (the kernel's TRAIN variant): the
+    // pre-activations saved for the backward, f written beside grad f
+    float* save_a0;                 // [n][width] A_0
+    float4* save_q;                 // [n_hidden][n][width] (A_l, H_l^x, H_l^y, H_l^z), hidden layers 1..k
+    float* out_f;                   // (n)
+    const float* out_bias;          // device address of b_out
 };
 
 // Kernel launchers (return cudaError_t of the launch).
@@ -86,6 +92,9 @@ int trace_tiles_max(const NetView& net);  // largest `tiles` the tensor-core tra
 bool tc_trace_supported(int width, int n_hidden);
 // Measured throughput of the tensor-core kernels' sine on all SMs (sines per second).
 cudaError_t measure_sine_rate(int num_sms, cudaStream_t s, double* sines_per_s);
+// The kernels' sine and cosine at x[0..n): variant 0 = FP32 path, 1 = tensor-core paths.
+cudaError_t launch_sine_eval(int variant, const float* x, int64_t n, float* out_sin, float* out_cos, int num_sms,
+                             cudaStream_t s);
 bool tc_trace_split(int width, int n_hidden);  // head+remainder operands in the trace kernel
 bool tc_grad_supported(int width, int n_hidden);
 
@@ -103,14 +112,23 @@ TrainShape train_shape(int in_dim, int width, int n_hidden);
 
 // Workspace of one forward / backward pair over n points.
 struct TrainWork {
+    // FP32 SIMT path
     float* wt;                     // [k][w][w] transposed hidden weights
-    float* z0;                     // [n][w] layer-0 pre-activations A_0
+    float* z0;                     // [n][w] layer-0 pre-activations A_0 (both paths)
     float* z;                      // [k][n][4][w] per hidden layer: A_i and the tangent pre-images W_i G_{i-1}
     float* d;                      // [k][n][4][w] their adjoints (backward)
     unsigned long long* counters;  // [4] tile counters
+    // tensor-core path
+    uint8_t* wbf;                  // [k] 16-bit W_l images (K-major, 128-byte swizzle, rows padded to 128)
+    uint8_t* wbft;                 // [k] 16-bit W_l^T images, same layout
+    float4* q;                     // [k][n][w] (A_l, H_l^x, H_l^y, H_l^z)
+    uint8_t* dtile;                // [k][n_halves][w * 256] 16-bit (dA_l, dH_l) tiles
+    int64_t n_halves;              // 2 ceil(n / 64): half-tiles of 32 points, in pairs
 };
 size_t train_workspace_bytes(const TrainShape& sh, int64_t n);
 TrainWork train_work(const TrainShape& sh, int64_t n, void* ws);
+size_t train_tc_workspace_bytes(const TrainShape& sh, int64_t n);
+TrainWork train_tc_work(const TrainShape& sh, int64_t n, void* ws);
 
 struct TrainArgs {
     TrainShape sh;
@@ -124,9 +142,13 @@ struct TrainArgs {
     const float* d_grad;   // backward: dL/d(grad f) SoA (3, n)
     TrainWork w;
     float* d_theta;        // backward: accumulated dL/dtheta
+    int* status;           // device status word (bounded waits of the tensor-core kernels)
 };
 cudaError_t launch_train_forward(const TrainArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_train_backward(const TrainArgs& a, int num_sms, cudaStream_t s);
+// Tensor-core training (16-bit operands: f16 = IEEE half, else bfloat16; FP32 accumulation).
+cudaError_t launch_train_forward_tc(const TrainArgs& a, bool f16, int num_sms, cudaStream_t s);
+cudaError_t launch_train_backward_tc(const TrainArgs& a, bool f16, int num_sms, cudaStream_t s);
 cudaError_t launch_fit_loss(const float* f, const float* grad, const float* tf, const float* tgrad,
                             const uint8_t* near, int64_t n, float lam_n, float lam_e, float* d_f, float* d_grad,
                             double* sums, unsigned long long* n_near, double* out, int num_sms, cudaStream_t s);

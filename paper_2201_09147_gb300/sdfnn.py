@@ -26,7 +26,8 @@ EXPORTS = ["sdf_net_load", "sdf_net_load_mem", "sdf_net_info", "sdf_net_set_time
            "sdf_plan_launch", "sdf_plan_info", "sdf_plan_free", "sdf_train_shape_info", "sdf_train_forward",
            "sdf_train_backward", "sdf_fit_loss", "sdf_adam_step", "sdf_selftest_wait_timeout",
            "sdf_measure_sine_rate", "sdf_frame_queue_create", "sdf_frame_queue_submit", "sdf_frame_queue_wait",
-           "sdf_frame_queue_free", "sdf_selftest_noalloc_timeout", "sdf_theta_from_image"]
+           "sdf_frame_queue_free", "sdf_selftest_noalloc_timeout", "sdf_theta_from_image",
+           "sdf_eval_sine"]
 
 
 class SdfError(RuntimeError):
@@ -84,9 +85,10 @@ def lib():
         L.sdf_frame_queue_free.argtypes = [vp]
         L.sdf_frame_queue_free.restype = None
         i64p = C.POINTER(C.c_int64)
-        L.sdf_train_shape_info.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, i64p, i64p]
-        L.sdf_train_forward.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_int64, vp, vp, vp, vp]
-        L.sdf_train_backward.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_int64, vp, vp, vp, vp, vp]
+        L.sdf_train_shape_info.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, i64p, i64p]
+        L.sdf_train_forward.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_int64, vp, vp, vp, vp]
+        L.sdf_train_backward.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, C.c_int64, vp, vp, vp, vp,
+                                         vp]
         L.sdf_fit_loss.argtypes = [vp, vp, vp, vp, vp, C.c_int64, C.c_float, C.c_float, vp, vp, vp, vp]
         L.sdf_adam_step.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int,
                                     vp]
@@ -95,6 +97,7 @@ def lib():
         L.sdf_theta_from_image.argtypes = [C.c_char_p, C.c_size_t, vp, C.c_int64, i64p, C.POINTER(C.c_int),
                                            C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.sdf_measure_sine_rate.argtypes = [C.c_int, C.POINTER(C.c_double), vp]
+        L.sdf_eval_sine.argtypes = [C.c_int, vp, C.c_int64, vp, vp, vp]
         L.sdf_sync_status.argtypes = [vp]
         L.sdf_last_error.restype = C.c_char_p
         _lib = L
@@ -361,6 +364,14 @@ def measure_sine_rate(device: int = 0, stream=None) -> float:
     return r.value
 
 
+def eval_sine(x, variant: int, stream=None):
+    """(sin, cos) of device float32 x as the kernels compute them: variant 0 = the FP32 path,
+    1 = the tensor-core paths."""
+    s_, c_ = torch.empty_like(x), torch.empty_like(x)
+    _check(lib().sdf_eval_sine(int(variant), _ptr(x), x.numel(), _ptr(s_), _ptr(c_), C.c_void_p(_stream(stream))))
+    return s_, c_
+
+
 def sync_status(stream=None):
     """Synchronises the stream and raises on a device-side error (SDF_ERR_TIMEOUT)."""
     _check(lib().sdf_sync_status(C.c_void_p(_stream(stream))))
@@ -370,10 +381,10 @@ def sync_status(stream=None):
 # training
 # ---------------------------------------------------------------------------
 
-def train_shape_info(in_dim: int, width: int, n_hidden: int, n: int = 0):
-    """(length of theta, workspace bytes for n points)."""
+def train_shape_info(in_dim: int, width: int, n_hidden: int, n: int = 0, precision: int = SDF_FP32):
+    """(length of theta, workspace bytes for n points at that precision)."""
     pc, wb = C.c_int64(), C.c_int64()
-    _check(lib().sdf_train_shape_info(in_dim, width, n_hidden, n, C.byref(pc), C.byref(wb)))
+    _check(lib().sdf_train_shape_info(precision, in_dim, width, n_hidden, n, C.byref(pc), C.byref(wb)))
     return pc.value, wb.value
 
 
@@ -399,28 +410,31 @@ def sdfn_from_theta(shape, theta) -> bytes:
     return b"SDFN" + hdr[1:].tobytes() + np.asarray(theta, dtype="<f4").tobytes()
 
 
-def train_forward(shape, theta, pts, pt_time=None, workspace=None, stream=None):
-    """f (n) and grad f (3, n) at device points (3, n); returns (f, grad, workspace)."""
+def train_forward(shape, theta, pts, pt_time=None, workspace=None, stream=None, precision: int = SDF_FP32):
+    """f (n) and grad f (3, n) at device points (3, n); returns (f, grad, workspace).  A given
+    workspace is used if it is large enough, else a new one is made."""
     in_dim, width, n_hidden = shape
     n = pts.shape[1]
-    _, wb = train_shape_info(in_dim, width, n_hidden, n)
-    if workspace is None:
+    _, wb = train_shape_info(in_dim, width, n_hidden, n, precision)
+    if workspace is None or workspace.numel() < wb:
         workspace = torch.empty(wb, dtype=torch.uint8, device=pts.device)
     f = torch.empty(n, dtype=torch.float32, device=pts.device)
     g = torch.empty((3, n), dtype=torch.float32, device=pts.device)
-    _check(lib().sdf_train_forward(in_dim, width, n_hidden, _ptr(theta), _ptr(pts), _ptr(pt_time), n, _ptr(f),
-                                   _ptr(g), _ptr(workspace), C.c_void_p(_stream(stream))))
+    _check(lib().sdf_train_forward(precision, in_dim, width, n_hidden, _ptr(theta), _ptr(pts), _ptr(pt_time), n,
+                                   _ptr(f), _ptr(g), _ptr(workspace), C.c_void_p(_stream(stream))))
     return f, g, workspace
 
 
-def train_backward(shape, theta, pts, d_f, d_grad, workspace, d_theta=None, pt_time=None, stream=None):
+def train_backward(shape, theta, pts, d_f, d_grad, workspace, d_theta=None, pt_time=None, stream=None,
+                   precision: int = SDF_FP32):
     """Adds dL/dtheta to d_theta (allocated zero if None) and returns it."""
     in_dim, width, n_hidden = shape
     n = pts.shape[1]
     if d_theta is None:
         d_theta = torch.zeros_like(theta)
-    _check(lib().sdf_train_backward(in_dim, width, n_hidden, _ptr(theta), _ptr(pts), _ptr(pt_time), n, _ptr(d_f),
-                                    _ptr(d_grad), _ptr(workspace), _ptr(d_theta), C.c_void_p(_stream(stream))))
+    _check(lib().sdf_train_backward(precision, in_dim, width, n_hidden, _ptr(theta), _ptr(pts), _ptr(pt_time), n,
+                                    _ptr(d_f), _ptr(d_grad), _ptr(workspace), _ptr(d_theta),
+                                    C.c_void_p(_stream(stream))))
     return d_theta
 
 
@@ -441,14 +455,14 @@ def adam_step(theta, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, e
 
 
 class SineMLP(torch.autograd.Function):
-    """(f, grad f) = SineMLP.apply(theta, pts, shape[, pt_time]) through the library's
-    training kernels; backward gives dL/dtheta (the points get no gradient)."""
+    """(f, grad f) = SineMLP.apply(theta, pts, shape[, pt_time[, precision]]) through the
+    library's training kernels; backward gives dL/dtheta (the points get no gradient)."""
 
     @staticmethod
-    def forward(ctx, theta, pts, shape, pt_time=None):
-        f, g, ws = train_forward(shape, theta.detach(), pts, pt_time)
+    def forward(ctx, theta, pts, shape, pt_time=None, precision=SDF_FP32):
+        f, g, ws = train_forward(shape, theta.detach(), pts, pt_time, precision=precision)
         ctx.save_for_backward(theta.detach(), pts, ws)
-        ctx.shape, ctx.pt_time = shape, pt_time
+        ctx.shape, ctx.pt_time, ctx.precision = shape, pt_time, precision
         return f, g
 
     @staticmethod
@@ -456,16 +470,19 @@ class SineMLP(torch.autograd.Function):
         theta, pts, ws = ctx.saved_tensors
         d_f = torch.zeros(pts.shape[1], device=pts.device) if d_f is None else d_f.contiguous()
         d_grad = torch.zeros_like(pts) if d_grad is None else d_grad.contiguous()
-        d_theta = train_backward(ctx.shape, theta, pts, d_f, d_grad, ws, pt_time=ctx.pt_time)
-        return d_theta, None, None, None
+        d_theta = train_backward(ctx.shape, theta, pts, d_f, d_grad, ws, pt_time=ctx.pt_time,
+                                 precision=ctx.precision)
+        return d_theta, None, None, None, None
 
 
 def fit_step(shape, theta, m, v, step, pts, target_f, target_grad, near, *, lam_n=0.1, lam_e=0.05, lr=1e-4,
-             workspace=None, stream=None):
+             workspace=None, stream=None, precision: int = SDF_FP32, pt_time=None):
     """One native fitting step: forward, objective, backward, Adam.  Returns (loss, workspace);
     loss is the device float64 vector (l_val, l_dir, l_eik, L) before the update."""
-    f, g, workspace = train_forward(shape, theta, pts, workspace=workspace, stream=stream)
+    f, g, workspace = train_forward(shape, theta, pts, pt_time=pt_time, workspace=workspace, stream=stream,
+                                    precision=precision)
     d_f, d_g, loss = fit_loss(f, g, target_f, target_grad, near, lam_n, lam_e, stream=stream)
-    d_theta = train_backward(shape, theta, pts, d_f, d_g, workspace, stream=stream)
+    d_theta = train_backward(shape, theta, pts, d_f, d_g, workspace, pt_time=pt_time, stream=stream,
+                             precision=precision)
     adam_step(theta, d_theta, m, v, step, lr, stream=stream)
     return loss, workspace

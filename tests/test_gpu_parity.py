@@ -344,7 +344,47 @@ def test_mesh_normal_map_full_size_sampled(sdf, precision):
     ref = oracle.Net(fine_b).normal_map(pts[:, idx].astype(np.float64))
     ar = angle_report(out[:, idx], ref)
     print(ar)
-    assert ar["angle_p999"] <= TOL[precision][2]
+    # the stated 0.5 deg for both operand types (BF16 measured 0.47 deg p99.9 on 18,836 vertices)
+    assert ar["angle_p999"] <= 0.5
+
+
+_HITS = {}
+
+# BF16 normal mapping, p99.9 angle against FP64 (Sec. 5): the stated 0.5 deg holds for the three
+# fitted width-256 networks; the (128,2) measured 0.52 deg (coarse hits) and 0.54 deg (mesh), so
+# SDF_BF16 is held to 0.6 deg there and does not meet 0.5 deg in general.  FP16 stays below 0.07 deg
+# on all four.
+BF16_NORMAL_BOUND = {"s8_256x1": 0.5, "s8_256x2": 0.5, "s8_256x3": 0.5, "s8_128x2": 0.6}
+
+
+@pytest.mark.parametrize("name", sorted(BF16_NORMAL_BOUND))
+@pytest.mark.parametrize("precision", [1, 3], ids=["bf16", "fp16"])
+def test_normal_bound_per_fitted_network(sdf, precision, name):
+    """Neural normal mapping of every fitted (256,k) network and the (128,2) at two point sets of
+    the benchmark: the coarse (64,1) hits of the 1920 x 1080 frame (every 8th hit) and 20,000 sampled
+    vertices of the full-size mesh, against FP64 normals at the same points."""
+    if "hits" not in _HITS:
+        wl = workloads.get("normal_map_1080p")
+        orig, dirs = wl.rays()
+        g = gpu_trace(sdf, wl.level_bytes(), sdf.SDF_BF16, wl, orig, dirs)
+        hidx = np.nonzero(g["hit"])[0][::8]
+        _HITS["hits"] = np.ascontiguousarray(g["pos"][:, hidx])
+        mesh = _MESH7.get("pts")
+        if mesh is None:
+            mesh, _MESH7["frac"] = workloads.mesh_points(subdivisions=7)
+            _MESH7["pts"] = mesh
+        midx = np.sort(np.unique((inputs.uniform01(77, 20000) * mesh.shape[1]).astype(np.int64)))
+        _HITS["mesh"] = np.ascontiguousarray(mesh[:, midx])
+    b = (workloads.SCENES / f"{name}.sdfn").read_bytes()
+    net = sdf.Net(b, precision)
+    bound = BF16_NORMAL_BOUND[name] if precision == 1 else 0.1
+    for label in ("hits", "mesh"):
+        pts = _HITS[label]
+        out = sdf.normal_map(net, torch.from_numpy(pts).cuda()).cpu().numpy()
+        sdf.sync_status()
+        ar = angle_report(out, oracle.Net(b).normal_map(pts.astype(np.float64)))
+        print(name, precision, label, ar)
+        assert ar["n"] > 15000 and ar["angle_p999"] <= bound
 
 
 @pytest.mark.parametrize("name", ["s8_256x3", "s8_256x2", "s8_128x2", "s8_256x1"])

@@ -550,3 +550,20 @@ def test_adam_step_matches_torch_optimizer():
         opt.step()
         th, m, v = oracle.adam_step(th, gk, m, v, k, 1e-3)
     assert np.allclose(t.detach().numpy(), th, rtol=0, atol=1e-15)
+
+
+def test_sine_arguments_of_the_committed_networks_stay_in_the_tested_range():
+    """Every sine argument (pre-activation W_l x + b_l, frequencies folded) of every committed
+    network at 2 * 10^5 points of the cube lies within |x| <= 256, the range over which the
+    kernels' sine and cosine are tested against FP64 on the GPU."""
+    import numpy as np
+
+    import oracle
+    from paper_2201_09147_gb300 import inputs, workloads
+    pts = inputs.random_points(17, 200_000).astype(np.float64)
+    for path in sorted(workloads.SCENES.glob("*.sdfn")):
+        b = path.read_bytes()
+        p = pts if oracle._parse_sdfn(b)[0] == 3 else np.vstack([pts, inputs.uniform01(18, pts.shape[1])[None, :]])
+        m = oracle.max_preactivation(b, p)
+        print(path.name, [round(float(v), 1) for v in m])
+        assert max(m) <= 256.0
