@@ -229,8 +229,10 @@ def schedule_errors(samples):
         out[name] = {"rays": int(gh.size), "sample": f"every {SCHEDULE_ROW_STRIDE}th row", **_decisions(gh, oh, amb),
                      "hit_point_p999": _q(dp, 0.999), "hit_point_max": float(dp.max()) if dp.size else None,
                      "normal_deg_p999": _q(ang, 0.999), "normal_deg_max": float(ang.max()) if ang.size else None}
-    if "animation_32" in samples:
-        sm = samples["animation_32"]
+    for an in ("animation_32", "animation_32_pair", "animation_32_single"):
+        if an not in samples:
+            continue
+        sm = samples[an]
         wa = sm["wl"]
         gh_all, oh_all, amb_all, dps, angs = [], [], [], [], []
         onets = [oracle.Net(b) for b in wa.level_bytes()]
@@ -254,7 +256,7 @@ def schedule_errors(samples):
             amb_all.append(res["lo"]["hit"] != res["hi"]["hit"])
         gh, oh, amb = np.concatenate(gh_all), np.concatenate(oh_all), np.concatenate(amb_all)
         dp, ang = np.concatenate(dps), np.concatenate(angs)
-        out["animation_32"] = {"rays": int(gh.size), "sample": f"{ANIM_SAMPLE} seeded rays of each of the 32 frames",
+        out[an] = {"rays": int(gh.size), "sample": f"{ANIM_SAMPLE} seeded rays of each of the 32 frames",
                                **_decisions(gh, oh, amb), "hit_point_p999": _q(dp, 0.999),
                                "hit_point_max": float(dp.max()) if dp.size else None,
                                "normal_deg_p999": _q(ang, 0.999), "normal_deg_max": float(ang.max()) if ang.size else None}
@@ -680,9 +682,13 @@ def main():
         samples["mesh_normal_map"] = {"pts": mesh_h[:, im], "normal": mesh_out.cpu().numpy()[:, im]}
         del mesh, mesh_out
 
-        # 32 animated frames of mixed sizes: one autotuned plan (CUDA graph) against per-frame calls
-        wa = workloads.get("animation_32")
-        if all((workloads.SCENES / f).exists() for f in wa.levels + [wa.fine]):
+        # 32 animated frames of mixed sizes (8 x 256^2, 16 x 1280x720, 8 x 1920x1080): one autotuned
+        # plan (CUDA graph) per schedule; the first against per-frame calls
+        from paper_2201_09147_gb300 import inputs as _inputs
+        for an in ("animation_32", "animation_32_pair", "animation_32_single"):
+            wa = workloads.get(an)
+            if not all((workloads.SCENES / f).exists() for f in wa.levels + [wa.fine]):
+                continue
             oa_h, da_h, ta_h, off = workloads.batch_rays(wa.frames)
             oa, da, ta = (torch.from_numpy(x).cuda() for x in (oa_h, da_h, ta_h))
             del oa_h, da_h
@@ -694,7 +700,6 @@ def main():
             tiles, nodes = plan_a.info()
             n_hits_a = int(plan_a.hit.sum().item())
             # ANIM_SAMPLE rays of every frame (seeded), for the error against the oracle
-            from paper_2201_09147_gb300 import inputs as _inputs
             a_pos, a_hit, a_nrm = plan_a.pos.cpu().numpy(), plan_a.hit.cpu().numpy(), plan_a.normal.cpu().numpy()
             a_frames = []
             for k, (fw, fh, tk) in enumerate(wa.frames):
@@ -702,57 +707,79 @@ def main():
                 fi = np.sort(np.unique((_inputs.uniform01(500 + k, ANIM_SAMPLE) * fw * fh).astype(np.int64)))
                 a_frames.append({"size": (fw, fh), "time": float(tk), "idx": fi, "pos": a_pos[:, lo_ + fi],
                                  "hit": a_hit[lo_ + fi], "normal": a_nrm[:, lo_ + fi]})
-            samples["animation_32"] = {"wl": wa, "frames": a_frames}
+            samples[an] = {"wl": wa, "frames": a_frames}
             del a_pos, a_hit, a_nrm
             plan_a.close()
-            frames = []
-            for k, (fw, fh, tk) in enumerate(wa.frames):
-                lo, hi = int(off[k]), int(off[k + 1])
-                frames.append((oa[:, lo:hi].contiguous(), da[:, lo:hi].contiguous(), float(tk)))
+            entry = {"rays": wa.n_rays, "frames": "8 x 256^2, 16 x 1280x720, 8 x 1920x1080, t_k = k/31",
+                     "levels": [f"{x} (delta {d}, cap {c})" for x, d, c in zip(wa.levels, wa.delta, wa.caps)],
+                     "normals": wa.fine, "final_mode": wa.final_mode,
+                     "plan_Mrays_s": wa.n_rays / (ms_plan / 1e3) / 1e6, "plan_ms": ms_plan,
+                     "autotuned_tiles": tiles, "graph_nodes": nodes, "hits": n_hits_a}
+            if an == "animation_32":
+                frames = []
+                for k, (fw, fh, tk) in enumerate(wa.frames):
+                    lo, hi = int(off[k]), int(off[k + 1])
+                    frames.append((oa[:, lo:hi].contiguous(), da[:, lo:hi].contiguous(), float(tk)))
 
-            def per_frame():
-                for fo, fd, tk in frames:
-                    p_, _, h_, _ = sdfnn.trace_multiscale(na, wa.delta, wa.caps, wa.eps, fo, fd,
-                                                          step_scale=wa.step_scale, final_mode=wa.final_mode,
-                                                          time=tk, want_iters=False)
-                    fa.set_time(tk)
-                    sdfnn.normal_map(fa, p_, h_)
+                def per_frame():
+                    for fo, fd, tk in frames:
+                        p_, _, h_, _ = sdfnn.trace_multiscale(na, wa.delta, wa.caps, wa.eps, fo, fd,
+                                                              step_scale=wa.step_scale, final_mode=wa.final_mode,
+                                                              time=tk, want_iters=False)
+                        fa.set_time(tk)
+                        sdfnn.normal_map(fa, p_, h_)
 
-            ms_frames = timed_ms(per_frame, 3)
-            result["comparisons"]["animation_32"] = {
-                "rays": wa.n_rays, "frames": "8 x 256^2, 16 x 1280x720, 8 x 1920x1080, t_k = k/31",
-                "plan_Mrays_s": wa.n_rays / (ms_plan / 1e3) / 1e6, "plan_ms": ms_plan,
-                "per_frame_calls_Mrays_s": wa.n_rays / (ms_frames / 1e3) / 1e6, "per_frame_calls_ms": ms_frames,
-                "autotuned_tiles": tiles, "graph_nodes": nodes, "hits": n_hits_a}
-            del frames, oa, da, ta
-        sdfnn.sync_status()
+                ms_frames = timed_ms(per_frame, 3)
+                entry["per_frame_calls_Mrays_s"] = wa.n_rays / (ms_frames / 1e3) / 1e6
+                entry["per_frame_calls_ms"] = ms_frames
+                del frames
+            result["comparisons"][an] = entry
+            del oa, da, ta
+            sdfnn.sync_status()
 
-        # native fitting step of a (256,3) network on 2^20 points (forward with tangents,
-        # objective, backward, Adam; FP32 SIMT kernels)
-        from paper_2201_09147_gb300 import inputs as _inputs
-        shape, theta_h = sdfnn.theta_from_sdfn(wl.fine_bytes())
-        th = torch.from_numpy(theta_h).cuda()
-        m_ = torch.zeros_like(th)
-        v_ = torch.zeros_like(th)
+        # native fitting steps on 2^20 points (forward with tangents, objective, backward, Adam):
+        # the 3-net nested sequence with BF16 tensor-core contractions (config 5), and the (256,3)
+        # with BF16 and with FP32 CUDA-core contractions
         fp, ftf, ftg, fnear = (torch.from_numpy(x).cuda()
                                for x in _inputs.fit_batch(_inputs.sphere_scene(1), 0, 1 << 20))
-        ws_ = None
-        loss_, ws_ = sdfnn.fit_step(shape, th, m_, v_, 1, fp, ftf, ftg, fnear, lr=1e-5, workspace=ws_)
-        torch.cuda.synchronize()
-        fit_ms = []
-        for k in range(2, 5):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            loss_, ws_ = sdfnn.fit_step(shape, th, m_, v_, k, fp, ftf, ftg, fnear, lr=1e-5, workspace=ws_)
-            b.record(stream)
+
+        def fit_ms_of(name, prec):
+            shape, theta_h = sdfnn.theta_from_sdfn((workloads.SCENES / f"{name}.sdfn").read_bytes())
+            th = torch.from_numpy(theta_h).cuda()
+            m_, v_ = torch.zeros_like(th), torch.zeros_like(th)
+            loss_, ws_ = sdfnn.fit_step(shape, th, m_, v_, 1, fp, ftf, ftg, fnear, lr=1e-5, precision=prec)
             torch.cuda.synchronize()
-            fit_ms.append(a.elapsed_time(b))
+            out = []
+            for k in range(2, 6):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                loss_, ws_ = sdfnn.fit_step(shape, th, m_, v_, k, fp, ftf, ftg, fnear, lr=1e-5, workspace=ws_,
+                                            precision=prec)
+                b.record(stream)
+                torch.cuda.synchronize()
+                out.append(a.elapsed_time(b))
+            sdfnn.sync_status()
+            ws_gb = ws_.numel() / 1e9
+            del ws_
+            torch.cuda.empty_cache()
+            return statistics.median(out), float(loss_[3].item()), ws_gb
+
+        seq = {}
+        for name in ("s8_64x2", "s8_128x2", "s8_256x2"):
+            ms_, obj_, gb_ = fit_ms_of(name, sdfnn.SDF_BF16)
+            seq[name] = {"ms_per_step": ms_, "objective": obj_, "workspace_GB": gb_}
+        bf_ms, bf_obj, bf_gb = fit_ms_of("s8_256x3", sdfnn.SDF_BF16)
+        f32_ms, f32_obj, f32_gb = fit_ms_of("s8_256x3", sdfnn.SDF_FP32)
+        seq_ms = sum(v["ms_per_step"] for v in seq.values())
+        result["comparisons"]["fit_step_nested_sequence_2^20"] = {
+            "nets": seq, "ms_per_step": seq_ms, "points_per_s": (1 << 20) / (seq_ms / 1e3),
+            "kernels": "BF16 tcgen05: forward + tangents, backward-data, weight gradients; FP32 objective and Adam"}
         result["comparisons"]["fit_step_256x3_2^20"] = {
-            "ms_per_step": statistics.median(fit_ms), "points_per_s": (1 << 20) / (statistics.median(fit_ms) / 1e3),
-            "objective": float(loss_[3].item()), "workspace_GB": ws_.numel() / 1e9,
-            "kernels": "FP32 SIMT: forward+tangents, objective, backward, weight-gradient GEMMs, Adam"}
-        del ws_, fp, ftf, ftg, fnear
+            "bf16_tensor_core": {"ms_per_step": bf_ms, "objective": bf_obj, "workspace_GB": bf_gb},
+            "fp32_cuda_core": {"ms_per_step": f32_ms, "objective": f32_obj, "workspace_GB": f32_gb},
+            "speedup": f32_ms / bf_ms}
+        del fp, ftf, ftg, fnear
         sdfnn.sync_status()
 
     if rank == 0 and not args.no_cpu_baseline:

@@ -48,7 +48,12 @@ SEQUENCE_NETS = {
     "s8_256x1": (256, 1, 3000),
     "s8_256x2": (256, 2, 3000),
     "s8_256x3": (256, 3, 3000),
+    "a8_128x2_t": (128, 2, 3000, 4),
 }
+# the nested sequence of the 3-level workload (and the 4-D middle network of the animated pair)
+# is fitted natively, on the GPU, with BF16 tensor-core training: 4000 steps of 2^18 points
+NATIVE_NETS = {"s8_64x2", "s8_128x2", "s8_256x2", "a8_128x2_t"}
+NATIVE_STEPS, NATIVE_BATCH = 4000, 1 << 18
 
 
 class Siren(torch.nn.Module):
@@ -160,29 +165,56 @@ def fit_net(scene, width, n_hidden, steps, seed=0, batch=1 << 14, lr=1e-4, lam_n
     return model.cpu().to_sinenet(template)
 
 
-def fit_net_native(scene, width, n_hidden, steps, seed=0, batch=1 << 14, lr=1e-4, lam_n=0.1, lam_e=0.05,
-                   log_every=500, scene_seed=1):
+def fit_net_native(scene, width, n_hidden, steps, seed=0, batch=1 << 18, lr=1e-4, lam_n=0.1, lam_e=0.05,
+                   log_every=500, scene_seed=1, in_dim=3, precision=None):
     """The same objective and Adam, run natively on the GPU through the library's
     training kernels (sdf_train_forward / sdf_fit_loss / sdf_train_backward /
-    sdf_adam_step) with parameters in folded form; 3-D networks.  A fresh batch
-    of inputs.fit_batch points per step, seeded by (seed, step)."""
+    sdf_adam_step), parameters in folded form; by default with BF16 tensor-core
+    contractions.  The batches (half near the surface with N(0, 0.02) jitter,
+    half uniform; 4-D: a uniform time per point, the near-surface half following
+    the moving spheres) are drawn on the GPU by torch from a generator seeded
+    with `seed`, the targets from the analytic scene."""
     from . import sdfnn
-    template = inputs.siren_init(seed, width, n_hidden)
+    precision = sdfnn.SDF_BF16 if precision is None else precision
+    dev = torch.device("cuda")
+    template = inputs.siren_init(seed, width, n_hidden, in_dim=in_dim)
     shape, theta = sdfnn.theta_from_sdfn(inputs.net_to_bytes(template))
-    th = torch.from_numpy(theta).cuda()
+    th = torch.from_numpy(theta).to(dev)
     m, v = torch.zeros_like(th), torch.zeros_like(th)
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    c_all = torch.as_tensor(scene.centres, dtype=torch.float32, device=dev)
+    r_all = torch.as_tensor(scene.radii, dtype=torch.float32, device=dev)
+    half = batch // 2
+    near = torch.zeros(batch, dtype=torch.uint8, device=dev)
+    near[:half] = 1
     ws = None
     t0 = time.time()
     for it in range(steps):
-        pts, tf, tg, near = (torch.from_numpy(x).cuda() for x in inputs.fit_batch(scene, seed * 1_000_003 + it, batch))
+        k = torch.randint(0, len(scene.radii), (half,), generator=gen, device=dev)
+        u = torch.randn(half, 3, generator=gen, device=dev)
+        u = u / u.norm(dim=1, keepdim=True)
+        jit = 0.02 * torch.randn(half, 3, generator=gen, device=dev)
+        unif = torch.rand(batch - half, 3, generator=gen, device=dev) * 2.0 - 1.0
+        tt, centres = None, None
+        if in_dim == 4:
+            tt = torch.rand(batch, generator=gen, device=dev)
+            centres = animated_centres(scene_seed, tt.cpu()).to(dev)
+            cnear = centres[torch.arange(half, device=dev), k]
+        else:
+            cnear = c_all[k]
+        x = torch.cat([(cnear + r_all[k][:, None] * u + jit).clamp(-1.0, 1.0), unif], dim=0)
+        gv, gg = scene_torch(scene, x, centres)
         # cosine schedule to lr / 20, as the torch fitter
         lr_t = lr * (0.05 + 0.95 * 0.5 * (1.0 + math.cos(math.pi * it / steps)))
-        loss, ws = sdfnn.fit_step(shape, th, m, v, it + 1, pts, tf, tg, near, lam_n=lam_n, lam_e=lam_e, lr=lr_t,
-                                  workspace=ws)  # same batch size every step: the workspace is reused
+        # the parameters are trained folded (W' = omega W): Adam's steps on the sine layers are
+        # scaled by omega so that they match the torch fitter's steps on the SIREN parameters
+        loss, ws = sdfnn.fit_step(shape, th, m, v, it + 1, x.T.contiguous(), gv.contiguous(), gg.T.contiguous(), near,
+                                  lam_n=lam_n, lam_e=lam_e, lr=lr_t, workspace=ws, precision=precision,
+                                  pt_time=tt, sine_lr_scale=template.omega)
         if log_every and (it % log_every == 0 or it == steps - 1):
             lv = loss.cpu().numpy()
-            print(f"  ({width},{n_hidden}) native it {it:5d} loss {lv[3]:.5f} val {lv[0]:.5f} n {lv[1]:.4f} "
-                  f"eik {lv[2]:.4f}  {time.time() - t0:.0f}s", flush=True)
+            print(f"  ({width},{n_hidden}) in{in_dim} native it {it:5d} loss {lv[3]:.5f} val {lv[0]:.5f} "
+                  f"n {lv[1]:.4f} eik {lv[2]:.4f}  {time.time() - t0:.0f}s", flush=True)
     sdfnn.sync_status()
     return inputs.net_from_bytes(sdfnn.sdfn_from_theta(shape, th.cpu().numpy()))
 
@@ -195,7 +227,7 @@ def main():
     ap.add_argument("--device", default="cpu")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--native", action="store_true",
-                    help="fit on the GPU with the library's training kernels (3-D networks)")
+                    help="fit every listed network on the GPU with the library's BF16 training kernels")
     args = ap.parse_args()
     if args.threads:
         torch.set_num_threads(args.threads)
@@ -207,15 +239,18 @@ def main():
     for name in args.nets.split(","):
         w, k, steps, *rest = SEQUENCE_NETS[name]
         in_dim = rest[0] if rest else 3
-        steps = args.steps or steps
+        native = args.native or name in NATIVE_NETS
+        steps = args.steps or (NATIVE_STEPS if native else steps)
         print(f"fitting {name}: ({w},{k}) in_dim {in_dim}, {steps} steps", flush=True)
-        if args.native and in_dim == 3:
-            net = fit_net_native(scene, w, k, steps)
+        if native:
+            net = fit_net_native(scene, w, k, steps, batch=NATIVE_BATCH, in_dim=in_dim)
+            info = {"fitter": "native (library training kernels, BF16 tensor cores)", "batch": NATIVE_BATCH}
         else:
             net = fit_net(scene, w, k, steps, device=args.device, in_dim=in_dim)
+            info = {"fitter": "torch (bootstrap)", "batch": 1 << 14}
         inputs.write_net(out / f"{name}.sdfn", net)
         meta[name] = {"width": w, "n_hidden": k, "in_dim": in_dim, "steps": steps, "seed": 0, "scene_seed": 1,
-                      "fitter": "native" if args.native and in_dim == 3 else "torch"}
+                      **info}
     meta_path.write_text(json.dumps(meta, indent=1, sort_keys=True) + "\n")
 
 

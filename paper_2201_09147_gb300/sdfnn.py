@@ -476,13 +476,21 @@ class SineMLP(torch.autograd.Function):
 
 
 def fit_step(shape, theta, m, v, step, pts, target_f, target_grad, near, *, lam_n=0.1, lam_e=0.05, lr=1e-4,
-             workspace=None, stream=None, precision: int = SDF_FP32, pt_time=None):
+             workspace=None, stream=None, precision: int = SDF_FP32, pt_time=None, sine_lr_scale: float = 1.0):
     """One native fitting step: forward, objective, backward, Adam.  Returns (loss, workspace);
-    loss is the device float64 vector (l_val, l_dir, l_eik, L) before the update."""
+    loss is the device float64 vector (l_val, l_dir, l_eik, L) before the update.
+    sine_lr_scale multiplies the learning rate of the sine layers' (folded) parameters: with the
+    frequency omega it gives the steps Adam takes on the unfolded SIREN parameters."""
     f, g, workspace = train_forward(shape, theta, pts, pt_time=pt_time, workspace=workspace, stream=stream,
                                     precision=precision)
     d_f, d_g, loss = fit_loss(f, g, target_f, target_grad, near, lam_n, lam_e, stream=stream)
     d_theta = train_backward(shape, theta, pts, d_f, d_g, workspace, pt_time=pt_time, stream=stream,
                              precision=precision)
-    adam_step(theta, d_theta, m, v, step, lr, stream=stream)
+    if sine_lr_scale == 1.0:
+        adam_step(theta, d_theta, m, v, step, lr, stream=stream)
+    else:
+        in_dim, width, n_hidden = shape
+        k = width * in_dim + width + n_hidden * (width * width + width)  # the sine layers come first
+        adam_step(theta[:k], d_theta[:k], m[:k], v[:k], step, lr * sine_lr_scale, stream=stream)
+        adam_step(theta[k:], d_theta[k:], m[k:], v[k:], step, lr, stream=stream)
     return loss, workspace

@@ -28,6 +28,12 @@ evaluates a network.  The fitted sequences live in ``scenes/`` (written by
   256 x 256, 16 at 1280 x 720, 8 at 1920 x 1080 (31,858,688 rays), traced as
   one batch with a time per ray through the 4-D (64,1) to its delta shell
   and normal-mapped with the 4-D (256,3) (Sec. 3.2, Sec. 5).
+* ``animation_32_pair`` - the same 32 frames with the paper's animated pair
+  (Sec. 6: coarse (64,1), baseline (128,2)): the 4-D (64,1) to its delta
+  shell, normals of the 4-D (128,2).
+* ``animation_32_single`` - the same 32 frames traced on the 4-D (256,3)
+  itself (its zero set, 40 steps) with its own normals: the single-network
+  reading of the batched animation.
 * ``mesh_normals`` - vertices of a subdivision-7 icosphere moved onto the
   scene's zero set, normal-mapped with the fine (256,3).
 """
@@ -86,6 +92,9 @@ def random_siren_64x1() -> inputs.SineNet:
 # delta of the 4-D (64,1) against the 4-D (256,3): the largest |f_c - f_f| found near the
 # surface (|f_f| < 0.05) over 20,000 points at five times was 0.057
 ANIM_DELTA = 0.06
+# delta of the 4-D (64,1) against the 4-D (128,2) of the animated pair: the same 0.06 (Eq. 1 holds
+# on 10^6 samples at eight times, tests/test_oracle_nesting.py)
+ANIM_PAIR_DELTA = 0.06
 
 
 def animation_frames(counts=((8, 256, 256), (16, 1280, 720), (8, 1920, 1080))):
@@ -126,6 +135,12 @@ def get(name: str, width: int | None = None, height: int | None = None, frames=N
                      "s8_256x3.sdfn")
     elif name == "animation_32":
         w = Workload(name, ["a8_64x1_t.sdfn"], [ANIM_DELTA], [40], 1e-3, [1.0], 1, 0, 0, "a8_256x3_t.sdfn")
+        w.frames = animation_frames() if frames is None else frames
+    elif name == "animation_32_pair":
+        w = Workload(name, ["a8_64x1_t.sdfn"], [ANIM_PAIR_DELTA], [40], 1e-3, [1.0], 1, 0, 0, "a8_128x2_t.sdfn")
+        w.frames = animation_frames() if frames is None else frames
+    elif name == "animation_32_single":
+        w = Workload(name, ["a8_256x3_t.sdfn"], [0.0], [40], 1e-3, [1.0], 0, 0, 0, "a8_256x3_t.sdfn")
         w.frames = animation_frames() if frames is None else frames
     elif name == "plain_256x3_1080p":
         w = Workload(name, ["s8_256x3.sdfn"], [0.0], [40], 1e-3, [1.0], 0, 1920, 1080, "s8_256x3.sdfn")

@@ -52,10 +52,15 @@ def _oracle_frames(wl, orig, dirs, off, pos, hit, idx_per_frame=None):
     return np.concatenate(o_pos, axis=1), np.concatenate(o_hit), np.concatenate(o_nrm, axis=1)
 
 
+ANIM_WORKLOADS = ["animation_32", "animation_32_pair", "animation_32_single"]
+
+
+@pytest.mark.parametrize("name", ANIM_WORKLOADS)
 @pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
-def test_frame_batch_vs_oracle(sdf, precision):
-    """Four frames of different sizes and times traced as one batch (per-ray times)."""
-    wl = workloads.get("animation_32", frames=FRAMES)
+def test_frame_batch_vs_oracle(sdf, precision, name):
+    """Four frames of different sizes and times traced as one batch (per-ray times): the coarse
+    4-D (64,1) with (256,3) or (128,2) normals mapped, and the 4-D (256,3) traced itself."""
+    wl = workloads.get(name, frames=FRAMES)
     orig, dirs, tm, off = workloads.batch_rays(wl.frames)
     nets = [sdf.Net(b, precision) for b in wl.level_bytes()]
     fine = sdf.Net(wl.fine_bytes(), precision)

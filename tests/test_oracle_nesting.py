@@ -92,9 +92,10 @@ def test_eq1_nesting_of_every_workload(samples3, name):
         assert n_bad == 0           # Eq. 1 holds on every sample
 
 
-def test_eq1_nesting_of_the_animated_pair_at_every_time(samples4):
+@pytest.mark.parametrize("name", ["animation_32", "animation_32_pair"])
+def test_eq1_nesting_of_the_animated_pair_at_every_time(samples4, name):
     """Sec. 3.2: the 4-D family f_c(., t) |> f_f(., t) must be nested for each t."""
-    wl = workloads.get("animation_32")
+    wl = workloads.get(name)
     fc = values(wl.levels[0], samples4, 4)
     ff = values(wl.fine, samples4, 4)
     for t in np.unique(samples4[3]):
