@@ -303,6 +303,35 @@ def source_sha(path: Path) -> str:
     return hashlib.sha256(path.read_bytes()).hexdigest()[:16]
 
 
+# the sources the inference kernels compile from: DRAM traffic measured by ncu is valid for these only
+KERNEL_SOURCES = ["tc.cu", "grad_tc.cuh", "tc_common.cuh", "common.cuh", "rays.cuh", "internal.h"]
+
+
+def kernel_sources_sha() -> str:
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        h.update((ROOT / "paper_2201_09147_gb300" / "csrc" / name).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def profile_train(points: int) -> int:
+    """Lean run for ncu: two BF16 tensor-core fitting steps of the (256,3) network on `points` points."""
+    import torch
+    from paper_2201_09147_gb300 import build, inputs, sdfnn, workloads
+    build.build()
+    pts, tf, tg, near = (torch.from_numpy(x).cuda() for x in inputs.fit_batch(inputs.sphere_scene(1), 0, points))
+    shape, theta = sdfnn.theta_from_sdfn((workloads.SCENES / "s8_256x3.sdfn").read_bytes())
+    th = torch.from_numpy(theta).cuda()
+    m, v = torch.zeros_like(th), torch.zeros_like(th)
+    ws = None
+    for k in (1, 2):
+        loss, ws = sdfnn.fit_step(shape, th, m, v, k, pts, tf, tg, near, lr=1e-5, workspace=ws,
+                                  precision=sdfnn.SDF_BF16)
+    sdfnn.sync_status()
+    print(json.dumps({"profile_train": points, "objective": float(loss[3].item())}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -317,7 +346,11 @@ def main():
                     help="lean run for ncu: the timed steps only (no L2 flush buffer, no comparison legs)")
     ap.add_argument("--profile-normals", default="bf16", choices=["bf16", "fp16", "fp8"],
                     help="with --profile: operand type of the normal-mapping network")
+    ap.add_argument("--profile-train", type=int, default=0, metavar="POINTS",
+                    help="lean run for ncu: two BF16 fitting steps of the (256,3) on POINTS points, nothing else")
     args = ap.parse_args()
+    if args.profile_train:
+        return profile_train(args.profile_train)
     if args.profile:
         args.no_cpu_baseline = args.no_plain = True
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
@@ -411,7 +444,7 @@ def main():
     traffic_tbl = {}
     if traffic_path.exists():
         tj = json.loads(traffic_path.read_text())
-        if tj.get("source_sha") == source_sha(ROOT / "paper_2201_09147_gb300" / "csrc" / "tc.cu"):
+        if tj.get("source_sha") == kernel_sources_sha():
             traffic_tbl = tj.get("bytes_per_launch", {})
     # the normal-mapping kernel against the tensor roof (reported for both kernels; the
     # dominant one is `roofline`)
@@ -419,7 +452,7 @@ def main():
     nm_peak = pk["bf16_tflops_sustained"]
     roofline_nm = {"kernel": "grad_tc_kernel<256> (neural normal mapping, (256,3))", "bound": "tensor",
                    "achieved": nm_achieved, "peak": nm_peak, "unit": "TFLOP/s", "frac": nm_achieved / nm_peak,
-                   "traffic": traffic_tbl.get("grad_tc_kernel<256, 0>"),
+                   "traffic": traffic_tbl.get("grad_tc_kernel<256, 0, 0>"),
                    "peak_source": f"{pk['source']} bf16 sustained",
                    "work": f"{n_hit} points x {normal_flops_per_point} hidden-layer MMA flops"}
     if nm_ms >= tr_ms:

@@ -355,7 +355,7 @@ void sdf_frame_queue_free(sdf_frame_queue_t queue);
  *   (pt_time (n) for 4-input networks, else NULL); saves the layers'
  *   pre-activations in `workspace` (device, 256-byte aligned, of the size
  *   above) for the backward.
- * sdf_train_backward: ADDS dL/dtheta to d_theta given d_f = dL/df (n) and
+ * sdf_train_backward: ADDS dL/dtheta to d_theta (16-byte aligned, like theta) given d_f = dL/df (n) and
  *   d_grad = dL/d(grad f) (3, n), from the workspace of the forward call made
  *   with the same theta, points and n (zero d_theta first for a fresh
  *   gradient).  Points are independent: chunks of a batch may be run one

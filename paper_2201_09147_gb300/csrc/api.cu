@@ -1568,6 +1568,7 @@ int sdf_train_backward(int precision, int in_dim, int width, int n_hidden, const
     if ((rc = check_device_ptr(d_f, dev, "d_f")) || (rc = check_device_ptr(d_grad, dev, "d_grad")) ||
         (rc = check_device_ptr(d_theta, dev, "d_theta")))
         return rc;
+    if (reinterpret_cast<uintptr_t>(d_theta) % 16) return fail(SDF_ERR_ARG, "d_theta must be 16-byte aligned");
     DeviceGuard g(dev);
     if (!g.ok) return fail(SDF_ERR_CUDA, "cudaSetDevice(%d) failed", dev);
     DeviceInfo di;

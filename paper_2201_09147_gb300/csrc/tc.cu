@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
     volatile int* abort_flag = reinterpret_cast<volatile int*>(base + L.misc + 8);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int tile = tid >> 7, ttid = tid & 127, twarp = ttid >> 5;
+    const int issuer = 32 * (tile & 3);  // lane 0 of the tile's warp (tile mod 4)
     constexpr uint32_t xbytes = 128u * W * 2u;
     const uint32_t bar_mma = base_s + L.bars + 8u * (1 + tile);
     const uint32_t x_s = base_s + L.x + tile * xbytes, xlo_s = base_s + L.xlo + tile * xbytes;
@@ -386,7 +387,10 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
             float f = 0.0f;
             bool good = true;
             for (int l = 0; l < KH; ++l) {
-                if (ttid == 0) {
+                // the tile's MMAs are issued from its warp (tile mod 4), so that the issue work of
+                // the CTA's tiles is spread over the four schedulers of the SM (warp w of every
+                // tile runs on scheduler w)
+                if (ttid == issuer) {
                     tc_fence_after();
                     const uint64_t xd0 = desc_kmajor_sw128(x_s), xld0 = desc_kmajor_sw128(xlo_s);
                     const uint64_t wd0 = desc_kmajor_sw128(w_s + l * W * W * 2u);

@@ -615,10 +615,14 @@ __global__ void __launch_bounds__(WgCfg<W>::THREADS) train_wgrad_tc_kernel(const
                     float v[32];
                     tmem_ld32(tmem + (static_cast<uint32_t>(quad * 32) << 16) + mt * W + cc * 32u, v);
                     tmem_wait_ld();
-                    if (nrow < W)
+                    if (nrow < W) {
+                        // 16-byte vector reductions: a quarter of the atomic operations of scalar ones
+                        float4* row = reinterpret_cast<float4*>(gw + static_cast<size_t>(nrow) * W + cc * 32);
 #pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            atomicAdd(gw + static_cast<size_t>(nrow) * W + cc * 32 + i, v[i] * invS);
+                        for (int i = 0; i < 8; ++i)
+                            atomicAdd(row + i, make_float4(v[4 * i] * invS, v[4 * i + 1] * invS, v[4 * i + 2] * invS,
+                                                           v[4 * i + 3] * invS));
+                    }
                 }
                 tc_fence_before();
                 mbar_arrive(bar_flushed);
