@@ -119,3 +119,16 @@ def angle_report(gpu_vec, orc_vec, mask=None):
     return {"n": int(ang.size), "angle_p999": q999(ang), "angle_max": float(ang.max()) if ang.size else 0.0,
             "angle_mean": float(ang.mean()) if ang.size else 0.0,
             "angle_median": float(np.median(ang)) if ang.size else 0.0}
+
+
+# BF16 normals against FP16 normals of the same network at the same points.  The error of a 16-bit
+# path scales with its operand type's unit roundoff, 8x larger for bfloat16 (2^-9) than for half
+# (2^-12); 1.5 more covers the shape of the error distribution at p99.9.  The FP16 path itself is
+# held to the stated bounds, so this ties every BF16 normal to what its arithmetic allows on that
+# network (the flat BF16 bound above stays as a backstop).  The floor covers angles near FP32 level.
+BF16_OVER_FP16 = 12.0
+ANGLE_FLOOR_DEG = 0.02
+
+
+def bf16_within_fp16(bf16_p999: float, fp16_p999: float) -> bool:
+    return bf16_p999 <= BF16_OVER_FP16 * fp16_p999 + ANGLE_FLOOR_DEG

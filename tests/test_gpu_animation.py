@@ -10,7 +10,7 @@ import torch
 
 import oracle
 from paper_2201_09147_gb300 import inputs, workloads
-from parity import PRECISION_IDS, PRECISIONS, TOL, angle_report, trace_report
+from parity import PRECISION_IDS, PRECISIONS, TOL, angle_report, bf16_within_fp16, trace_report
 
 pytestmark = pytest.mark.gpu
 
@@ -77,6 +77,15 @@ def test_frame_batch_vs_oracle(sdf, precision, name):
     print(ar)
     assert ar["angle_p999"] <= ang_tol
     assert np.all(nrm[:, hit == 0] == 0.0)
+    if precision == sdf.SDF_BF16:
+        # FP16 normals of the same fine network at the same points: BF16 within what its unit
+        # roundoff allows (tests/parity.py)
+        f16 = sdf.Net(wl.fine_bytes(), sdf.SDF_FP16)
+        twin = sdf.normal_map_timed(f16, _dev(pos), _dev(tm), _dev(hit))
+        sdf.sync_status()
+        ar16 = angle_report(_np(twin), o_nrm, hit.astype(bool))
+        print("bf16 / fp16", ar["angle_p999"], ar16["angle_p999"])
+        assert bf16_within_fp16(ar["angle_p999"], ar16["angle_p999"])
 
 
 def _random_4d(width, n_hidden):

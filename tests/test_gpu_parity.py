@@ -16,8 +16,8 @@ import oracle
 from paper_2201_09147_gb300 import inputs, workloads
 from parity import (DECISION_MARGIN, FP8_ANGLE_MEDIAN_DEG, FP8_ANGLE_P999_DEG, FP8_MAGNITUDE_REL, FP8_TRACE_AGREEMENT,
                     FP8_TRACE_POS_MEDIAN, FP8_TRACE_POS_P99, HIT_AGREEMENT,
-                    PRECISION_IDS, PRECISIONS, RANDOM_NET_ANGLE_FACTOR, TOL, angle_report, capped_report,
-                    trace_report)
+                    PRECISION_IDS, PRECISIONS, RANDOM_NET_ANGLE_FACTOR, TOL, angle_report, bf16_within_fp16,
+                    capped_report, trace_report)
 
 pytestmark = pytest.mark.gpu
 
@@ -40,6 +40,20 @@ def oracle_trace(level_bytes, wl, orig, dirs, idx=None):
     tp = oracle.TraceParams([oracle.SDF.of_net(n) for n in onets], wl.delta, wl.caps, scales, wl.eps,
                             final_mode=wl.final_mode)
     return tp.trace_batch(orig, dirs, idx=idx)
+
+
+def fp16_twin(sdf, net_bytes, pts_dev, mask_dev=None, time_dev=None):
+    """Unit normals of the same network with FP16 operands at the same device points (host array)."""
+    net = sdf.Net(net_bytes, sdf.SDF_FP16)
+    out = (sdf.normal_map(net, pts_dev, mask_dev) if time_dev is None
+           else sdf.normal_map_timed(net, pts_dev, time_dev, mask_dev))
+    sdf.sync_status()
+    return out.cpu().numpy()
+
+
+def assert_bf16_ratio(ar_bf16, ar_fp16, label=""):
+    print(label, "normal p99.9 bf16", ar_bf16["angle_p999"], "fp16", ar_fp16["angle_p999"])
+    assert bf16_within_fp16(ar_bf16["angle_p999"], ar_fp16["angle_p999"])
 
 
 def check_trace(g, o, precision, label):
@@ -117,8 +131,11 @@ def test_normals_vs_oracle(sdf, precision, name, make):
     assert np.quantile(rel[ok], 0.999) <= np.radians(tol) * 4 + 1e-4
     # normal map = unit gradient
     unit = ref / np.linalg.norm(ref, axis=0, keepdims=True)
-    assert angle_report(nm, unit, ok)["angle_p999"] <= tol
+    ar_nm = angle_report(nm, unit, ok)
+    assert ar_nm["angle_p999"] <= tol
     assert np.allclose(np.linalg.norm(nm, axis=0)[ok], 1.0, atol=1e-5)
+    if precision == sdf.SDF_BF16:
+        assert_bf16_ratio(ar_nm, angle_report(fp16_twin(sdf, b, torch.from_numpy(pts).cuda()), unit, ok), name)
 
 
 @pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
@@ -135,7 +152,11 @@ def test_normal_map_mask(sdf, precision):
     m = mask.astype(bool)
     assert np.all(out[:, ~m] == 0.0)
     ref = oracle.Net(b).normal_map(pts, mask)
-    assert angle_report(out, ref, m)["angle_p999"] <= TOL[precision][2]
+    ar = angle_report(out, ref, m)
+    assert ar["angle_p999"] <= TOL[precision][2]
+    if precision == sdf.SDF_BF16:
+        twin = fp16_twin(sdf, b, torch.from_numpy(pts).cuda(), torch.from_numpy(mask).cuda())
+        assert_bf16_ratio(ar, angle_report(twin, ref, m), "mask")
 
 
 # ---------------------------------------------------------------------------
@@ -164,7 +185,10 @@ def test_trace_random_siren(sdf, precision):
     sdf.sync_status()
     ref = oracle.Net(lb[0]).normal_map(g["pos"].astype(np.float64), g["hit"])
     tol = TOL[precision][2] * (RANDOM_NET_ANGLE_FACTOR if precision else 1.0)
-    assert angle_report(nrm.cpu().numpy(), ref, hit)["angle_p999"] <= tol
+    ar = angle_report(nrm.cpu().numpy(), ref, hit)
+    assert ar["angle_p999"] <= tol
+    if precision == sdf.SDF_BF16:
+        assert_bf16_ratio(ar, angle_report(fp16_twin(sdf, lb[0], g["pos_dev"], g["hit_dev"]), ref, hit), "siren")
 
 
 @pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
@@ -187,6 +211,9 @@ def test_normal_map_workload_small(sdf, precision):
     ar = angle_report(nrm, ref, hit)
     print(ar)
     assert ar["angle_p999"] <= TOL[precision][2]
+    if precision == sdf.SDF_BF16:
+        twin = fp16_twin(sdf, wl.fine_bytes(), g["pos_dev"], g["hit_dev"])
+        assert_bf16_ratio(ar, angle_report(twin, ref, hit), "normal_map_small")
 
 
 @pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
@@ -206,6 +233,9 @@ def test_nested_3level_small(sdf, precision):
     ar = angle_report(nrm.cpu().numpy(), ref, g["hit"].astype(bool))
     print(ar)
     assert ar["angle_p999"] <= TOL[precision][2]
+    if precision == sdf.SDF_BF16:
+        twin = fp16_twin(sdf, wl.fine_bytes(), g["pos_dev"], g["hit_dev"])
+        assert_bf16_ratio(ar, angle_report(twin, ref, g["hit"].astype(bool)), wl.name)
 
 
 @pytest.mark.parametrize("name", ["three_level_512", "silhouette_512"])
@@ -229,6 +259,9 @@ def test_three_level_normal_map_small(sdf, precision, name):
     ar = angle_report(nrm.cpu().numpy(), ref, g["hit"].astype(bool))
     print(ar)
     assert ar["angle_p999"] <= TOL[precision][2]
+    if precision == sdf.SDF_BF16:
+        twin = fp16_twin(sdf, wl.fine_bytes(), g["pos_dev"], g["hit_dev"])
+        assert_bf16_ratio(ar, angle_report(twin, ref, g["hit"].astype(bool)), wl.name)
 
 
 @pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
@@ -263,6 +296,9 @@ def test_normal_map_1080p_sampled(sdf, precision):
     ar = angle_report(nrm.cpu().numpy()[:, idx], ref, hit)
     print(ar)
     assert ar["angle_p999"] <= TOL[precision][2]
+    if precision == sdf.SDF_BF16:
+        twin = fp16_twin(sdf, wl.fine_bytes(), g["pos_dev"], g["hit_dev"])[:, idx]
+        assert_bf16_ratio(ar, angle_report(twin, ref, hit), "1080p sampled")
     # every ray of the frame got a decision and misses carry zero normals
     allhit = g["hit"].astype(bool)
     assert set(np.unique(g["hit"])) <= {0, 1}
@@ -307,6 +343,9 @@ def test_512_workloads_full_size_sampled(sdf, precision, name):
     ar = angle_report(nrm.cpu().numpy()[:, idx], ref, gs["hit"].astype(bool))
     print(ar)
     assert ar["angle_p999"] <= TOL[precision][2]
+    if precision == sdf.SDF_BF16:
+        twin = fp16_twin(sdf, wl.fine_bytes(), g["pos_dev"], g["hit_dev"])[:, idx]
+        assert_bf16_ratio(ar, angle_report(twin, ref, gs["hit"].astype(bool)), name)
 
 
 @pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
@@ -322,6 +361,8 @@ def test_mesh_normal_map(sdf, precision):
     ar = angle_report(out.cpu().numpy(), ref)
     print(ar)
     assert ar["angle_p999"] <= TOL[precision][2]
+    if precision == sdf.SDF_BF16:
+        assert_bf16_ratio(ar, angle_report(fp16_twin(sdf, fine_b, torch.from_numpy(pts).cuda()), ref), "mesh5")
 
 
 _MESH7 = {}
