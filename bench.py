@@ -37,6 +37,7 @@ UNIT = "Mrays/s"
 WORKLOAD = "normal_map_1080p"
 ORACLE_ROW_STRIDE = 32  # the CPU-baseline sample: every 32nd image row
 SCHEDULE_ROW_STRIDE = 32  # error of the 512 x 512 schedules against the oracle: every 32nd row
+VARIANT_ROW_STRIDE = 64  # error of config 3's other readings (1080p) against the oracle: every 64th row
 ANIM_SAMPLE = 256  # error of the animation batch: rays per frame (seeded), all 32 frames
 MESH_SAMPLE = 3000  # error of the mesh normal mapping: vertices (seeded)
 DECISION_MARGIN_BF16 = 5e-4  # value error of the BF16 path: decisions within it of eps are ambiguous
@@ -206,7 +207,7 @@ def schedule_errors(samples):
 
     import oracle
     out = {}
-    for name in ("three_level_512", "silhouette_512"):
+    for name in ("three_level_512", "silhouette_512", "normal_map_1080p_c64x2", "normal_map_1080p_zero"):
         if name not in samples:
             continue
         sm = samples[name]
@@ -226,7 +227,8 @@ def schedule_errors(samples):
         dp = np.linalg.norm(sm["pos"][:, both] - o["pos"][:, both], axis=0)
         ref = oracle.Net(wl.fine_bytes()).normal_map(sm["pos"].astype(np.float64), sm["hit"])
         ang = _angles(sm["normal"][:, gh], ref[:, gh])
-        out[name] = {"rays": int(gh.size), "sample": f"every {SCHEDULE_ROW_STRIDE}th row", **_decisions(gh, oh, amb),
+        out[name] = {"rays": int(gh.size), "sample": sm.get("sample", f"every {SCHEDULE_ROW_STRIDE}th row"),
+                     **_decisions(gh, oh, amb),
                      "hit_point_p999": _q(dp, 0.999), "hit_point_max": float(dp.max()) if dp.size else None,
                      "normal_deg_p999": _q(ang, 0.999), "normal_deg_max": float(ang.max()) if ang.size else None}
     for an in ("animation_32", "animation_32_pair", "animation_32_single"):
@@ -702,6 +704,31 @@ def main():
                              "orig": w3.rays(rows=rows3)}
             plan3.close()
 
+        # config 3's other readings of "coarse 64-wide net" and of the end condition: the (64,2) of the
+        # nested sequence as the coarse net, and the (64,1) traced to its zero set; (256,3) normals, BF16
+        for name in ("normal_map_1080p_c64x2", "normal_map_1080p_zero"):
+            wv = workloads.get(name)
+            cv = [sdfnn.Net(b, sdfnn.SDF_BF16, local) for b in wv.level_bytes()]
+
+            def vstep(wv=wv, cv=cv):
+                sdfnn.trace_multiscale(cv, wv.delta, wv.caps, wv.eps, orig, dirs, step_scale=wv.step_scale,
+                                       final_mode=wv.final_mode, out_pos=pos, out_t=tt, out_hit=hit,
+                                       want_iters=False)
+                sdfnn.normal_map(fine, pos, hit, out=nrm)
+
+            msv = timed_ms(vstep, 10)
+            vstep()
+            sdfnn.sync_status()
+            result["comparisons"][f"{name}_Mrays_s"] = n / (msv / 1e3) / 1e6
+            result["comparisons"][f"{name}_hits"] = int(hit.sum().item())
+            if args.split == "frames":
+                rows_v = np.arange(0, wl.height, VARIANT_ROW_STRIDE)
+                iv = (rows_v[:, None] * wl.width + np.arange(wl.width)[None, :]).ravel()
+                samples[name] = {"wl": wv, "idx": iv, "pos": pos.cpu().numpy()[:, iv], "hit": hit.cpu().numpy()[iv],
+                                 "normal": nrm.cpu().numpy()[:, iv],
+                                 "orig": (np.ascontiguousarray(orig_h[:, iv]), np.ascontiguousarray(dirs_h[:, iv])),
+                                 "sample": f"every {VARIANT_ROW_STRIDE}th row of the 1080p frame"}
+
         # neural normal mapping onto the full-size mesh (displaced icosphere, subdivision 7), BF16
         mesh_h, _ = workloads.mesh_points(7)
         mesh = torch.from_numpy(mesh_h).cuda()
@@ -831,7 +858,7 @@ def main():
         idx = (rows[:, None] * wl.width + np.arange(wl.width)[None, :]).ravel()
         fine_oracle = oracle.Net(wl.fine_bytes())
 
-        def error_of(cnets, fnet):
+        def error_of(cnets, fnet, qfmt=None):
             sdfnn.trace_multiscale(cnets, wl.delta, wl.caps, wl.eps, orig, dirs, step_scale=wl.step_scale,
                                    final_mode=wl.final_mode, out_pos=pos, out_t=tt, out_hit=hit, want_iters=False)
             sdfnn.normal_map(fnet, pos, hit, out=nrm)
@@ -844,16 +871,29 @@ def main():
             dp = np.linalg.norm(gp[:, both] - res["pos"][:, both], axis=0)
             ref = fine_oracle.normal_map(gp.astype(np.float64), gh.astype(np.uint8))
             ang = _angles(gn[:, gh], ref[:, gh])
-            return {"rays": int(idx.size), "hits": int(gh.sum()), "hit_agreement": float(np.mean(gh == oh)),
-                    "hit_point_p999": float(np.quantile(dp, 0.999)) if dp.size else None,
-                    "hit_point_max": float(dp.max()) if dp.size else None,
-                    "normal_deg_p999": float(np.quantile(ang, 0.999)) if ang.size else None,
-                    "normal_deg_max": float(ang.max()) if ang.size else None}
+            out = {"rays": int(idx.size), "hits": int(gh.sum()), "hit_agreement": float(np.mean(gh == oh)),
+                   "hit_point_p999": float(np.quantile(dp, 0.999)) if dp.size else None,
+                   "hit_point_max": float(dp.max()) if dp.size else None,
+                   "normal_deg_p999": float(np.quantile(ang, 0.999)) if ang.size else None,
+                   "normal_deg_max": float(ang.max()) if ang.size else None,
+                   # hits where |grad f| < 1e-12 get (0, 0, 0): counted, and part of the angles above
+                   "zero_normals": int((np.linalg.norm(gn[:, gh], axis=0) == 0.0).sum())}
+            if qfmt:
+                # the oracle on the 16-bit hidden weights the kernel multiplies with: the angle from
+                # the exact FP64 normals is the weight rounding alone, the angle to the GPU's the
+                # arithmetic (16-bit activations and tangents, FP32 accumulation, hardware sine)
+                qref = oracle.Net(oracle.quantised_image(wl.fine_bytes(), qfmt)).normal_map(
+                    gp.astype(np.float64), gh.astype(np.uint8))
+                aq, ag = _angles(qref[:, gh], ref[:, gh]), _angles(gn[:, gh], qref[:, gh])
+                out["split_vs_oracle_on_16bit_weights"] = {
+                    "weights": qfmt, "weight_rounding_deg_p999": _q(aq, 0.999), "weight_rounding_deg_median": _q(aq, 0.5),
+                    "arithmetic_deg_p999": _q(ag, 0.999), "arithmetic_deg_median": _q(ag, 0.5)}
+            return out
 
         if args.split == "frames":  # rank 0 renders the headline frame itself
-            result["error_vs_oracle"] = error_of(coarse, fine)
+            result["error_vs_oracle"] = error_of(coarse, fine, "bf16")
             if not args.no_plain:
-                result["error_vs_oracle_fp16"] = error_of(c16, f16)
+                result["error_vs_oracle_fp16"] = error_of(c16, f16, "f16")
                 result["error_vs_oracle_fp8_normal_map"] = error_of(coarse, f8)
         if not args.no_plain:
             result["error_vs_oracle_schedules"] = schedule_errors(samples)

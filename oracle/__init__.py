@@ -9,6 +9,10 @@ precision: Eq. 2 (network), Alg. 2 with Eqs. 3-4 (analytic normals), Alg. 1
 (multiscale sphere tracing), the neural normal mapping of Sec. 5 and the
 threshold recurrences of Props. 1-2 (Sec. 3.3).
 
+``quantised_image`` writes the network with its hidden weights rounded to
+16 bits as the tensor-core paths store them; the oracle then evaluates it in
+FP64 (a reported mode that separates weight rounding from arithmetic error).
+
 ``fit_loss`` and ``adam_step`` (FP64, numpy on top of the C network) define
 the fitting objective and the optimiser step of the training path.  The
 paper trains each network of a sequence with an external framework it only
@@ -267,6 +271,36 @@ def _parse_sdfn(data: bytes):
     w_out = q[o:o + width]
     b_out = float(q[o + width])
     return in_dim, width, n_hidden, layers, w_out, b_out
+
+
+def round_bf16(x) -> np.ndarray:
+    """Each float32 of x rounded to the nearest bfloat16 (ties to even), returned as float32: the top
+    16 bits of the float32 pattern after adding half of the dropped range (0x7FFF plus the lowest
+    kept bit, so that an exact half rounds to the even neighbour).  Finite inputs only."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return r.astype(np.uint32).view(np.float32)
+
+
+def quantised_image(net_bytes: bytes, fmt: str = "bf16") -> bytes:
+    """The SDFN image of the network whose hidden weights are those the 16-bit tensor-core paths
+    multiply with, stored folded (flag 1): every hidden W' = omega W formed in FP64, rounded to
+    float32, then to bfloat16 ("bf16") or IEEE half ("f16"), round to nearest even; layer 0, the
+    biases and the output row as the float32 rounding of their folded FP64 values.  Evaluated by
+    this oracle in FP64, it separates the error of storing the weights in 16 bits from the error of
+    the 16-bit arithmetic on the activations (the reference-only mode of Sec. 5.1's normals)."""
+    in_dim, width, n_hidden, layers, w_out, b_out = _parse_sdfn(net_bytes)
+    hdr = bytearray(net_bytes[:32])
+    flags = int(np.frombuffer(bytes(hdr[28:32]), dtype="<u4")[0]) | 1
+    hdr[28:32] = np.array([flags], dtype="<u4").tobytes()
+    parts = []
+    for li, (W, b) in enumerate(layers):
+        w32 = W.astype(np.float32)
+        if li > 0:
+            w32 = round_bf16(w32) if fmt == "bf16" else w32.astype(np.float16).astype(np.float32)
+        parts += [w32.ravel(), b.astype(np.float32)]
+    parts += [w_out.astype(np.float32), np.array([b_out], np.float32)]
+    return bytes(hdr) + np.concatenate(parts).astype("<f4").tobytes()
 
 
 def eval_batch(net_bytes: bytes, pts, threads: int | None = None) -> np.ndarray:

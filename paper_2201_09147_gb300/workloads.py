@@ -17,6 +17,12 @@ evaluates a network.  The fitted sequences live in ``scenes/`` (written by
   (final_mode 1, delta_0 = 0.04, cap 40) at 1920 x 1080, then map the
   normals of the fine (256,3) onto the end points (Sec. 5).  Its plain
   comparison is the (256,3) alone, 40 steps, with its own normals.
+* ``normal_map_1080p_c64x2`` - the same frame with the (64,2) of the nested
+  sequence as the coarse net (the other reading of config 3's "coarse
+  64-wide net"), delta_0 = 0.04, cap 40.
+* ``normal_map_1080p_zero`` - the coarse (64,1) traced to its own zero set
+  (final_mode 0, cap 40), then the (256,3) normals mapped onto those end
+  points: the zero-set reading of Sec. 5.
 * ``three_level_512`` - the schedule of the last row of Tab. 3: the (64,1)
   for 20 steps to its delta shell (0.04), the (256,1) for 5 steps to its
   own shell (0.02) against the (256,3), whose normals are then mapped onto
@@ -127,6 +133,10 @@ def get(name: str, width: int | None = None, height: int | None = None, frames=N
                      1e-3, [1.0, 1.0, 1.0], 0, 512, 512, "s8_256x2.sdfn")
     elif name == "normal_map_1080p":
         w = Workload(name, ["s8_64x1.sdfn"], [0.04], [40], 1e-3, [1.0], 1, 1920, 1080, "s8_256x3.sdfn")
+    elif name == "normal_map_1080p_c64x2":
+        w = Workload(name, ["s8_64x2.sdfn"], [0.04], [40], 1e-3, [1.0], 1, 1920, 1080, "s8_256x3.sdfn")
+    elif name == "normal_map_1080p_zero":
+        w = Workload(name, ["s8_64x1.sdfn"], [0.0], [40], 1e-3, [1.0], 0, 1920, 1080, "s8_256x3.sdfn")
     elif name == "three_level_512":
         w = Workload(name, ["s8_64x1.sdfn", "s8_256x1.sdfn"], [0.04, 0.02], [20, 5], 1e-3, [1.0, 1.0], 1, 512, 512,
                      "s8_256x3.sdfn")

@@ -191,15 +191,17 @@ def test_trace_random_siren(sdf, precision):
         assert_bf16_ratio(ar, angle_report(fp16_twin(sdf, lb[0], g["pos_dev"], g["hit_dev"]), ref, hit), "siren")
 
 
+@pytest.mark.parametrize("name", ["normal_map_1080p", "normal_map_1080p_c64x2", "normal_map_1080p_zero"])
 @pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)
-def test_normal_map_workload_small(sdf, precision):
-    """Coarse (64,1) to its delta shell, then (256,3) normals (Sec. 5), 200 x 113 rays."""
-    wl = workloads.get("normal_map_1080p", 200, 113)
+def test_normal_map_workload_small(sdf, precision, name):
+    """Coarse (64,1) to its delta shell, then (256,3) normals (Sec. 5), 200 x 113 rays; and config 3's
+    other readings: the (64,2) as the coarse net, and the (64,1) traced to its zero set."""
+    wl = workloads.get(name, 200, 113)
     orig, dirs = wl.rays()
     lb = wl.level_bytes()
     g = gpu_trace(sdf, lb, precision, wl, orig, dirs)
     o = oracle_trace(lb, wl, orig, dirs)
-    rep = check_trace(g, o, precision, f"normal_map_small p={precision}")
+    rep = check_trace(g, o, precision, f"{name} small p={precision}")
     assert rep["n_both"] > 1000
     fine = sdf.Net(wl.fine_bytes(), precision)
     nrm = sdf.normal_map(fine, g["pos_dev"], g["hit_dev"])
@@ -213,7 +215,7 @@ def test_normal_map_workload_small(sdf, precision):
     assert ar["angle_p999"] <= TOL[precision][2]
     if precision == sdf.SDF_BF16:
         twin = fp16_twin(sdf, wl.fine_bytes(), g["pos_dev"], g["hit_dev"])
-        assert_bf16_ratio(ar, angle_report(twin, ref, hit), "normal_map_small")
+        assert_bf16_ratio(ar, angle_report(twin, ref, hit), name)
 
 
 @pytest.mark.parametrize("precision", PRECISIONS, ids=PRECISION_IDS)

@@ -37,7 +37,7 @@ def nesting_pairs(name):
     return pairs
 
 
-WORKLOADS_3D = ["nested_3level_512", "normal_map_1080p", "three_level_512", "silhouette_512"]
+WORKLOADS_3D = ["nested_3level_512", "normal_map_1080p", "normal_map_1080p_c64x2", "three_level_512", "silhouette_512"]
 
 
 @pytest.fixture(scope="module")
@@ -168,7 +168,7 @@ def first_hit_report(name, cap_factor=1):
             "false_hits": int((hit & ~has & ~grazing).sum())}
 
 
-@pytest.mark.parametrize("name", WORKLOADS_3D)
+@pytest.mark.parametrize("name", WORKLOADS_3D + ["normal_map_1080p_zero"])
 def test_first_hit_brute_force(name):
     """P6 on 32 x 32 images.  Every Alg. 1 hit lies on a brute-force root within 10 eps along the
     ray (or within eps of the level set without crossing it); the share of roots reached with the

@@ -567,3 +567,66 @@ def test_sine_arguments_of_the_committed_networks_stay_in_the_tested_range():
         m = oracle.max_preactivation(b, p)
         print(path.name, [round(float(v), 1) for v in m])
         assert max(m) <= 256.0
+
+
+# ---------------------------------------------------------------------------
+# 16-bit weight image (reference-only mode: weight rounding vs arithmetic error)
+# ---------------------------------------------------------------------------
+
+def test_round_bf16_ties_to_even_and_matches_torch():
+    """Hand cases of round-to-nearest-even at 8 significand bits, then random float32 values
+    against torch's own float32 -> bfloat16 conversion (a library routine)."""
+    torch = pytest.importorskip("torch")
+    h = np.array([1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, -(1 + 2 ** -8), 1 + 2 ** -8 + 2 ** -20, 2 ** -130], np.float32)
+    assert oracle.round_bf16(h).tolist() == [1.0, 1.0, 1 + 2 ** -6, -1.0, 1 + 2 ** -7, 2 ** -130]
+    x = (np.random.default_rng(5).standard_normal(200_000) * 30).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    assert np.array_equal(oracle.round_bf16(x), ref)
+
+
+def _params(data):
+    in_dim, width, n_hidden, layers, w_out, b_out = oracle._parse_sdfn(data)
+    return layers, w_out, b_out
+
+
+def test_quantised_image_rounds_only_the_hidden_weights():
+    """Hidden weights: the 16-bit rounding of float32(omega W) (within half an ulp, exactly
+    representable); layer 0, biases and the output row: float32 of the folded values."""
+    b = inputs.net_to_bytes(inputs.siren_init(3, 64, 2))
+    ref_layers, ref_wo, ref_bo = _params(b)
+    for fmt, ulp_bits in (("bf16", 8), ("f16", 11)):
+        layers, w_out, b_out = _params(oracle.quantised_image(b, fmt))
+        for li, ((W, bb), (W0, b0)) in enumerate(zip(layers, ref_layers)):
+            f32 = W0.astype(np.float32).astype(np.float64)
+            assert np.array_equal(bb, b0.astype(np.float32).astype(np.float64))
+            if li == 0:
+                assert np.array_equal(W, f32)
+                continue
+            # half an ulp: relative 2^-(bits) for normal values; half the smallest subnormal (2^-25)
+            # below half's normal range (bfloat16 has float32's exponent range)
+            err, mag = np.abs(W - f32), np.abs(f32)
+            normal = mag >= (2.0 ** -14 if fmt == "f16" else 2.0 ** -126)
+            assert (err[normal] / mag[normal]).max() <= 2.0 ** -ulp_bits * 1.0000001
+            assert np.all(err[~normal] <= 2.0 ** -25)
+            assert not np.array_equal(W, f32)  # a random layer is not 16-bit exact
+            if fmt == "bf16":
+                assert np.all((W.astype(np.float32).view(np.uint32) & 0xFFFF) == 0)
+            else:
+                assert np.array_equal(W.astype(np.float16).astype(np.float64), W)
+        assert np.array_equal(w_out, ref_wo.astype(np.float32).astype(np.float64)) and b_out == np.float32(ref_bo)
+
+
+def test_quantised_image_of_a_16bit_exact_net_evaluates_unchanged():
+    """A folded network whose hidden weights are already bfloat16 values is its own 16-bit image:
+    the oracle's f at random points is then identical, bit for bit."""
+    net = inputs.siren_init(4, 64, 2)
+    folded = inputs.SineNet(net.in_dim, net.width, net.n_hidden, net.omega0, net.omega,
+                            [w.astype(np.float64) * (net.omega0 if i == 0 else (net.omega if i <= net.n_hidden else 1.0))
+                             for i, w in enumerate(net.weights)],
+                            [b.astype(np.float64) * (net.omega0 if i == 0 else (net.omega if i <= net.n_hidden else 1.0))
+                             for i, b in enumerate(net.biases)], folded=True)
+    for i in range(1, net.n_hidden + 1):
+        folded.weights[i] = oracle.round_bf16(np.asarray(folded.weights[i], np.float32))
+    b = inputs.net_to_bytes(folded)
+    pts = inputs.random_points(9, 2000).astype(np.float64)
+    assert np.array_equal(oracle.eval_batch(oracle.quantised_image(b), pts), oracle.eval_batch(b, pts))
