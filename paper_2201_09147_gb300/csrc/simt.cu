@@ -244,23 +244,83 @@ __global__ void __launch_bounds__(kSimtThreads) grad_simt_kernel(const GradArgs 
     }
 }
 
-__global__ void mask_compact_kernel(const uint8_t* __restrict__ mask, int64_t n, int32_t* __restrict__ list,
-                                    unsigned long long* count, float* __restrict__ out) {
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < n;
-         base += stride) {
-        const int64_t i = base + lane;
-        const bool in = i < n;
-        const bool m = in && mask[i] != 0;
-        const long long k = warp_grab(count, m);
-        if (m) {
-            list[k] = static_cast<int32_t>(i);
-        } else if (in && out) {
-            out[i] = 0.0f;
-            out[n + i] = 0.0f;
-            out[2 * n + i] = 0.0f;
+// Compaction of the masked points for the gradient kernels: list[0 .. *count)
+// receives every i with mask[i] != 0 (in order within a block's 4096 points;
+// the blocks' slices in the order their atomics land), and, when out is given,
+// out[c * n + i] = 0 for every point (the gradient kernel then writes the
+// masked-in ones).  Each thread takes 16 consecutive mask bytes; the block
+// places its points with a warp scan and a scan over its 8 warps, and takes
+// its slice of the list with one atomic (one per 4096 points instead of one
+// per 32, which serialised on the counter).
+constexpr int kCompactPer = 16;
+constexpr int kCompactThreads = 256;
+
+__global__ void __launch_bounds__(kCompactThreads) mask_compact_kernel(const uint8_t* __restrict__ mask, int64_t n,
+                                                                      int32_t* __restrict__ list,
+                                                                      unsigned long long* count,
+                                                                      float* __restrict__ out) {
+    __shared__ uint32_t warp_off[kCompactThreads / 32];
+    __shared__ unsigned long long block_base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int64_t kBlockPts = static_cast<int64_t>(kCompactThreads) * kCompactPer;
+    // 16-byte vector stores of the zeros need every component row 16-byte aligned
+    const bool vec_out = out != nullptr && (n % 4) == 0 && (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
+    for (int64_t b0 = static_cast<int64_t>(blockIdx.x) * kBlockPts; b0 < n;
+         b0 += static_cast<int64_t>(gridDim.x) * kBlockPts) {
+        const int64_t i0 = b0 + static_cast<int64_t>(tid) * kCompactPer;
+        const bool full = i0 + kCompactPer <= n;
+        uint32_t bits = 0;  // bit j: point i0 + j is masked in
+        if (full && (reinterpret_cast<uintptr_t>(mask + i0) & 15u) == 0) {
+            const uint4 v = *reinterpret_cast<const uint4*>(mask + i0);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < kCompactPer; ++j) bits |= (((w[j >> 2] >> (8 * (j & 3))) & 0xFFu) != 0u ? 1u : 0u) << j;
+        } else {
+            for (int j = 0; j < kCompactPer; ++j)
+                if (i0 + j < n && mask[i0 + j] != 0) bits |= 1u << j;
         }
+        const uint32_t c = static_cast<uint32_t>(__popc(bits));
+        uint32_t x = c;  // inclusive scan over the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_off[warp] = x;
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t t = 0;
+            for (int w = 0; w < kCompactThreads / 32; ++w) {
+                const uint32_t v = warp_off[w];
+                warp_off[w] = t;
+                t += v;
+            }
+            block_base = t ? atomicAdd(count, static_cast<unsigned long long>(t)) : 0ull;
+        }
+        __syncthreads();
+        unsigned long long k = block_base + warp_off[warp] + (x - c);
+        while (bits) {
+            const int j = __ffs(bits) - 1;
+            bits &= bits - 1u;
+            list[k++] = static_cast<int32_t>(i0 + j);
+        }
+        if (out) {
+            if (vec_out && full) {
+                const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+                for (int comp = 0; comp < 3; ++comp)
+#pragma unroll
+                    for (int q = 0; q < kCompactPer / 4; ++q)
+                        reinterpret_cast<float4*>(out + comp * n + i0)[q] = z;
+            } else {
+                for (int j = 0; j < kCompactPer && i0 + j < n; ++j) {
+                    out[i0 + j] = 0.0f;
+                    out[n + i0 + j] = 0.0f;
+                    out[2 * n + i0 + j] = 0.0f;
+                }
+            }
+        }
+        __syncthreads();  // warp_off and block_base are rewritten by the next round
     }
 }
 
@@ -334,9 +394,10 @@ cudaError_t launch_wait_timeout_selftest(int* status, unsigned long long budget_
 cudaError_t launch_mask_compact(const uint8_t* mask, int64_t n, int32_t* list, unsigned long long* count, float* out,
                                 int num_sms, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    int blocks = static_cast<int>((n + 255) / 256);
-    if (blocks > num_sms * 8) blocks = num_sms * 8;
-    mask_compact_kernel<<<blocks, 256, 0, s>>>(mask, n, list, count, out);
+    const int64_t per_block = static_cast<int64_t>(kCompactThreads) * kCompactPer;
+    int64_t blocks = (n + per_block - 1) / per_block;
+    if (blocks > static_cast<int64_t>(num_sms) * 8) blocks = static_cast<int64_t>(num_sms) * 8;
+    mask_compact_kernel<<<static_cast<int>(blocks), kCompactThreads, 0, s>>>(mask, n, list, count, out);
     return cudaGetLastError();
 }
 
