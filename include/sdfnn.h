@@ -350,7 +350,7 @@ void sdf_frame_queue_free(sdf_frame_queue_t queue);
  * sdf_train_shape_info: the length of theta and the workspace bytes the
  *   forward / backward pair needs for n points at that precision (either
  *   pointer may be NULL).  FP32: (1 + 8k) w floats per point; 16-bit:
- *   (1 + 6k) w floats per point plus two 16-bit copies of the hidden weights.
+ *   (1 + 5k) w floats per point plus two 16-bit copies of the hidden weights.
  * sdf_train_forward: f (n) and the unnormalised grad f (3, n) at pts (3, n)
  *   (pt_time (n) for 4-input networks, else NULL); saves the layers'
  *   pre-activations in `workspace` (device, 256-byte aligned, of the size

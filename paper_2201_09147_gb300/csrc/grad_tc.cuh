@@ -100,6 +100,19 @@ __host__ __device__ inline GradLayout grad_layout(int KH) {
     return L;
 }
 
+// Saved training records of hidden layer l (training forward -> backward and
+// weight gradient); np = the point count rounded up to whole 64-point tiles.
+// A_l is [l][np/4][W][4] floats and H_l [l][np/2][W][2] uint2, so that the
+// records of 4 (A) or 2 (H) consecutive points of one unit are one 16-byte
+// vector for the kernels that read them.
+__host__ __device__ inline int64_t rec_points(int64_t n) { return (n + 63) / 64 * 64; }
+__host__ __device__ inline size_t rec_a(size_t l, size_t np, int W, size_t p, int m) {
+    return ((l * (np / 4) + p / 4) * static_cast<size_t>(W) + static_cast<size_t>(m)) * 4 + (p & 3);
+}
+__host__ __device__ inline size_t rec_h(size_t l, size_t np, int W, size_t p, int m) {
+    return ((l * (np / 2) + p / 2) * static_cast<size_t>(W) + static_cast<size_t>(m)) * 2 + (p & 1);
+}
+
 // Byte offset in the MN-major 16-bit X of the 16-byte chunk holding points
 // 2c, 2c + 1 (all four streams) of half h for feature m.
 template <int W>
@@ -213,8 +226,8 @@ __device__ __forceinline__ void warp_sum32(float (&v)[32], int lane) {
 }
 
 // TRAIN (16-bit operands only): the training forward.  Besides grad f the
-// kernel saves A_0 and, per hidden layer, (A_l, H_l) = (W_l P_{l-1} + b_l,
-// W_l G_{l-1}) in FP32 for the backward, and the output layer runs in FP32 on
+// kernel saves A_0 and, per hidden layer, A_l = W_l P_{l-1} + b_l in FP32 and
+// H_l = W_l G_{l-1} in the 16-bit operand type for the backward, and the output layer runs in FP32 on
 // the CUDA cores instead of as an MMA: f = w_out . sin(A_k) + b_out and
 // grad f = w_out . (cos(A_k) (.) H_k), summed over the features by a warp
 // butterfly and shared-memory atomics, so no tangent of the last layer is
@@ -510,14 +523,14 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
                             uint32_t w[4];
+                            float sa[2];  // this pair's saved records: A_l, and H_l in 16 bits
+                            uint2 sh[2];
 #pragma unroll
                             for (int e = 0; e < 2; ++e) {
                                 const int j = (2 * c + e) * 4;
                                 const float A = v[j] + bb;
-                                const int idx = idxs[p0 + q * 8 + 2 * c + e];
-                                if (idx >= 0)
-                                    a.save_q[(static_cast<size_t>(l) * a.n + idx) * W + m] =
-                                        make_float4(A, v[j + 1], v[j + 2], v[j + 3]);
+                                sa[e] = A;
+                                sh[e] = make_uint2(pack16x2<F16>(v[j + 1], v[j + 2]), pack16x2<F16>(v[j + 3], 0.0f));
                                 float sn, cs;
                                 sincos_fast(A, &sn, &cs);
                                 if (last) {
@@ -532,6 +545,15 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
                                 }
                             }
                             if (!last) st_shared_v4(x_s + xoff16<W>(h, m, q * 4 + c), w[0], w[1], w[2], w[3]);
+                            // the pair's points are consecutive and the first even (training batches
+                            // run without a list); a pair past the batch end stores into the padding
+                            const int idx = idxs[p0 + q * 8 + 2 * c];
+                            if (idx >= 0) {
+                                const size_t np = static_cast<size_t>(a.save_np);
+                                *reinterpret_cast<float2*>(a.save_a + rec_a(l, np, W, idx, m)) = make_float2(sa[0], sa[1]);
+                                *reinterpret_cast<uint4*>(a.save_h + rec_h(l, np, W, idx, m)) =
+                                    make_uint4(sh[0].x, sh[0].y, sh[1].x, sh[1].y);
+                            }
                         }
                         if (last) {
                             warp_sum32(v, lane);

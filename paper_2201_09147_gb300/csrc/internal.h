@@ -78,7 +78,9 @@ struct GradArgs {
     // training forward of the tensor-core path (the kernel's TRAIN variant): the
     // pre-activations saved for the backward, f written beside grad f
     float* save_a0;                 // [n][width] A_0
-    float4* save_q;                 // [n_hidden][n][width] (A_l, H_l^x, H_l^y, H_l^z), hidden layers 1..k
+    float* save_a;                  // A_l, hidden layers 1..k (layout: rec_a in grad_tc.cuh)
+    uint2* save_h;                  // (H_l^x, H_l^y | H_l^z, 0) in the operand type (layout: rec_h)
+    int64_t save_np;                // points of the record layout: n rounded up to 64
     float* out_f;                   // (n)
     const float* out_bias;          // device address of b_out
 };
@@ -121,7 +123,8 @@ struct TrainWork {
     // tensor-core path
     uint8_t* wbf;                  // [k] 16-bit W_l images (K-major, 128-byte swizzle, rows padded to 128)
     uint8_t* wbft;                 // [k] 16-bit W_l^T images, same layout
-    float4* q;                     // [k][n][w] (A_l, H_l^x, H_l^y, H_l^z)
+    float* qa;                     // A_l records (rec_a layout)
+    uint2* qh;                     // H_l^x, H_l^y | H_l^z, 0 as 16-bit operand-type values (rec_h layout)
     uint8_t* dtile;                // [k][n_halves][w * 256] 16-bit (dA_l, dH_l) tiles
     int64_t n_halves;              // 2 ceil(n / 64): half-tiles of 32 points, in pairs
 };

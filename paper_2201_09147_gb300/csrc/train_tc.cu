@@ -51,7 +51,9 @@ size_t train_tc_workspace_bytes(const TrainShape& sh, int64_t n) {
     const size_t W = sh.width, k = sh.n_hidden, N = static_cast<size_t>(n);
     const size_t halves = tile_halves(N);
     const size_t wimg = static_cast<size_t>(rows_pad_of(sh.width)) * W * 2 * k;
-    return 2 * align256(wimg) + align256(N * W * 4) + align256(k * N * W * 16) + align256(k * halves * W * 256) + 256;
+    const size_t NP = static_cast<size_t>(rec_points(n));
+    return 2 * align256(wimg) + align256(N * W * 4) + align256(k * NP * W * 4) + align256(k * NP * W * 8) +
+           align256(k * halves * W * 256) + 256;
 }
 
 TrainWork train_tc_work(const TrainShape& sh, int64_t n, void* ws) {
@@ -66,8 +68,11 @@ TrainWork train_tc_work(const TrainShape& sh, int64_t n, void* ws) {
     p += align256(wimg);
     w.z0 = reinterpret_cast<float*>(p);
     p += align256(N * W * 4);
-    w.q = reinterpret_cast<float4*>(p);
-    p += align256(k * N * W * 16);
+    const size_t NP = static_cast<size_t>(rec_points(n));
+    w.qa = reinterpret_cast<float*>(p);
+    p += align256(k * NP * W * 4);
+    w.qh = reinterpret_cast<uint2*>(p);
+    p += align256(k * NP * W * 8);
     w.dtile = p;
     p += align256(k * halves * W * 256);
     w.counters = reinterpret_cast<unsigned long long*>(p);
@@ -112,13 +117,26 @@ struct TrainTcArgs {
     const float* d_f;            // (n)
     const float* d_grad;         // SoA (3, n)
     const float* a0;             // [n][W] A_0 (training forward)
-    const float4* q;             // [k][n][W] (A_l, H_l)
+    const float* qa;             // A_l records (rec_a layout)
+    const uint2* qh;             // H_l records, 16-bit operand type (x, y | z, 0) (rec_h layout)
+    int64_t np;                  // points of the record layout (n rounded up to 64)
     uint8_t* dtile;              // [k][n_halves][W * 256]: D_l tiles, 16-bit, the swizzled operand image
     int64_t n_halves;
     float* d_theta;
     int* status;
     const uint32_t* amax_bits;   // bits of max |d_f|, |d_grad| (a non-negative float)
 };
+
+// A saved (A_l, H_l) from its A and its 16-bit H image (x, y | z, 0).  The
+// kernels load the records of a chunk of consecutive points as 16-byte
+// vectors (4 points' A, 2 points' H per load), all in flight at once, and
+// decode each one where it is used.
+template <bool F16>
+__device__ __forceinline__ float4 decode_q(float a, uint32_t hxy, uint32_t hz) {
+    return make_float4(a, from16<F16>(static_cast<uint16_t>(hxy & 0xFFFFu)), from16<F16>(static_cast<uint16_t>(hxy >> 16)),
+                       from16<F16>(static_cast<uint16_t>(hz & 0xFFFFu)));
+}
+__device__ __forceinline__ float pick4(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
 
 // Largest |d_f|, |d_grad| of the batch, as the bits of a non-negative float
 // (their order is the floats' order, so an integer maximum serves).
@@ -305,7 +323,6 @@ __global__ void __launch_bounds__(GradCfg<W, kOpBF16>::THREADS) train_bwd_tc_ker
                     if (!ok) break;
                     tc_fence_after();
                 }
-                const float4* ql = l >= 0 ? a.q + static_cast<size_t>(l) * a.n * W : nullptr;
                 uint8_t* dt = l >= 0 ? a.dtile + (static_cast<size_t>(l) * a.n_halves + T) * (W * 256u) : nullptr;
                 float s_b = 0.0f, s_o = 0.0f, s_w[4] = {0.0f, 0.0f, 0.0f, 0.0f};
                 for (int q = 0; q < C::HROWS / 32; ++q) {
@@ -318,11 +335,18 @@ __global__ void __launch_bounds__(GradCfg<W, kOpBF16>::THREADS) train_bwd_tc_ker
                     }
                     if (live && l >= 0) {
                         // the chunk's 8 saved (A, H): independent read-only loads, all in flight at once
-                        float4 Qc[8];
+                        // the chunk's 8 points are consecutive, the first a multiple of 8
+                        float4 a4[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+                        uint4 h4[4] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u),
+                                       make_uint4(0u, 0u, 0u, 0u)};
+                        const int idx8 = idxs[p0 + q * 8];
+                        if (idx8 >= 0) {
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const int idx = idxs[p0 + q * 8 + e];
-                            Qc[e] = idx >= 0 ? __ldg(ql + static_cast<size_t>(idx) * W + m) : make_float4(0.f, 0.f, 0.f, 0.f);
+                            for (int u = 0; u < 2; ++u)
+                                a4[u] = __ldg(reinterpret_cast<const float4*>(a.qa + rec_a(l, a.np, W, idx8 + 4 * u, m)));
+#pragma unroll
+                            for (int u = 0; u < 4; ++u)
+                                h4[u] = __ldg(reinterpret_cast<const uint4*>(a.qh + rec_h(l, a.np, W, idx8 + 2 * u, m)));
                         }
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
@@ -330,7 +354,11 @@ __global__ void __launch_bounds__(GradCfg<W, kOpBF16>::THREADS) train_bwd_tc_ker
 #pragma unroll
                             for (int e = 0; e < 2; ++e) {
                                 const int p = p0 + q * 8 + 2 * c + e, j = (2 * c + e) * 4;
-                                const float4 Q = Qc[2 * c + e];
+                                const int ee = 2 * c + e;  // point of the chunk
+                                const uint4& hp = h4[ee >> 1];
+                                const float4 Q = idxs[p] >= 0 ? decode_q<F16>(pick4(a4[ee >> 2], ee & 3),
+                                                                              (ee & 1) ? hp.z : hp.x, (ee & 1) ? hp.w : hp.y)
+                                                              : make_float4(0.f, 0.f, 0.f, 0.f);
                                 float y0, y1, y2, y3;
                                 if (top) {
                                     // the adjoints enter scaled by S (a power of two): 16-bit operands
@@ -567,7 +595,6 @@ __global__ void __launch_bounds__(WgCfg<W>::THREADS) train_wgrad_tc_kernel(const
             const float4 w0k = reinterpret_cast<const float4*>(w0s)[k];
             uint32_t g = 0;
             for (int l = 0; l < KH && ok; ++l) {
-                const float4* ql = l > 0 ? a.q + static_cast<size_t>(l - 1) * a.n * W : nullptr;
                 for (int64_t kb = kb_lo; kb < kb_hi && ok; ++kb, ++g) {
                     const uint32_t stage = static_cast<uint32_t>(g % C::NS), use = static_cast<uint32_t>(g / C::NS);
                     if (use > 0)
@@ -577,16 +604,32 @@ __global__ void __launch_bounds__(WgCfg<W>::THREADS) train_wgrad_tc_kernel(const
                     const uint32_t sx = st_s + stage * C::STAGE + C::A_BYTES;
                     const int64_t pbase = (kb >> 1) * 32 + (kb & 1) * 16;
                     // the K block's 16 saved (A, H) (or A_0): independent read-only loads first
-                    float4 Qc[16];
+                    // the K block's 16 consecutive points (pbase a multiple of 16): layer l - 1's records
+                    // as 4 + 8 16-byte loads, or A_0 (layer 0, whose tangents are W_0's columns)
+                    float4 a4[4];
+                    uint4 h4[8];
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const int64_t p = pbase + e;
-                        if (p >= a.n)
-                            Qc[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        else if (l > 0)
-                            Qc[e] = __ldg(ql + static_cast<size_t>(p) * W + k);
-                        else
-                            Qc[e] = make_float4(__ldg(a.a0 + static_cast<size_t>(p) * W + k), w0k.x, w0k.y, w0k.z);
+                    for (int u = 0; u < 4; ++u) a4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) h4[u] = make_uint4(0u, 0u, 0u, 0u);
+                    if (pbase < a.n) {
+                        if (l > 0) {
+#pragma unroll
+                            for (int u = 0; u < 4; ++u)
+                                a4[u] = __ldg(reinterpret_cast<const float4*>(a.qa + rec_a(l - 1, a.np, W, pbase + 4 * u, k)));
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                h4[u] = __ldg(reinterpret_cast<const uint4*>(a.qh + rec_h(l - 1, a.np, W, pbase + 2 * u, k)));
+                        } else {
+#pragma unroll
+                            for (int u = 0; u < 16; ++u) {
+                                const float v0 = pbase + u < a.n ? __ldg(a.a0 + static_cast<size_t>(pbase + u) * W + k) : 0.0f;
+                                if ((u & 3) == 0) a4[u >> 2].x = v0;
+                                else if ((u & 3) == 1) a4[u >> 2].y = v0;
+                                else if ((u & 3) == 2) a4[u >> 2].z = v0;
+                                else a4[u >> 2].w = v0;
+                            }
+                        }
                     }
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
@@ -594,7 +637,14 @@ __global__ void __launch_bounds__(WgCfg<W>::THREADS) train_wgrad_tc_kernel(const
 #pragma unroll
                         for (int e = 0; e < 2; ++e) {
                             const int64_t p = pbase + 2 * c + e;
-                            const float4 Q = Qc[2 * c + e];
+                            const int ee = 2 * c + e;
+                            const uint4& hp = h4[ee >> 1];
+                            const float A = pick4(a4[ee >> 2], ee & 3);
+                            // layer 0's tangents are W_0's columns (FP32); above, the saved H_l;
+                            // points past the batch (the padding is never written) are zero
+                            float4 Q = l > 0 ? decode_q<F16>(A, (ee & 1) ? hp.z : hp.x, (ee & 1) ? hp.w : hp.y)
+                                             : make_float4(A, w0k.x, w0k.y, w0k.z);
+                            if (p >= a.n) Q = make_float4(0.f, 0.f, 0.f, 0.f);
                             float sn = 0.0f, cs = 0.0f;
                             if (p < a.n) sincos_fast(Q.x, &sn, &cs);
                             w[2 * e] = pack16x2<F16>(sn, cs * Q.y);
@@ -668,7 +718,9 @@ cudaError_t forward_tc_w(const TrainArgs& a, int num_sms, cudaStream_t s) {
     ga.grab = a.w.counters;
     ga.status = a.status;
     ga.save_a0 = a.w.z0;
-    ga.save_q = a.w.q;
+    ga.save_a = a.w.qa;
+    ga.save_h = a.w.qh;
+    ga.save_np = rec_points(a.n);
     ga.out_f = a.out_f;
     ga.out_bias = a.theta + sh.off_bout;
     using C = GradCfg<W, F16 ? kOpF16 : kOpBF16>;
@@ -698,7 +750,9 @@ cudaError_t backward_tc_w(const TrainArgs& a, int num_sms, cudaStream_t s) {
     t.d_f = a.d_f;
     t.d_grad = a.d_grad;
     t.a0 = a.w.z0;
-    t.q = a.w.q;
+    t.qa = a.w.qa;
+    t.qh = a.w.qh;
+    t.np = rec_points(a.n);
     t.dtile = a.w.dtile;
     t.n_halves = a.w.n_halves;
     t.d_theta = a.d_theta;
