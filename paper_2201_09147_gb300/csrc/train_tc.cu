@@ -348,6 +348,18 @@ __global__ void __launch_bounds__(GradCfg<W, kOpBF16>::THREADS) train_bwd_tc_ker
                             for (int u = 0; u < 4; ++u)
                                 h4[u] = __ldg(reinterpret_cast<const uint4*>(a.qh + rec_h(l, a.np, W, idx8 + 2 * u, m)));
                         }
+                        // the next chunk's records (this layer's next chunk, or the first chunk of the
+                        // layer below) towards L2 while this one is processed
+                        {
+                            const int ln = q + 1 < C::HROWS / 32 ? l : l - 1;
+                            const int in8 = idxs[p0 + ((q + 1) % (C::HROWS / 32)) * 8];
+                            if (ln >= 0 && in8 >= 0) {
+#pragma unroll
+                                for (int u = 0; u < 2; ++u) prefetch_l2(a.qa + rec_a(ln, a.np, W, in8 + 4 * u, m));
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) prefetch_l2(a.qh + rec_h(ln, a.np, W, in8 + 2 * u, m));
+                            }
+                        }
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
                             uint32_t w[4];
