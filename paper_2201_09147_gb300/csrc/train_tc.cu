@@ -138,6 +138,9 @@ __device__ __forceinline__ float4 decode_q(float a, uint32_t hxy, uint32_t hz) {
 }
 __device__ __forceinline__ float pick4(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
 
+// Hint: bring the line holding p into L2 (no register, no completion to wait for).
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // Largest |d_f|, |d_grad| of the batch, as the bits of a non-negative float
 // (their order is the floats' order, so an integer maximum serves).
 __global__ void adjoint_max_kernel(const float* __restrict__ d_f, const float* __restrict__ d_grad, int64_t n,
