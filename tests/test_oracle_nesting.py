@@ -141,21 +141,24 @@ def _box_interval(o, v, lo=-1.0, hi=1.0):
 MARCH_H = 1e-3
 
 
-def first_hit_report(name, cap_factor=1):
-    """Alg. 1 (caps times cap_factor) against the dense-march first root on a 32 x 32 image."""
+def first_hit_report(name, cap_factor=1, time=None):
+    """Alg. 1 (caps times cap_factor) against the dense-march first root on a 32 x 32 image (4-D
+    networks at the given time)."""
     wl = workloads.get(name, 32, 32)
     orig, dirs = wl.rays()
     lb = wl.level_bytes()
     onets = [oracle.Net(b) for b in lb]
-    tp = oracle.TraceParams([oracle.SDF.of_net(n) for n in onets], wl.delta, [cap_factor * c for c in wl.caps],
-                            wl.step_scale, wl.eps, final_mode=wl.final_mode)
+    t = 0.0 if time is None else float(np.float32(time))
+    tp = oracle.TraceParams([oracle.SDF.of_net(n, time=t) for n in onets], wl.delta,
+                            [cap_factor * c for c in wl.caps], wl.step_scale, wl.eps, final_mode=wl.final_mode)
     r = tp.trace_batch(orig, dirs)
-    if name not in _ROOTS:
+    if (name, time) not in _ROOTS:
         o, v = orig.astype(np.float64), dirs.astype(np.float64)
         tn, tf = _box_interval(o, v)
         d_last = wl.delta[-1] if wl.final_mode == 1 else 0.0
-        _ROOTS[name] = oracle.first_roots_batch(lb[-1], d_last, o, v, tn, tf, h=MARCH_H)
-    t_root, fmin = _ROOTS[name]
+        _ROOTS[(name, time)] = oracle.first_roots_batch(lb[-1], d_last, o, v, tn, tf, h=MARCH_H,
+                                                        time=None if time is None else t)
+    t_root, fmin = _ROOTS[(name, time)]
     hit = r["hit"].astype(bool)
     has = ~np.isnan(t_root)
     same = hit & has & (np.abs(r["tau"].astype(np.float64) - t_root) <= 10 * wl.eps)
@@ -181,3 +184,19 @@ def test_first_hit_brute_force(name):
         assert rp["later_root"] <= max(1, 0.01 * rp["roots"])  # a thin feature skipped at most rarely
     assert rep["roots"] > 150
     assert rep4["reached_first_root"] >= 0.95 * rep4["roots"]
+
+
+@pytest.mark.parametrize("name", ["animation_32", "animation_32_single"])
+def test_first_hit_brute_force_animated(name):
+    """P6 for config 4's schedules (4-D networks, Sec. 3.2) at the first frame's time and mid-way,
+    with the same criteria as the 3-D workloads (the animated pair traces the same coarse level as
+    animation_32: only its normals differ)."""
+    for t in (0.0, 0.5):
+        rep = first_hit_report(name, time=t)
+        rep4 = first_hit_report(name, 4, time=t)
+        print(name, "t", t, "configured caps", rep, "4x caps", rep4)
+        for rp in (rep, rep4):
+            assert rp["false_hits"] == 0
+            assert rp["later_root"] <= max(1, 0.01 * rp["roots"])
+        assert rep["roots"] > 150
+        assert rep4["reached_first_root"] >= 0.95 * rep4["roots"]
