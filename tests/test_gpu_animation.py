@@ -10,7 +10,7 @@ import torch
 
 import oracle
 from paper_2201_09147_gb300 import inputs, workloads
-from parity import PRECISION_IDS, PRECISIONS, TOL, angle_report, bf16_within_fp16, trace_report
+from parity import DECISION_MARGIN, PRECISION_IDS, PRECISIONS, TOL, angle_report, bf16_within_fp16, trace_report
 
 pytestmark = pytest.mark.gpu
 
@@ -182,11 +182,16 @@ def test_plan_three_dimensional_and_trace_only(sdf):
     assert tr.normal is None and torch.equal(tr.pos, pos) and torch.equal(tr.hit, hit)
 
 
+@pytest.mark.parametrize("name", ANIM_WORKLOADS)
 @pytest.mark.parametrize("precision", [1, 3], ids=["bf16", "fp16"])
-def test_animation_32_frames_sampled(sdf, precision):
-    """All 32 frames (31,858,688 rays) in one autotuned plan, as the benchmark runs it; the
-    oracle traces 120 sampled rays of every frame."""
-    wl = workloads.get("animation_32")
+def test_animation_32_frames_sampled(sdf, precision, name):
+    """All 32 frames (31,858,688 rays) in one autotuned plan, as the benchmark runs it, for each of
+    config 4's schedules; the oracle traces 120 sampled rays of every frame.  The single-network
+    schedule traces the 4-D (256,3) itself with 16-bit operands (no head/remainder split at width
+    256) for up to 40 steps: its end points carry that per-step value error (margin m) along the
+    ray, so it is held to the capped-schedule criteria: every GPU hit lies, in FP64, within eps + 2m
+    of the zero set, and the end points of the common hits within the BF16 position tolerance."""
+    wl = workloads.get(name)
     orig, dirs, tm, off = workloads.batch_rays(wl.frames)
     o, d, t = _dev(orig), _dev(dirs), _dev(tm)
     nets = [sdf.Net(b, precision) for b in wl.level_bytes()]
@@ -205,6 +210,13 @@ def test_animation_32_frames_sampled(sdf, precision):
     agree_tol, pos_tol, ang_tol = TOL[precision]
     rep = trace_report(pos[:, flat], hit[flat], o_pos, o_hit)
     print(precision, {k: v for k, v in rep.items() if k != "both"})
+    if name == "animation_32_single":
+        gh = hit[flat].astype(bool)
+        p4 = np.vstack([pos[:, flat], tm[flat][None, :]]).astype(np.float64)
+        resid = np.abs(oracle.eval_batch(wl.fine_bytes(), p4[:, gh]))
+        print("FP64 residual at the GPU hits: max", float(resid.max()), "bound", wl.eps + 2 * DECISION_MARGIN[precision])
+        assert resid.max() <= wl.eps + 2 * DECISION_MARGIN[precision]
+        pos_tol = TOL[1][1]
     assert rep["agree"] >= agree_tol and rep["pos_p999"] <= pos_tol
     assert rep["n_both"] > 300
     ar = angle_report(nrm[:, flat], o_nrm, hit[flat].astype(bool))
