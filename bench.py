@@ -878,6 +878,15 @@ def main():
                    "normal_deg_max": float(ang.max()) if ang.size else None,
                    # hits where |grad f| < 1e-12 get (0, 0, 0): counted, and part of the angles above
                    "zero_normals": int((np.linalg.norm(gn[:, gh], axis=0) == 0.0).sum())}
+            # FP64 residual of the GPU's end points against the level set the last level traces
+            d_last = wl.delta[-1] if wl.final_mode == 1 else 0.0
+            lvl = np.abs(oracle.eval_batch(wl.level_bytes()[-1], gp[:, gh].astype(np.float64)) - d_last)
+            out["end_residual_p999"] = _q(lvl, 0.999)
+            out["end_residual_max"] = float(lvl.max()) if lvl.size else None
+            # end to end: the GPU normal at its end point against the FP64 normal at the oracle's
+            ang_e2e = _angles(gn[:, both], onrm[:, both])
+            out["normal_deg_end_to_end_p999"] = _q(ang_e2e, 0.999)
+            out["normal_deg_end_to_end_max"] = float(ang_e2e.max()) if ang_e2e.size else None
             if qfmt:
                 # the oracle on the 16-bit hidden weights the kernel multiplies with: the angle from
                 # the exact FP64 normals is the weight rounding alone, the angle to the GPU's the
