@@ -331,12 +331,14 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
             // stages in MMA order: per slot of the schedule, the stages of its layer
             // (K blocks SKB * sg .. of every TMEM tile: contiguous in the weight image)
             uint32_t g = 0;
+            int lh[2] = {0, 0};  // slot of each half within its pair (grp mod GPP, counted)
             for (int k = 0; k < n_groups + LAG && ok; ++k)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int grp = k - h * LAG;
                     if (grp < 0 || grp >= n_groups) continue;
-                    const int l = grp % GPP;
+                    const int l = lh[h];
+                    lh[h] = l + 1 == GPP ? 0 : l + 1;
                     for (int sg = 0; sg < C::STAGES_PER_LAYER && l < KH && ok; ++sg, ++g) {
                         const uint32_t stage = g % C::NS, use = g / C::NS;
                         if (use > 0) ok = mbar_wait_bounded(bar_empty + 8u * stage, (use - 1) & 1u, a.status, abort_flag);
@@ -359,12 +361,14 @@ __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS) grad_tc_kernel(const 
             constexpr uint32_t idesc_h = idesc_f32acc(128, C::HROWS, F16 || FP8) | (FP8 ? 0u : kIdescMajorMnB);
             constexpr uint32_t idesc_o = idesc_f32acc(128, 16, F16 || FP8) | (FP8 ? 0u : kIdescMajorMnA);
             uint32_t g = 0, xr_phase[2] = {0u, 0u};
+            int lh[2] = {0, 0};
             for (int k = 0; k < n_groups + LAG && ok; ++k)
 #pragma unroll
                 for (int h = 0; h < 2 && ok; ++h) {
                     const int grp = k - h * LAG;
                     if (grp < 0 || grp >= n_groups) continue;
-                    const int l = grp % GPP;
+                    const int l = lh[h];
+                    lh[h] = l + 1 == GPP ? 0 : l + 1;
                     ok = mbar_wait_bounded(bar_xready + 8u * h, xr_phase[h], a.status, abort_flag);
                     xr_phase[h] ^= 1u;
                     if (!ok) break;
