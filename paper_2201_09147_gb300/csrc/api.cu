@@ -25,6 +25,7 @@ struct sdf_net {
     float time = 0.0f;
     float bout = 0.0f;
     float* d_f32 = nullptr;       // folded FP32 parameters
+    std::vector<float> h_f32;     // the same, on the host (launch parameters of the width-64 trace)
     uint8_t* d_bf16 = nullptr;    // swizzled 16-bit hidden weights (SDF_BF16 / SDF_FP16)
     size_t off_w0 = 0, off_b0 = 0, off_wt[kMaxHidden] = {}, off_bh[kMaxHidden] = {}, off_wout = 0;
     uint32_t bf16_layer_bytes = 0;
@@ -468,6 +469,7 @@ int load_from_memory(const uint8_t* buf, size_t len, int precision, int device, 
     }
     cudaError_t e = cudaMalloc(&n->d_f32, f32.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(n->d_f32, f32.data(), f32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    n->h_f32 = f32;
     if (e == cudaSuccess && !bf.empty()) {
         e = cudaMalloc(&n->d_bf16, bf.size());
         if (e == cudaSuccess) e = cudaMemcpy(n->d_bf16, bf.data(), bf.size(), cudaMemcpyHostToDevice);
@@ -552,6 +554,31 @@ size_t trace_scratch_bytes(int m, int64_t n) {
     return 2 * kMaxLevels * sizeof(unsigned long long) + ((m > 1) ? 2 * static_cast<size_t>(n) * sizeof(int32_t) : 0);
 }
 
+// The width-64 parameters of one level as launch parameters (TraceConsts):
+// the same values, in the same pair layout, as the kernel would otherwise
+// stage in shared memory, the scalar time folded into the layer-0 bias by
+// one fused multiply-add as there.
+void fill_trace_consts(const sdf_net* n, LevelArgs& la) {
+    const float* f = n->h_f32.data();
+    const float *w0 = f + n->off_w0, *b0 = f + n->off_b0, *bl = f + n->off_bh[n->n_hidden - 1], *wo = f + n->off_wout;
+    const bool timed = la.ray_time != nullptr && n->in_dim == 4;
+    float* bls = &la.k.bl[0].x;
+    float* wos = &la.k.wo[0].x;
+    for (int i = 0; i < kConstWidth; ++i) {
+        const int p = i >> 1, e = i & 1;
+        const float wt = n->in_dim == 4 ? w0[i * 4 + 3] : 0.0f;
+        const float bb = timed ? b0[i] : std::fma(wt, la.time, b0[i]);
+        float* pa = &la.k.w0[2 * p].x;
+        float* pb = &la.k.w0[2 * p + 1].x;
+        pa[e] = w0[i * n->in_dim + 0];
+        pa[2 + e] = w0[i * n->in_dim + 1];
+        pb[e] = w0[i * n->in_dim + 2];
+        pb[2 + e] = bb;
+        bls[i] = bl[i];
+        wos[i] = wo[i];
+    }
+}
+
 // Zeroes the 2 * kMaxLevels counters and launches the levels of Alg. 1 on
 // `s` (the validated parameters' device current); list0 / list1 hold n
 // entries each (unused with one level).  tiles: per-level tile counts for
@@ -591,6 +618,7 @@ int launch_levels_at(const sdf_trace_params* P, const float* orig, const float* 
         la.out_count = last ? nullptr : &counters[kMaxLevels + j];
         la.grab = &counters[j];
         la.status = status;
+        if (net->width == kConstWidth) fill_trace_consts(net, la);
         e = (net->precision != SDF_FP32) ? launch_trace_level_tc(la, num_sms, s)
                                          : launch_trace_level_simt(la, num_sms, s);
         if (e != cudaSuccess) return cuda_fail(e, "launching trace level");

@@ -34,8 +34,24 @@ struct NetView {
     const uint8_t* wout_q;
 };
 
+// The per-unit FP32 parameters of a width-64 network that the trace kernel
+// reads for every ray and step, carried in the launch parameters so that its
+// FMAs read them from the constant bank instead of shared memory.  Layer 0 on
+// unit pairs p = (2p, 2p+1): w0[2p] = (w_x0, w_x1, w_y0, w_y1) and
+// w0[2p+1] = (w_z0, w_z1, b_0, b_1), the bias holding w_t * time when the
+// time is one scalar for all rays; bl = bias of the last hidden layer and
+// wo = the output weights, four units per float4.  Filled by the host for
+// width-64 networks only.
+constexpr int kConstWidth = 64;
+struct TraceConsts {
+    float4 w0[kConstWidth];
+    float4 bl[kConstWidth / 4];
+    float4 wo[kConstWidth / 4];
+};
+
 // One level of Alg. 1 as launched.
 struct LevelArgs {
+    TraceConsts k;    // width-64 networks (see TraceConsts)
     NetView net;
     float d;          // t = f(p) - d
     float scale;      // step = scale * t

@@ -137,8 +137,10 @@ __device__ __forceinline__ void stage_layer0_pairs(const NetView& net, float tim
 // w_x p_x + (w_y p_y + (w_z p_z + b)), so each lane rounds as a scalar FMA
 // would.  With TIMED the ray's time is read here (it is not kept in a
 // register between steps).
+// w0p: the pairs in shared memory, or (width 64) in the launch parameters,
+// where the loop is unrolled whole so that every index is a constant.
 template <int W, bool F16, bool SPLIT, bool TIMED>
-__device__ __forceinline__ void trace_layer0(const LevelArgs& a, const float* w0s, const float* wts, const Ray& ray,
+__device__ __forceinline__ void trace_layer0(const LevelArgs& a, const float4* w0p, const float* wts, const Ray& ray,
                                              int row, uint32_t x_s, uint32_t xlo_s) {
     const float tm = (TIMED && ray.state == kSlotActive) ? __ldg(a.ray_time + ray.idx) : 0.0f;
     const float2 px = make_float2(ray.px, ray.px), py = make_float2(ray.py, ray.py), pz = make_float2(ray.pz, ray.pz);
@@ -148,8 +150,8 @@ __device__ __forceinline__ void trace_layer0(const LevelArgs& a, const float* w0
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int pr = k8 * 4 + q;
-            const float4 A = reinterpret_cast<const float4*>(w0s)[2 * pr];
-            const float4 B = reinterpret_cast<const float4*>(w0s)[2 * pr + 1];
+            const float4 A = w0p[2 * pr];
+            const float4 B = w0p[2 * pr + 1];
             float2 c = make_float2(B.z, B.w);
             if (TIMED) c = __ffma2_rn(reinterpret_cast<const float2*>(wts)[pr], t2, c);
             const float2 z = __ffma2_rn(make_float2(A.x, A.y), px,
@@ -244,6 +246,11 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
     float* wts = reinterpret_cast<float*>(base + L.wt);
     float* bhs = reinterpret_cast<float*>(base + L.bh);
     float* wos = reinterpret_cast<float*>(base + L.wout);
+    // layer 0, the last hidden bias and the output weights: launch parameters at width 64
+    constexpr bool kc = W == kConstWidth;
+    const float4* w0p = kc ? a.k.w0 : reinterpret_cast<const float4*>(w0s);
+    const float* blast = kc ? reinterpret_cast<const float*>(a.k.bl) : bhs + (KH - 1) * W;
+    const float* wop = kc ? reinterpret_cast<const float*>(a.k.wo) : wos;
     const uint32_t bar_w = base_s + L.bars;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + L.misc);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(base + L.misc + 8);
@@ -363,9 +370,9 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
             const bool wact = __any_sync(0xffffffffu, ray.state == kSlotActive);
             if (wact) {
                 if (timed)
-                    trace_layer0<W, F16, SPLIT, true>(a, w0s, wts, ray, ttid, x_s, xlo_s);
+                    trace_layer0<W, F16, SPLIT, true>(a, w0p, wts, ray, ttid, x_s, xlo_s);
                 else
-                    trace_layer0<W, F16, SPLIT, false>(a, w0s, wts, ray, ttid, x_s, xlo_s);
+                    trace_layer0<W, F16, SPLIT, false>(a, w0p, wts, ray, ttid, x_s, xlo_s);
             }
             fence_proxy_async_smem();
             tc_fence_before();
@@ -445,7 +452,7 @@ __global__ void __launch_bounds__(kTraceMaxThreads, 1) trace_level_tc_kernel(con
                             float(&v)[16] = (q & 1) ? vb : va;
                             float(&vn)[16] = (q & 1) ? va : vb;
                             if (q + 1 < W / 16) tmem_ld16(tmem + lane_base + (q + 1) * 16u, vn);
-                            output_dot<16>(v, bl + q * 16, wos + q * 16, acc01, acc23);
+                            output_dot<16>(v, blast + q * 16, wop + q * 16, acc01, acc23);
                             tmem_wait_ld();
                         }
                     }
@@ -678,9 +685,9 @@ __global__ void __launch_bounds__(stream_threads(ST)) trace_level_tc_stream_kern
                     else
                         trace_layer0_e4m3<W, false>(a, w0s, wts, ray, ttid, x_s);
                 } else if (timed) {
-                    trace_layer0<W, F16, false, true>(a, w0s, wts, ray, ttid, x_s, x_s);
+                    trace_layer0<W, F16, false, true>(a, reinterpret_cast<const float4*>(w0s), wts, ray, ttid, x_s, x_s);
                 } else {
-                    trace_layer0<W, F16, false, false>(a, w0s, wts, ray, ttid, x_s, x_s);
+                    trace_layer0<W, F16, false, false>(a, reinterpret_cast<const float4*>(w0s), wts, ray, ttid, x_s, x_s);
                 }
             }
             fence_proxy_async_smem();
