@@ -20,6 +20,10 @@ struct Ray {
 };
 
 // Slab test of the ray against [lo, hi]^3: entry distance (>= 0) or -1 on a miss.
+// One hardware reciprocal per axis (relative error of a few units in the last
+// place: the entry point moves by ~1e-7, far inside every tolerance of the
+// trace); a component below the smallest normal float is taken as parallel
+// to its slab.
 __device__ __forceinline__ float slab_entry(float ox, float oy, float oz, float vx, float vy, float vz, float lo,
                                             float hi) {
     float tn = -INFINITY, tf = INFINITY;
@@ -27,8 +31,9 @@ __device__ __forceinline__ float slab_entry(float ox, float oy, float oz, float 
     bool miss = false;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        if (v[c] != 0.0f) {
-            const float t1 = (lo - o[c]) / v[c], t2 = (hi - o[c]) / v[c];
+        if (fabsf(v[c]) >= 0x1p-126f) {
+            const float r = __fdividef(1.0f, v[c]);
+            const float t1 = (lo - o[c]) * r, t2 = (hi - o[c]) * r;
             tn = fmaxf(tn, fminf(t1, t2));
             tf = fminf(tf, fmaxf(t1, t2));
         } else if (o[c] < lo || o[c] > hi) {
