@@ -35,8 +35,10 @@ struct NetView {
 };
 
 // The per-unit FP32 parameters of a width-64 network that the trace kernel
-// reads for every ray and step, carried in the launch parameters so that its
-// FMAs read them from the constant bank instead of shared memory.  Layer 0 on
+// reads for every ray and step, carried in the launch parameters so that the
+// kernel loads them through the constant cache instead of shared memory (a
+// float4 that all lanes load from one shared address costs extra shared-memory
+// wavefronts; a uniform constant load does not).  Layer 0 on
 // unit pairs p = (2p, 2p+1): w0[2p] = (w_x0, w_x1, w_y0, w_y1) and
 // w0[2p+1] = (w_z0, w_z1, b_0, b_1), the bias holding w_t * time when the
 // time is one scalar for all rays; bl = bias of the last hidden layer and
