@@ -531,6 +531,58 @@ def test_edge_cases(sdf):
     sdf.sync_status()
 
 
+def _degenerate_rays():
+    """Unit rays that exercise every branch of the box-entry (slab) test of Alg. 1's ray setup."""
+    rays = []
+    for ax in range(3):  # along each axis, from outside, through the interior
+        for s in (-1.0, 1.0):
+            o, v = [0.1, -0.2, 0.3], [0.0, 0.0, 0.0]
+            o[ax], v[ax] = -2.5 * s, s
+            rays.append((o, v))
+    for ax in range(3):  # parallel to a slab and outside it: a miss with no evaluation
+        o, v = [0.0, 0.0, 0.0], [0.0, 0.0, 0.0]
+        o[ax], o[(ax + 1) % 3], v[(ax + 1) % 3] = 1.5, 2.5, -1.0
+        rays.append((o, v))
+    rays += [([1.0, 0.3, 2.5], [0.0, 0.0, -1.0]),     # parallel, on a face of the closed slab
+             ([-1.0, 0.3, 2.5], [0.0, 0.0, -1.0]),
+             ([1.0, 1.0, 2.5], [0.0, 0.0, -1.0]),      # parallel along an edge: enters at a corner
+             ([0.2, 0.1, 1.0], [0.0, 0.0, -1.0]),      # starts on a face, pointing in
+             ([0.0, 0.0, 0.95], [0.0, 0.0, 1.0]),      # starts inside, pointing out
+             ([0.0, 0.0, 0.0], [0.6, 0.0, 0.8]),       # starts at the centre
+             ([0.3, 0.2, 2.5], [1e-30, 1e-30, -1.0]),  # tiny normal components
+             ([0.3, 0.2, 2.5], [1e-40, -1e-40, -1.0]),  # subnormal components: parallel to their slabs
+             ([1.5, 0.2, 2.5], [1e-40, 0.0, -1.0])]    # subnormal and outside its slab: a miss
+    o = np.array([r[0] for r in rays], np.float32).T.copy()
+    v = np.array([r[1] for r in rays], np.float32).T.copy()
+    ro, rv = inputs.random_rays(11, 64)  # oblique rays from every side
+    return np.concatenate([o, ro], axis=1), np.concatenate([v, rv], axis=1)
+
+
+@pytest.mark.parametrize("kernel", ["simt_fp32", "tc_w64_bf16", "tc_w128_bf16", "stream_w256_bf16"])
+def test_box_entry_of_degenerate_rays(sdf, kernel):
+    """A level with no iterations passes its rays on at their entry into the box, so the end points
+    are the slab test's entry points (Alg. 1's ray setup): the FP64 oracle's to a few FP32 units in
+    the last place of the entry distance (<= 5); rays that miss the box end at their origin with no
+    evaluation and no hit, and with 32 iterations allowed they still take none."""
+    width, n_hidden, precision = {"simt_fp32": (64, 1, sdf.SDF_FP32), "tc_w64_bf16": (64, 1, sdf.SDF_BF16),
+                                  "tc_w128_bf16": (128, 2, sdf.SDF_BF16),
+                                  "stream_w256_bf16": (256, 1, sdf.SDF_BF16)}[kernel]
+    b = inputs.net_to_bytes(inputs.siren_init(4, width, n_hidden, out_shift=0.3))
+    o, v = _degenerate_rays()
+    w0 = workloads.Workload("entry", [b], [0.0], [0], 1e-3, None, 0, 1, 1, b)
+    g = gpu_trace(sdf, [b], precision, w0, o, v)
+    r = oracle_trace([b], w0, o, v)
+    assert np.array_equal(g["iters"], r["iters"]) and not g["hit"].any() and not r["hit"].any()
+    assert np.abs(g["pos"].astype(np.float64) - r["pos"]).max() <= 4e-6
+    miss = np.all(r["pos"] == o.astype(np.float64), axis=0) & (np.abs(o).max(axis=0) > 1.0)
+    assert miss.sum() >= 4  # the parallel and subnormal misses above
+    assert np.array_equal(g["pos"][:, miss], o[:, miss])
+    w32 = workloads.Workload("entry32", [b], [0.0], [32], 1e-3, None, 0, 1, 1, b)
+    g32 = gpu_trace(sdf, [b], precision, w32, o, v)
+    assert (g32["iters"][miss] == 0).all() and not g32["hit"][miss].any()
+    assert np.array_equal(g32["pos"][:, miss], o[:, miss])
+
+
 @pytest.mark.parametrize("memory", ["pinned", "pageable", "mixed"])
 @pytest.mark.parametrize("size", [(160, 90), (640, 480), (1920, 1080)], ids=["1chunk", "2chunks", "4chunks"])
 def test_render_host_matches_device(sdf, size, memory):
