@@ -232,13 +232,14 @@ __device__ __forceinline__ void warp_sum32(float (&v)[32], int lane) {
 // grad f = w_out . (cos(A_k) (.) H_k), summed over the features by a warp
 // butterfly and shared-memory atomics, so no tangent of the last layer is
 // rounded to 16 bits.
-template <int W, int OP, bool TRAIN = false>
+//
 // One block per SM is stated for the width-64/128 training and E4M3 variants,
 // where it lets the compiler use the registers that one block leaves free
 // instead of spilling (fitting steps of the (64,2) and (128,2) 3 % and 5 %
 // faster).  Without it otherwise: the width-256 variants then allocate 96
 // registers (the cap of 18 warps, five of which share one scheduler's 16 K
 // registers) and spill, and the width-128 normal map measured 1 % slower.
+template <int W, int OP, bool TRAIN = false>
 __global__ void __launch_bounds__(GradCfg<W, OP>::THREADS, (W < 256 && (TRAIN || OP == kOpE4M3)) ? 1 : 0)
     grad_tc_kernel(const GradArgs a) {
     using C = GradCfg<W, OP>;

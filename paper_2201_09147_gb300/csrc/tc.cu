@@ -137,8 +137,7 @@ __device__ __forceinline__ void stage_layer0_pairs(const NetView& net, float tim
 // w_x p_x + (w_y p_y + (w_z p_z + b)), so each lane rounds as a scalar FMA
 // would.  With TIMED the ray's time is read here (it is not kept in a
 // register between steps).
-// w0p: the pairs in shared memory, or (width 64) in the launch parameters,
-// where the loop is unrolled whole so that every index is a constant.
+// w0p: the pairs in shared memory, or (width 64) in the launch parameters.
 template <int W, bool F16, bool SPLIT, bool TIMED>
 __device__ __forceinline__ void trace_layer0(const LevelArgs& a, const float4* w0p, const float* wts, const Ray& ray,
                                              int row, uint32_t x_s, uint32_t xlo_s) {
